@@ -1,0 +1,102 @@
+"""Pins Run(A), Mono(A) and Inv(A) (Section 2) to brute force, the worked
+example and the closed forms the paper states for its input classes."""
+import itertools
+from functools import lru_cache
+
+import numpy as np
+import pytest
+
+import oracle
+import sortrace_inputs as si
+
+
+def _mono_brute(seq):
+    """Fewest monotone pieces by dynamic programming over all cut points."""
+    n = len(seq)
+
+    def monotone(i, j):
+        s = seq[i:j]
+        return all(s[k] <= s[k + 1] for k in range(len(s) - 1)) or \
+            all(s[k] >= s[k + 1] for k in range(len(s) - 1))
+
+    @lru_cache(None)
+    def best(i):
+        if i == n:
+            return 0
+        return min(1 + best(j) for j in range(i + 1, n + 1) if monotone(i, j))
+
+    return best(0)
+
+
+def test_mono_runs_inv_brute_force():
+    for n in range(0, 8):
+        for seq in itertools.product(range(3), repeat=n):
+            a = np.array(seq, dtype=np.int32)
+            assert oracle.mono(a) == _mono_brute(seq), seq
+            desc = sum(1 for i in range(n - 1) if seq[i] > seq[i + 1])
+            assert oracle.runs(a) == (desc + 1 if n else 0)
+            inv = sum(1 for i in range(n) for j in range(i + 1, n) if seq[i] > seq[j])
+            assert oracle.inversions(a) == inv
+
+
+def test_worked_example():
+    a = np.array([1, 15, 18, 19, 20, 16, 11, 10, 9, 8, 7, 6, 5, 4, 3, 2], dtype=np.int32)
+    assert oracle.runs(a) == 12
+    assert oracle.mono(a) == 2
+
+
+@pytest.mark.parametrize("n", [1, 2, 17, 1000])
+def test_reversed_and_sorted(n):
+    r = si.reversed_i32(n, 1)
+    assert oracle.runs(r) == n
+    assert oracle.mono(r) == 1
+    assert oracle.inversions(r) == n * (n - 1) // 2
+    s = np.sort(r)
+    assert oracle.runs(s) == 1 and oracle.mono(s) == 1 and oracle.inversions(s) == 0
+
+
+@pytest.mark.parametrize("k", [1, 2, 4, 8, 64])
+def test_teeth_closed_forms(k):
+    n = 4096
+    eq = si.k_equal_teeth(n, k)
+    assert oracle.runs(eq) == k and oracle.mono(eq) == k
+    ev = si.k_even_teeth(n, k)
+    assert oracle.mono(ev) == k          # k <= n/3
+    sh = si.k_sharp_teeth(n, k)
+    assert oracle.mono(sh) == k
+    if k == 1:
+        assert np.array_equal(sh, np.arange(n, 0, -1, dtype=np.int32))
+
+
+def test_even_teeth_half_n():
+    """k = n/2: (2,1,1,2,2,1,1,2,...) with Mono = n/4 + 1 (Section 2)."""
+    n = 4096
+    a = si.k_even_teeth(n, n // 2)
+    assert a[:8].tolist() == [2, 1, 1, 2, 2, 1, 1, 2]
+    assert oracle.mono(a) == n // 4 + 1
+
+
+@pytest.mark.parametrize("k", [1, 5, 40])
+def test_k_exchange_bounds(k):
+    n = 5000
+    a = si.k_exchange(n, k, seed=k)
+    rank = np.argsort(np.argsort(a, kind="stable"), kind="stable")
+    assert np.count_nonzero(rank != np.arange(n)) <= 2 * k
+    assert oracle.mono(a) <= 2 * k + 1
+
+
+@pytest.mark.parametrize("k", [1, 7, 256])
+def test_k_distance_bound(k):
+    n = 5000
+    a = si.k_distance(n, k, seed=k)
+    rank = np.argsort(np.argsort(a, kind="stable"), kind="stable")
+    assert np.max(np.abs(rank - np.arange(n))) <= k
+
+
+def test_nearly_sorted_is_k_exchange():
+    n = 1 << 16
+    a = si.nearly_sorted_i32(n, 2)
+    m = n // 100
+    s = np.sort(a)
+    assert np.count_nonzero(a != s) <= 2 * m
+    assert oracle.mono(a) <= 2 * m + 1

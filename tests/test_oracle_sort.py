@@ -1,0 +1,220 @@
+"""Pins the CPU oracle's sorts to things other than themselves: brute force on
+tiny inputs (exhaustive), insertion sort, the library special cases, the
+worked example of Section 3, closed-form comparison counts, and invariants."""
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import sortrace_inputs as si
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ALGOS = ("merge", "quick")
+
+
+def _all_dtypes_random(rng, n, dtype):
+    if dtype == np.float32:
+        bits = rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32)
+        # keep NaN patterns out (totalOrder would still order them, but the
+        # workloads have none); mix in signed zeros and small integers
+        f = bits.view(np.float32)
+        bad = np.isnan(f)
+        bits[bad] = 0x80000000
+        f = bits.view(np.float32).copy()
+        f[rng.integers(0, n, max(1, n // 8))] = rng.integers(-3, 4, max(1, n // 8)).astype(np.float32)
+        return f
+    info = np.iinfo(dtype)
+    lo = max(info.min, -(1 << 62)) if dtype == np.int64 else info.min
+    hi = min(info.max, (1 << 62)) if dtype in (np.int64, np.uint64) else info.max
+    a = rng.integers(lo, hi, n, dtype=np.int64 if dtype != np.uint64 else np.uint64, endpoint=True)
+    return a.astype(dtype)
+
+
+def _total_order_key(f32):
+    """Python-side totalOrder key for the library pin (sign, magnitude)."""
+    b = int(np.float32(f32).view(np.uint32))
+    return -(b & 0x7FFFFFFF) - 1 if b >> 31 else (b & 0x7FFFFFFF)
+
+
+@pytest.mark.parametrize("n", range(0, 8))
+def test_exhaustive_small_with_duplicates(n):
+    """Every sequence over an alphabet of min(n, 4) values for n <= 7 (and all
+    permutations of distinct values): merge and quick equal Python's sorted()."""
+    alpha = range(min(n, 4) or 1)
+    for seq in itertools.product(alpha, repeat=n):
+        a = np.array(seq, dtype=np.int32)
+        want = np.array(sorted(seq), dtype=np.int32)
+        for algo in ALGOS + ("isort",):
+            assert np.array_equal(oracle.sort_keys(a, algo), want), (algo, seq)
+    for perm in itertools.permutations(range(n)):
+        a = np.array(perm, dtype=np.int32)
+        for algo in ALGOS:
+            assert np.array_equal(oracle.sort_keys(a, algo), np.arange(n, dtype=np.int32))
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.uint32, np.float32, np.uint64, np.int64])
+def test_random_vs_insertion_sort(dtype):
+    rng = np.random.default_rng(7)
+    for n in (1, 2, 3, 31, 32, 33, 64, 65, 100, 257, 1000, 2000):
+        a = _all_dtypes_random(rng, n, dtype)
+        ref = oracle.sort_keys(a, "isort")
+        for algo in ALGOS:
+            got = oracle.sort_keys(a, algo)
+            assert got.tobytes() == ref.tobytes(), (dtype, n, algo)
+
+
+def test_insertion_sort_vs_library():
+    """The brute-force definition agrees with the library sort (special case)."""
+    rng = np.random.default_rng(3)
+    for dtype in (np.int32, np.uint32, np.uint64, np.int64):
+        a = _all_dtypes_random(rng, 1500, dtype)
+        assert np.array_equal(oracle.sort_keys(a, "isort"), np.sort(a))
+    f = _all_dtypes_random(rng, 1500, np.float32)
+    want = sorted(f.tolist(), key=_total_order_key)
+    got = oracle.sort_keys(f, "isort")
+    assert [_total_order_key(x) for x in got.tolist()] == [_total_order_key(x) for x in want]
+
+
+def test_float_total_order():
+    """-0.0 sorts before +0.0, negatives reverse by magnitude, denormals and
+    infinities sit where IEEE-754 totalOrder puts them."""
+    vals = np.array([1.0, -0.0, 0.0, -1.0, np.inf, -np.inf, 1e-45, -1e-45, 2.5, -2.5],
+                    dtype=np.float32)
+    got = oracle.sort_keys(vals)
+    want = np.array([-np.inf, -2.5, -1.0, -1e-45, -0.0, 0.0, 1e-45, 1.0, 2.5, np.inf],
+                    dtype=np.float32)
+    assert got.view(np.uint32).tolist() == want.view(np.uint32).tolist()
+
+
+def test_int_extremes():
+    a = np.array([0, 2**31 - 1, -2**31, -1, 1, -2**31, 2**31 - 1], dtype=np.int32)
+    for algo in ALGOS:
+        assert oracle.sort_keys(a, algo).tolist() == sorted(a.tolist())
+    u = np.array([2**64 - 1, 0, 2**63, 2**63 - 1, 1], dtype=np.uint64)
+    assert oracle.sort_keys(u).tolist() == sorted(u.tolist())
+
+
+@pytest.mark.parametrize("kind", list(si.INT32_CLASSES))
+def test_classes_merge_quick_library(kind):
+    """On each workload class the two oracles and the library agree."""
+    a = si.int32_input(kind, 1 << 16, seed=5)
+    m = oracle.sort_keys(a, "merge")
+    q = oracle.sort_keys(a, "quick")
+    assert np.array_equal(m, q)
+    assert np.array_equal(m, np.sort(a))
+
+
+def test_presorted_classes():
+    for a in (si.k_equal_teeth(4096, 8), si.k_even_teeth(4096, 2), si.k_sharp_teeth(4096, 8),
+              si.k_distance(4096, 256), si.k_exchange(4096, 16), si.k_even_teeth(4096, 2048)):
+        for algo in ALGOS:
+            assert np.array_equal(oracle.sort_keys(a, algo), np.sort(a))
+
+
+def test_pairs_stability():
+    """Stable pair sort: keys non-decreasing, payloads increasing within equal
+    keys, and the library's stable argsort gives the same permutation."""
+    rng = np.random.default_rng(11)
+    for dtype in (np.int32, np.uint64, np.float32):
+        for n in (0, 1, 2, 33, 500, 5000):
+            k = (rng.integers(0, 7, n).astype(dtype) if n else np.zeros(0, dtype))
+            v = np.arange(n, dtype=np.uint32)
+            ok, ov = oracle.sort_pairs(k, v)
+            perm = np.argsort(k, kind="stable")
+            assert np.array_equal(ov, v[perm])
+            assert np.array_equal(ok, k[perm])
+    # exhaustive: all sequences over 3 values, n <= 7, against brute force
+    for n in range(8):
+        for seq in itertools.product(range(3), repeat=n):
+            k = np.array(seq, dtype=np.int32)
+            v = np.arange(n, dtype=np.uint32)
+            _, ov = oracle.sort_pairs(k, v)
+            want = [i for _, i in sorted(zip(seq, range(n)), key=lambda p: p[0])]
+            assert ov.tolist() == want
+
+
+def test_pairs_isort_agrees():
+    rng = np.random.default_rng(2)
+    k = rng.integers(0, 50, 1500).astype(np.uint64)
+    v = rng.integers(0, 1 << 32, 1500, dtype=np.uint64).astype(np.uint32)
+    a = oracle.sort_pairs(k, v, "merge")
+    b = oracle.sort_pairs(k, v, "isort")
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_segmented():
+    rng = np.random.default_rng(4)
+    lens = rng.integers(0, 300, 50)
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    k = rng.integers(-1000, 1000, int(off[-1])).astype(np.int32)
+    got = oracle.sort_segmented(k, off)
+    for s in range(50):
+        assert np.array_equal(got[off[s]:off[s + 1]], np.sort(k[off[s]:off[s + 1]]))
+
+
+def _read_golden(name):
+    out = {"trace": []}
+    with open(os.path.join(HERE, "golden", name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            tag, *rest = line.split()
+            if tag == "trace":
+                out["trace"].append((rest[0], int(rest[1])))
+            else:
+                out[tag] = [int(x) for x in rest]
+    return out
+
+
+def test_worked_example_section3():
+    """The merge the paper walks through: 1 trimmed, 15..20 (4 items) copied to
+    temporary memory, then a gallop of 5..11 (7 items) after three wins."""
+    g = _read_golden("worked_example_sec3.txt")
+    a = np.array(g["input"], dtype=np.int32)
+    out, ev = oracle.sort_with_trace(a)
+    assert out.tolist() == g["sorted"]
+    assert ev == g["trace"]
+    assert oracle.runs(a) == g["run"][0]
+    assert oracle.mono(a) == g["mono"][0]
+
+
+def test_comparison_counts_closed_forms():
+    """A natural mergesort makes exactly n-1 comparisons on sorted input and on
+    strictly descending input (one scan, then a reversal)."""
+    n = 100000
+    for a in (np.arange(n, dtype=np.int32), si.reversed_i32(n, 3)):
+        oracle.reset_comparisons()
+        oracle.sort_keys(a, "merge")
+        assert oracle.comparisons() == n - 1
+
+
+def test_comparison_counts_k_exchange_soft():
+    """Table 4 reports about 1.00 comparison per item for mergesort on
+    k-exchange lists (k = 2^0..2^8, n = 2,000,000); a soft check at n = 2^20."""
+    n = 1 << 20
+    per = []
+    for k in (1, 16, 256):
+        a = si.k_exchange(n, k, seed=k)
+        oracle.reset_comparisons()
+        oracle.sort_keys(a, "merge")
+        per.append(oracle.comparisons() / n)
+    assert all(1.0 <= p < 1.2 for p in per), per
+
+
+def test_random_comparisons_table4():
+    """Table 4 (n = 2,000,000, random integers): mer6 makes 22.15 and hyb2
+    24.77 comparisons per item on average over 100 instances; one instance of
+    the oracles lands within a few percent of both."""
+    n = 2_000_000
+    a = si.uniform_i32(n, 9)
+    oracle.reset_comparisons()
+    oracle.sort_keys(a, "merge")
+    merge = oracle.comparisons() / n
+    oracle.reset_comparisons()
+    oracle.sort_keys(a, "quick")
+    quick = oracle.comparisons() / n
+    assert abs(merge - 22.15) / 22.15 < 0.03, merge
+    assert abs(quick - 24.77) / 24.77 < 0.05, quick
