@@ -1,0 +1,189 @@
+// sr_device.cuh -- device building blocks of the GB300 merge sort.
+//
+// Keys stay in their native bit patterns in global memory.  On load every key
+// is mapped to an unsigned "order image" U whose unsigned order is the key
+// order (two's-complement flip for signed types, IEEE-754 totalOrder for
+// float32); every comparison is then one unsigned compare, and the inverse map
+// is applied on store.
+//
+// The building blocks follow the merge structure of the paper's mergesort
+// (Section 3): runs are merged pairwise, round after round (policy e1), and a
+// merge never lets a B item pass an equal A item (stability, technique (a)).
+// Where the paper's merge is one sequential loop, here a merge of two runs is
+// cut along the diagonals of its merge matrix ("merge path") into pieces of
+// IPT outputs, one per thread, each found by a binary search -- the parallel
+// form of galloping (technique (g)).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sortrace.h"
+
+namespace sr {
+
+// ------------------------------------------------------------ key images
+
+template <int KT> struct Key;
+
+template <> struct Key<SR_KEY_I32> {
+    typedef uint32_t T;
+    typedef uint32_t U;
+    static __device__ __forceinline__ U ord(T x) { return x ^ 0x80000000u; }
+    static __device__ __forceinline__ T unord(U u) { return u ^ 0x80000000u; }
+};
+template <> struct Key<SR_KEY_U32> {
+    typedef uint32_t T;
+    typedef uint32_t U;
+    static __device__ __forceinline__ U ord(T x) { return x; }
+    static __device__ __forceinline__ T unord(U u) { return u; }
+};
+// totalOrder: a clear sign bit maps above every set one; negative patterns
+// are inverted so a larger magnitude orders lower.
+template <> struct Key<SR_KEY_F32> {
+    typedef uint32_t T;
+    typedef uint32_t U;
+    static __device__ __forceinline__ U ord(T x) {
+        return x ^ ((uint32_t)((int32_t)x >> 31) | 0x80000000u);
+    }
+    static __device__ __forceinline__ T unord(U u) {
+        return u ^ (((u >> 31) - 1u) | 0x80000000u);
+    }
+};
+template <> struct Key<SR_KEY_U64> {
+    typedef unsigned long long T;
+    typedef unsigned long long U;
+    static __device__ __forceinline__ U ord(T x) { return x; }
+    static __device__ __forceinline__ T unord(U u) { return u; }
+};
+template <> struct Key<SR_KEY_I64> {
+    typedef unsigned long long T;
+    typedef unsigned long long U;
+    static __device__ __forceinline__ U ord(T x) { return x ^ 0x8000000000000000ull; }
+    static __device__ __forceinline__ T unord(U u) { return u ^ 0x8000000000000000ull; }
+};
+
+template <typename U> __device__ __forceinline__ U umax_of() { return ~U(0); }
+
+// ---------------------------------------------------------- launch shapes
+//
+// IPT is odd so that thread t's IPT consecutive shared-memory words
+// t*IPT .. t*IPT+IPT-1 fall in distinct banks across a warp (gcd(IPT, 32) = 1).
+template <int KB, bool VALS> struct Shape;
+template <> struct Shape<4, false> { enum { NT = 256, IPT = 15, SORT_NT = 512 }; };
+template <> struct Shape<4, true>  { enum { NT = 256, IPT = 11, SORT_NT = 512 }; };
+template <> struct Shape<8, false> { enum { NT = 256, IPT = 11, SORT_NT = 512 }; };
+template <> struct Shape<8, true>  { enum { NT = 256, IPT = 9,  SORT_NT = 512 }; };
+
+// ------------------------------------------------------------- merge path
+
+// Number of A items among the first `diag` outputs of the stable merge of
+// sorted a[0..na) and b[0..nb): the largest i with a[i-1] <= b[diag-i]
+// (an A item goes first on ties).
+template <typename U>
+__device__ __forceinline__ int merge_path(const U *a, int na, const U *b, int nb, int diag) {
+    int lo = max(0, diag - nb), hi = min(diag, na);
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (!(b[diag - 1 - mid] < a[mid])) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// IPT outputs of the stable merge of s[a..a_end) and s[b..b_end) into
+// registers; ix[i] is the shared-memory index each output came from.
+template <typename U, int IPT>
+__device__ __forceinline__ void serial_merge(const U *s, int a, int a_end, int b, int b_end,
+                                             U (&k)[IPT], int (&ix)[IPT]) {
+    U ak = a < a_end ? s[a] : U(0);
+    U bk = b < b_end ? s[b] : U(0);
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+        const bool take_a = (b >= b_end) || ((a < a_end) && !(bk < ak));
+        k[i] = take_a ? ak : bk;
+        ix[i] = take_a ? a : b;
+        if (take_a) { ++a; if (a < a_end) ak = s[a]; }
+        else        { ++b; if (b < b_end) bk = s[b]; }
+    }
+}
+
+// Stable sort of a thread's IPT registers: odd-even transposition (only
+// neighbours swap, and only on a strict descent).
+template <typename U, int IPT, bool VALS>
+__device__ __forceinline__ void thread_sort(U (&k)[IPT], uint32_t (&v)[IPT]) {
+#pragma unroll
+    for (int r = 0; r < IPT; ++r) {
+#pragma unroll
+        for (int i = r & 1; i + 1 < IPT; i += 2) {
+            if (k[i + 1] < k[i]) {
+                const U tk = k[i]; k[i] = k[i + 1]; k[i + 1] = tk;
+                if (VALS) { const uint32_t tv = v[i]; v[i] = v[i + 1]; v[i + 1] = tv; }
+            }
+        }
+    }
+}
+
+// Sorts the NT*IPT items held blocked in registers (thread t holds items
+// t*IPT .. t*IPT+IPT-1): a stable register sort, then log2(NT) rounds of
+// pairwise merges through shared memory (sk: NT*IPT keys, sv: NT*IPT values).
+// On return the registers hold the sorted tile, blocked.
+template <typename U, int NT, int IPT, bool VALS>
+__device__ __forceinline__ void block_sort(U (&k)[IPT], uint32_t (&v)[IPT], U *sk, uint32_t *sv) {
+    thread_sort<U, IPT, VALS>(k, v);
+    const int t = threadIdx.x;
+#pragma unroll 1
+    for (int coop = 2; coop <= NT; coop <<= 1) {
+#pragma unroll
+        for (int i = 0; i < IPT; ++i) sk[t * IPT + i] = k[i];
+        if (VALS) {
+#pragma unroll
+            for (int i = 0; i < IPT; ++i) sv[t * IPT + i] = v[i];
+        }
+        __syncthreads();
+        const int first = t & ~(coop - 1);
+        const int run = (coop >> 1) * IPT;
+        const int a0 = first * IPT, b0 = a0 + run;
+        const int diag = (t - first) * IPT;
+        const int sp = merge_path(sk + a0, run, sk + b0, run, diag);
+        int ix[IPT];
+        serial_merge<U, IPT>(sk, a0 + sp, b0, b0 + diag - sp, b0 + run, k, ix);
+        if (VALS) {
+#pragma unroll
+            for (int i = 0; i < IPT; ++i) v[i] = sv[ix[i]];
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------- per-call control
+
+enum { MODE_SORT = 0, MODE_SORTED = 1, MODE_REVERSE = 2 };
+enum { MAX_PASSES = 48 };
+
+// Lives in the call's scratch; zeroed at the start of every call.
+struct Ctrl {
+    unsigned long long descents;        // pairs a[i] > a[i+1]
+    unsigned long long nondescents;     // pairs a[i] <= a[i+1]
+    unsigned long long tiles_ascending;
+    unsigned long long tiles_descending;
+    int unordered[MAX_PASSES];          // per merge pass: run pairs not already in order
+    int status;
+    int pad;
+};
+
+__device__ __forceinline__ int call_mode(const Ctrl *c, long long n) {
+    if (c->descents == 0) return MODE_SORTED;
+    if (c->nondescents == 0 && n > 1) return MODE_REVERSE;
+    return MODE_SORT;
+}
+
+// Which buffer (0 = caller's, 1 = scratch) holds the data before merge pass p:
+// the block sort wrote buffer cur0, and every pass that was not skipped flips it.
+__device__ __forceinline__ int buffer_before_pass(const Ctrl *c, int cur0, int p) {
+    int flips = 0;
+    for (int q = 0; q < p; ++q) flips += c->unordered[q] != 0;
+    return cur0 ^ (flips & 1);
+}
+
+}  // namespace sr

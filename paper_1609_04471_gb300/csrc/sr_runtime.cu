@@ -1,0 +1,157 @@
+// sr_runtime.cu -- per-device state, scratch pool, status word and statistics.
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+
+#include "sr_runtime.cuh"
+
+namespace sr {
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+DeviceState g_dev[kMaxDevices];
+thread_local CallRecord g_rec;
+}  // namespace
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int ceil_log2(unsigned long long x) {
+    int r = 0;
+    while ((1ull << r) < x) ++r;
+    return r;
+}
+
+size_t key_bytes_of(sr_key_type kt) { return (kt == SR_KEY_U64 || kt == SR_KEY_I64) ? 8 : 4; }
+
+bool valid_key_type(int kt) { return kt >= SR_KEY_I32 && kt <= SR_KEY_I64; }
+
+CallRecord &call_record() { return g_rec; }
+
+sr_status launch_status() {
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) return SR_OK;
+    if (e == cudaErrorMemoryAllocation) return SR_ERR_OOM;
+    return SR_ERR_CUDA;
+}
+
+sr_status device_state(DeviceState **out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return SR_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lock(g_mu);
+    DeviceState &ds = g_dev[dev];
+    if (ds.device < 0) {
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        if (cudaMemPoolCreate(&ds.pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return SR_ERR_CUDA;
+        }
+        // keep freed scratch cached in the pool between calls
+        uint64_t keep = ~0ull;
+        cudaMemPoolSetAttribute(ds.pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (cudaMalloc(&ds.status, sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&ds.last_ctrl, sizeof(Ctrl)) != cudaSuccess ||
+            cudaMemset(ds.status, 0, sizeof(int)) != cudaSuccess ||
+            cudaMemset(ds.last_ctrl, 0, sizeof(Ctrl)) != cudaSuccess ||
+            cudaDeviceSynchronize() != cudaSuccess) {
+            cudaGetLastError();
+            return SR_ERR_CUDA;
+        }
+        ds.device = dev;
+    }
+    *out = &ds;
+    return SR_OK;
+}
+
+sr_status scratch_alloc(DeviceState *ds, void **p, size_t bytes, cudaStream_t s) {
+    *p = nullptr;
+    const char *inj = std::getenv("SR_INJECT_OOM");
+    if (inj && inj[0] && std::strcmp(inj, "0") != 0) return SR_ERR_OOM;
+    if (bytes == 0) bytes = 256;
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, ds->pool, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return e == cudaErrorMemoryAllocation ? SR_ERR_OOM : SR_ERR_CUDA;
+    }
+    return SR_OK;
+}
+
+void scratch_free(void *p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
+
+}  // namespace sr
+
+using namespace sr;
+
+extern "C" const char *sr_status_string(sr_status s) {
+    switch (s) {
+    case SR_OK: return "SR_OK";
+    case SR_ERR_INVALID_ARG: return "SR_ERR_INVALID_ARG";
+    case SR_ERR_UNSUPPORTED: return "SR_ERR_UNSUPPORTED";
+    case SR_ERR_OOM: return "SR_ERR_OOM";
+    case SR_ERR_CUDA: return "SR_ERR_CUDA";
+    case SR_ERR_TIMEOUT: return "SR_ERR_TIMEOUT";
+    case SR_ERR_INTERNAL: return "SR_ERR_INTERNAL";
+    case SR_ERR_BAD_SEGMENTS: return "SR_ERR_BAD_SEGMENTS";
+    default: return "SR_ERR_UNKNOWN";
+    }
+}
+
+extern "C" sr_status sr_stream_status(sr_stream stream) {
+    DeviceState *ds = nullptr;
+    SR_TRY(device_state(&ds));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaStreamSynchronize(s) != cudaSuccess) { cudaGetLastError(); return SR_ERR_CUDA; }
+    int word = 0;
+    if (cudaMemcpy(&word, ds->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemset(ds->status, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return SR_ERR_CUDA;
+    }
+    return (sr_status)word;
+}
+
+extern "C" sr_status sr_get_stats(sr_stats *out) {
+    if (!out) return SR_ERR_INVALID_ARG;
+    CallRecord &r = call_record();
+    *out = r.host;
+    out->abi_version = SR_ABI_VERSION;
+    if (!r.has_ctrl) return SR_OK;
+    DeviceState *ds = nullptr;
+    SR_TRY(device_state(&ds));
+    if (cudaStreamSynchronize(r.stream) != cudaSuccess) { cudaGetLastError(); return SR_ERR_CUDA; }
+    Ctrl c;
+    if (cudaMemcpy(&c, ds->last_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return SR_ERR_CUDA;
+    }
+    const unsigned long long n = out->n;
+    const unsigned long long elem = (unsigned long long)(r.key_bytes + r.val_bytes);
+    out->runs = n ? c.descents + 1 : 0;
+    out->input_class = c.descents == 0 ? 1 : (c.nondescents == 0 && n > 1 ? 2 : 0);
+    unsigned long long bytes = n * (unsigned long long)r.key_bytes;     // the scan reads the keys
+    int skipped = 0, merged = 0;
+    if (out->input_class == 0) {
+        bytes += 2 * n * elem;                                          // block sort
+        for (int p = 0; p < out->passes_planned && p < MAX_PASSES; ++p) {
+            if (c.unordered[p] == 0) ++skipped;
+            else { ++merged; bytes += 2 * n * elem; }
+        }
+        if (((r.cur0 + merged) & 1) != 0) bytes += 2 * n * elem;         // copy back
+    } else if (out->input_class == 2) {
+        bytes += 2 * n * elem;                                          // one reversal
+    }
+    out->passes_skipped = skipped;
+    out->bytes_moved = bytes;
+    return SR_OK;
+}

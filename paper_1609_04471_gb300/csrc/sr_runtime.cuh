@@ -1,0 +1,64 @@
+// sr_runtime.cuh -- host-side runtime shared by the sort entry points:
+// per-device state (a stream-ordered scratch pool, the device status word,
+// the last call's control block), thread-local call statistics and error
+// mapping.  Nothing here is on the device's hot path.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "sortrace.h"
+#include "sr_device.cuh"
+
+namespace sr {
+
+struct DeviceState {
+    int device = -1;
+    cudaMemPool_t pool = nullptr;   // scratch: stream-ordered, kept cached
+    int *status = nullptr;          // device status word (sr_status codes)
+    Ctrl *last_ctrl = nullptr;      // copy of the last call's control block
+};
+
+// Per-device state of the current device, created on first use (the first
+// call on a device must not be inside a stream capture).
+sr_status device_state(DeviceState **out);
+
+// Scratch of `bytes` from the device pool, ordered on `s`.  Honours the
+// SR_INJECT_OOM environment variable (any non-empty value but "0") by failing
+// with SR_ERR_OOM, so the error path can be tested without exhausting memory.
+sr_status scratch_alloc(DeviceState *ds, void **p, size_t bytes, cudaStream_t s);
+void scratch_free(void *p, cudaStream_t s);
+
+// Maps the last CUDA error to a status (and clears it).
+sr_status launch_status();
+
+// Thread-local record of the last call, completed by sr_get_stats.
+struct CallRecord {
+    sr_stats host;                  // fields known on the host
+    cudaStream_t stream = nullptr;
+    bool has_ctrl = false;          // last_ctrl holds this call's control block
+    int key_bytes = 4;
+    int val_bytes = 0;
+    int cur0 = 0;
+};
+CallRecord &call_record();
+
+size_t align_up(size_t x, size_t a);
+int ceil_log2(unsigned long long x);
+size_t key_bytes_of(sr_key_type kt);
+bool valid_key_type(int kt);
+
+}  // namespace sr
+
+#define SR_TRY(expr)                               \
+    do {                                           \
+        sr_status _st = (expr);                    \
+        if (_st != SR_OK) return _st;              \
+    } while (0)
+
+#define SR_LAUNCHED()                              \
+    do {                                           \
+        sr_status _st = ::sr::launch_status();     \
+        if (_st != SR_OK) return _st;              \
+    } while (0)

@@ -1,0 +1,223 @@
+"""GPU parity of sr_sort_keys / sr_sort_pairs / sr_detect_runs against the CPU
+oracle, bit for bit, through the C ABI.  Sizes span one tile, several tiles
+and ragged tails; the four workload classes at 2^24 (the benchmark's launch
+configuration) are compared in full."""
+import numpy as np
+import pytest
+
+import oracle
+import sortrace_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+KT = {np.dtype(np.int32): 0, np.dtype(np.uint32): 1, np.dtype(np.float32): 2,
+      np.dtype(np.uint64): 3, np.dtype(np.int64): 4}
+# tile shapes of the library: merge tiles of 256*IPT keys, block-sort tiles of 512*IPT
+TILES = {4: (3840, 7680), 8: (2816, 5632)}
+
+
+def _to_dev(a):
+    import torch
+    bits = {4: np.int32, 8: np.int64}[a.dtype.itemsize]
+    return torch.from_numpy(np.ascontiguousarray(a).view(bits).copy()).cuda()
+
+
+def _from_dev(t, dtype):
+    return t.cpu().numpy().view(dtype)
+
+
+def _gpu_sort(sr, a):
+    t = _to_dev(a)
+    sr.sort_keys(t, key_type=KT[a.dtype])
+    return _from_dev(t, a.dtype)
+
+
+def _gpu_pairs(sr, k, v):
+    import torch
+    tk = _to_dev(k)
+    tv = torch.from_numpy(v.view(np.int32).copy()).cuda()
+    sr.sort_pairs(tk, tv, key_type=KT[k.dtype])
+    return _from_dev(tk, k.dtype), tv.cpu().numpy().view(np.uint32)
+
+
+def _random(rng, n, dtype):
+    if dtype == np.float32:
+        b = rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32)
+        f = b.view(np.float32)
+        b[np.isnan(f)] ^= 0x00400000      # keep a few NaN-free patterns distinct
+        return b.view(np.float32)
+    if dtype in (np.uint64, np.int64):
+        return rng.integers(0, 1 << 64, n, dtype=np.uint64).view(dtype) if dtype == np.int64 else \
+            rng.integers(0, 1 << 64, n, dtype=np.uint64)
+    return rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32).view(dtype)
+
+
+def _sizes(kb):
+    nv, ts = TILES[kb]
+    return sorted({0, 1, 2, 3, 5, 31, 32, 33, 255, 1000, nv - 1, nv, nv + 1, ts - 1, ts, ts + 1,
+                   2 * ts + 7, 4 * ts - 1, (1 << 16) + 1, 5 * ts + 3, 100_003, (1 << 20) - 1})
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.uint32, np.float32, np.uint64, np.int64])
+def test_keys_random_sizes(gpu_lib, dtype):
+    rng = np.random.default_rng(10)
+    for n in _sizes(np.dtype(dtype).itemsize):
+        a = _random(rng, n, dtype)
+        got = _gpu_sort(gpu_lib, a)
+        want = oracle.sort_keys(a)
+        assert got.tobytes() == want.tobytes(), (dtype, n)
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.float32, np.uint64])
+def test_keys_heavy_duplicates(gpu_lib, dtype):
+    rng = np.random.default_rng(11)
+    for n in (7, 4000, 9000, 123_457):
+        a = rng.integers(0, 5, n).astype(dtype)
+        assert _gpu_sort(gpu_lib, a).tobytes() == oracle.sort_keys(a).tobytes()
+
+
+def test_edge_values(gpu_lib):
+    i32 = np.array([0, -1, 1, 2**31 - 1, -2**31] * 3001, dtype=np.int32)
+    assert _gpu_sort(gpu_lib, i32).tobytes() == oracle.sort_keys(i32).tobytes()
+    f = np.array([0.0, -0.0, 1e-45, -1e-45, np.inf, -np.inf, 3.5, -3.5, 1.17549435e-38,
+                  -1.17549435e-38] * 2001, dtype=np.float32)
+    assert _gpu_sort(gpu_lib, f).view(np.uint32).tolist() == oracle.sort_keys(f).view(np.uint32).tolist()
+    # NaN patterns order by their bits under totalOrder
+    nan = np.array([np.nan, -np.nan, 1.0, -1.0, np.inf] * 999, dtype=np.float32)
+    nan.view(np.uint32)[::7] = 0x7FC00001
+    assert _gpu_sort(gpu_lib, nan).view(np.uint32).tolist() == oracle.sort_keys(nan).view(np.uint32).tolist()
+    u64 = np.array([0, 2**64 - 1, 2**63, 2**63 - 1, 1] * 4001, dtype=np.uint64)
+    assert _gpu_sort(gpu_lib, u64).tobytes() == oracle.sort_keys(u64).tobytes()
+    i64 = u64.view(np.int64)
+    assert _gpu_sort(gpu_lib, i64).tobytes() == oracle.sort_keys(i64).tobytes()
+
+
+def test_all_equal_and_presorted(gpu_lib):
+    for a in (np.full(50_001, 7, np.int32), np.arange(50_001, dtype=np.int32),
+              np.arange(50_001, 0, -1, dtype=np.int32),
+              np.repeat(np.arange(1000, 0, -1, dtype=np.int32), 50),   # descending, not strictly
+              si.k_equal_teeth(1 << 17, 8), si.k_even_teeth(1 << 17, 2), si.k_sharp_teeth(1 << 17, 8),
+              si.k_distance(1 << 17, 256), si.k_exchange(1 << 17, 16),
+              np.tile(np.array([1, 0], np.int32), 40_000)):
+        assert _gpu_sort(gpu_lib, a).tobytes() == oracle.sort_keys(a).tobytes()
+
+
+def test_sorted_input_moves_nothing(gpu_lib):
+    import torch
+    n = 1 << 20
+    a = np.sort(si.uniform_i32(n, 3))
+    t = _to_dev(a)
+    gpu_lib.sort_keys(t, key_type=0)
+    st = gpu_lib.stats()
+    assert st["input_class"] == 1 and st["runs"] == 1
+    assert st["bytes_moved"] == 4 * n           # the scan's read only
+    assert _from_dev(t, np.int32).tobytes() == a.tobytes()
+    torch.cuda.synchronize()
+
+
+def test_reversed_input_one_pass(gpu_lib):
+    n = (1 << 20) + 3
+    a = si.reversed_i32(n, 4)
+    t = _to_dev(a)
+    gpu_lib.sort_keys(t, key_type=0)
+    st = gpu_lib.stats()
+    assert st["input_class"] == 2 and st["runs"] == n
+    assert st["bytes_moved"] == 4 * n + 8 * n   # scan + one reversal
+    assert _from_dev(t, np.int32).tobytes() == oracle.sort_keys(a).tobytes()
+
+
+def test_teeth_skip_passes(gpu_lib):
+    """2-equal teeth whose teeth are whole numbers of block-sort tiles (128
+    tiles of 7680 int32 keys): every merge pass below the tooth length finds
+    all its run pairs in order and is skipped; only the last pass merges."""
+    n = 128 * TILES[4][1]
+    a = si.k_equal_teeth(n, 2)
+    t = _to_dev(a)
+    gpu_lib.sort_keys(t, key_type=0)
+    st = gpu_lib.stats()
+    assert st["passes_planned"] == 7 and st["passes_skipped"] == 6
+    assert _from_dev(t, np.int32).tobytes() == oracle.sort_keys(a).tobytes()
+
+
+@pytest.mark.parametrize("kind", list(si.INT32_CLASSES))
+def test_classes_2_20(gpu_lib, kind):
+    a = si.int32_input(kind, (1 << 20) + 17, seed=7)
+    assert _gpu_sort(gpu_lib, a).tobytes() == oracle.sort_keys(a).tobytes()
+
+
+def test_two_million_uniform_seed1(gpu_lib):
+    """2,000,000 uniform int32 keys, seed 1 (the paper's Table 1 size)."""
+    a = si.uniform_i32(2_000_000, 1)
+    assert _gpu_sort(gpu_lib, a).tobytes() == oracle.sort_keys(a).tobytes()
+
+
+@pytest.mark.parametrize("kind", list(si.INT32_CLASSES))
+def test_classes_2_24_full(gpu_lib, kind):
+    """The benchmark's workload: 2^24 int32 keys of each class, seed 1,
+    compared in full with the oracle."""
+    a = si.int32_input(kind, 1 << 24, seed=1)
+    assert _gpu_sort(gpu_lib, a).tobytes() == oracle.sort_keys(a).tobytes()
+
+
+def test_detect_runs_matches_oracle(gpu_lib):
+    for a in (si.uniform_i32(100_000, 2), si.k_exchange(100_000, 50), si.reversed_i32(77_777, 1),
+              np.sort(si.uniform_i32(70_000, 3)), si.few_unique_i32(90_000, 5),
+              np.array([1, 15, 18, 19, 20, 16, 11, 10, 9, 8, 7, 6, 5, 4, 3, 2], np.int32)):
+        info = gpu_lib.detect_runs(_to_dev(a), key_type=0)
+        assert info["runs"] == oracle.runs(a)
+        assert info["sorted"] == (oracle.runs(a) == 1)
+    f = si.lognormal_f32(200_001, 3)
+    assert gpu_lib.detect_runs(_to_dev(f), key_type=2)["runs"] == oracle.runs(f)
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.float32, np.uint64, np.int64, np.uint32])
+def test_pairs_stable(gpu_lib, dtype):
+    rng = np.random.default_rng(12)
+    for n in (0, 1, 2, 33, 2816, 2817, 5632, 5633, 30_001, 262_147):
+        k = (rng.integers(0, 9, n).astype(dtype) if n % 2 else _random(rng, n, dtype))
+        v = rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32)
+        gk, gv = _gpu_pairs(gpu_lib, k, v)
+        ok, ov = oracle.sort_pairs(k, v)
+        assert gk.tobytes() == ok.tobytes() and gv.tobytes() == ov.tobytes(), (dtype, n)
+
+
+def test_pairs_presorted(gpu_lib):
+    n = 200_003
+    for k in (np.arange(n, dtype=np.uint64), np.arange(n, 0, -1).astype(np.uint64),
+              np.repeat(np.arange(1000, 0, -1), n // 1000 + 1)[:n].astype(np.uint64)):
+        v = np.arange(n, dtype=np.uint32)
+        gk, gv = _gpu_pairs(gpu_lib, k, v)
+        ok, ov = oracle.sort_pairs(k, v)
+        assert gk.tobytes() == ok.tobytes() and gv.tobytes() == ov.tobytes()
+
+
+def test_pairs_zipf_2_20(gpu_lib):
+    k, v = si.pairs_u64_zipf(1 << 20, 1)
+    gk, gv = _gpu_pairs(gpu_lib, k, v)
+    ok, ov = oracle.sort_pairs(k, v)
+    assert gk.tobytes() == ok.tobytes() and gv.tobytes() == ov.tobytes()
+
+
+def test_deterministic(gpu_lib):
+    a = si.uniform_i32(3_000_001, 5)
+    assert _gpu_sort(gpu_lib, a).tobytes() == _gpu_sort(gpu_lib, a).tobytes()
+
+
+def test_host_entry_point(gpu_lib):
+    a = si.nearly_sorted_i32((1 << 20) + 5, 2)
+    b = a.copy()
+    gpu_lib.sort_keys_host(b)
+    assert b.tobytes() == oracle.sort_keys(a).tobytes()
+
+
+def test_oom_injection(gpu_lib, monkeypatch):
+    import torch
+    a = _to_dev(si.uniform_i32(100_000, 1))
+    before = a.clone()
+    monkeypatch.setenv("SR_INJECT_OOM", "1")
+    with pytest.raises(gpu_lib.SortError) as e:
+        gpu_lib.sort_keys(a, key_type=0)
+    assert e.value.code == 3
+    monkeypatch.delenv("SR_INJECT_OOM")
+    torch.cuda.synchronize()
+    assert torch.equal(a, before)
