@@ -1,0 +1,443 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 comparison sort.
+
+Workload (one "step"): sort the four 2^24-key int32 arrays of the benchmark
+configuration -- uniform random, strictly descending, nearly sorted (1% of
+positions exchanged) and few unique (16 values) -- all drawn from seed 1.
+Each array is restored from a pristine device copy and L2 is flushed (a
+512 MiB write, larger than the 129 MB L2) before every sort; only the sorts
+are timed, with CUDA events on the sorting stream.
+
+Printed: one JSON line with the metric (Gkeys/s), the per-kernel HBM roofline
+of the dominant kernel measured live, the end-to-end number through the
+host-buffer entry point, the CPU oracle baseline, clocks and launch count.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs N independent replicas (one per GPU; the sort does not shard).
+--impl reference times the CPU oracle (the paper's mergesort, single thread)
+on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Gkeys/s at 2^24–2^28 int32, % of HBM roofline; learned/batched vs plain"
+N_KEYS = 1 << 24
+CLASSES = ("uniform", "reversed", "nearly_sorted", "few_unique")
+SEED = 1
+FLUSH_BYTES = 512 << 20
+CPU_SAMPLE = 1 << 22          # keys of each array the CPU baseline sorts
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the 2^24..2^28 size sweep")
+    ap.add_argument("--profile-case", type=int, default=0, metavar="LOG2N",
+                    help="for ncu: sort a uniform int32 array of 2^LOG2N keys twice (warm-up + one) and exit")
+    ap.add_argument("--profile-pairs", action="store_true",
+                    help="with --profile-case: a stable uint64-key + uint32-payload sort instead")
+    return ap.parse_args()
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _ncu_traffic(kernel_tag: str):
+    """Per-launch DRAM bytes of a kernel from its committed ncu summary, or
+    None if the summary is missing or the kernel's sources changed since."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*(\d+)", txt)
+    h = re.search(r"source_sha256:\s*([0-9a-f]+)", txt)
+    if not m or not h:
+        return None
+    src = b""
+    for fn in ("sr_sort.cu", "sr_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1609_04471_gb300", "csrc", fn), "rb") as f:
+            src += f.read()
+    if hashlib.sha256(src).hexdigest()[:16] != h.group(1)[:16]:
+        return None
+    return int(m.group(1))
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.12)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = max((float(r[2]) for r in rows if r[2].replace(".", "").isdigit()), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _cpu_baseline(arrays, sample=CPU_SAMPLE):
+    """The oracle (single-threaded C mergesort) on the first `sample` keys of
+    each array of the workload; returns (Gkeys/s, seconds, keys)."""
+    import oracle
+    oracle.build()
+    keys = 0
+    t0 = time.perf_counter()
+    for a in arrays:
+        oracle.sort_keys(a[:sample], "merge")
+        keys += min(sample, a.size)
+    dt = time.perf_counter() - t0
+    return keys / dt / 1e9, dt, keys
+
+
+def _cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def _config():
+    return {"workload": "sort 4 arrays of 2^24 int32 keys (uniform, strictly descending, "
+                        "nearly sorted 1% exchanges, few unique 16 values), seed 1",
+            "n": N_KEYS, "arrays": 4, "l2": "flushed before every timed sort (512 MiB write)"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import sortrace_inputs as si
+    arrays = [si.int32_input(k, N_KEYS, SEED) for k in CLASSES]
+    for _ in range(args.warmup):
+        _cpu_baseline(arrays)
+    times = []
+    keys = 0
+    for _ in range(args.steps):
+        v, dt, keys = _cpu_baseline(arrays)
+        times.append(dt)
+    ms = 1e3 * sum(times) / len(times)
+    value = keys / (ms / 1e3) / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "i32", "data": "synthetic",
+        "config": _config(),
+        "cpu_baseline": {"value": value, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {CPU_SAMPLE} keys of each of the 4 arrays per step",
+                         "cpu": _cpu_model(), "nproc": os.cpu_count()},
+        "e2e": {"value": value, "unit": "Gkeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def _gen_arrays():
+    import sortrace_inputs as si
+    return [si.int32_input(k, N_KEYS, SEED) for k in CLASSES]
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import paper_1609_04471_gb300 as sr
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    sr.load()
+    peak, peak_kind = _peaks()
+
+    arrays = _gen_arrays()
+    pristine = [torch.from_numpy(a).to(dev) for a in arrays]
+    work = [torch.empty_like(p) for p in pristine]
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def one_step(step, timed, prof):
+        ms = []
+        for c in range(len(CLASSES)):
+            work[c].copy_(pristine[c])
+            flush.fill_(step & 0xFF)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            if prof is not None:
+                sr.profile_begin()
+            e0.record(stream)
+            sr.sort_keys(work[c])
+            e1.record(stream)
+            if prof is not None:
+                k = sr.profile_end()
+                st = sr.stats()
+                prof.append((c, k, st))
+            ms.append((e0, e1))
+        return ms
+
+    for w in range(args.warmup):
+        one_step(w, False, None)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    launches0 = sr.launch_count()
+    prof = []
+    events = []
+    wall0 = time.perf_counter()
+    for step in range(args.steps):
+        events.append(one_step(step, True, prof))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    launches = sr.launch_count() - launches0
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+
+    per_class_ms = [0.0] * len(CLASSES)
+    for evs in events:
+        for c, (e0, e1) in enumerate(evs):
+            per_class_ms[c] += e0.elapsed_time(e1)
+    per_class_ms = [m / args.steps for m in per_class_ms]
+    ms_step = sum(per_class_ms)
+    if ws > 1:
+        t = torch.tensor([ms_step], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t.item())
+    keys_step = N_KEYS * len(CLASSES)
+    value = keys_step * ws / (ms_step / 1e3) / 1e9
+
+    # live roofline of each kernel kind over the timed region
+    kinds = {}
+    path_bytes = 0
+    work_merges = 0
+    merge_ms_work = 0.0
+    for c, k, st in prof:
+        path_bytes += st["bytes_moved"]
+        for name, (n_l, t_ms) in k.items():
+            a = kinds.setdefault(name, [0, 0.0])
+            a[0] += n_l
+            a[1] += t_ms
+        if st["input_class"] == 0:
+            done = st["passes_planned"] - st["passes_skipped"]
+            if done == st["passes_planned"]:
+                work_merges += k["merge"][0]
+                merge_ms_work += k["merge"][1]
+    dominant = max(kinds.items(), key=lambda kv: kv[1][1])[0]
+    merge_bytes_launch = 2 * N_KEYS * 4            # read + write of every key
+    achieved = merge_bytes_launch / (merge_ms_work / work_merges / 1e3) / 1e9 if work_merges else None
+    traffic = _ncu_traffic("merge_pass_2p24_int32")
+    roofline = {
+        "bound": "hbm", "kernel": "k_merge (global merge pass)", "achieved": achieved, "peak": peak,
+        "unit": "GB/s", "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
+        "algorithmic_bytes_per_launch": merge_bytes_launch, "traffic": traffic,
+        "avg_launch_ms": merge_ms_work / work_merges if work_merges else None,
+        "launches_timed": work_merges,
+        "dominant_by_time": dominant,
+        "path_bytes_per_step": path_bytes / args.steps,
+        "path_frac": (path_bytes / args.steps) / (ms_step / 1e3) / 1e9 / peak,
+        "lower_bound_frac": (2 * 4 * keys_step) / (ms_step / 1e3) / 1e9 / peak,
+        "kernel_ms_per_step": {k: v[1] / args.steps for k, v in kinds.items() if v[0]},
+    }
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    host = [torch.from_numpy(a).pin_memory() for a in arrays]
+    host_src = [h.clone().pin_memory() for h in host]
+    for c in range(len(CLASSES)):
+        sr.sort_keys_host(host[c].numpy())
+    torch.cuda.synchronize()
+    e2e_ms = 0.0
+    for step in range(args.steps):
+        for c in range(len(CLASSES)):
+            host[c].copy_(host_src[c])
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sr.sort_keys_host(host[c].numpy())
+            e1.record(stream)
+            torch.cuda.synchronize()
+            e2e_ms += e0.elapsed_time(e1)
+    e2e_ms /= args.steps
+    if ws > 1:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": keys_step * ws / (e2e_ms / 1e3) / 1e9, "unit": "Gkeys/s",
+           "h2d_bytes_per_step": 4 * keys_step, "d2h_bytes_per_step": 4 * keys_step,
+           "ms_per_step": e2e_ms}
+
+    sweep = None
+    if not args.no_sweep:
+        sweep = _sweep(sr, torch, dev, stream, peak)
+
+    cpu = None
+    if rank == 0:
+        v, dt, keys = _cpu_baseline(arrays)
+        cpu = {"value": v, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {CPU_SAMPLE} keys of each of the 4 arrays ({keys} keys, {dt:.2f} s)",
+               "cpu": _cpu_model(), "nproc": os.cpu_count()}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "i32", "data": "synthetic",
+            "config": dict(_config(), parallelism="replicas" if ws > 1 else "single-gpu",
+                           per_class_ms=dict(zip(CLASSES, per_class_ms)), wall_s_timed_region=wall),
+            "roofline": roofline,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        if sweep is not None:
+            line["sweep"] = sweep
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _sweep(sr, torch, dev, stream, peak, reps=3):
+    """Uniform int32 at 2^24..2^28 (prefixes of one 2^28 draw): Gkeys/s and the
+    fraction of the HBM roofline on the passes model and on the 1 read + 1
+    write lower bound."""
+    import sortrace_inputs as si
+    big = torch.from_numpy(si.uniform_i32(1 << 28, SEED)).to(dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    out = {}
+    for lg in range(24, 29):
+        n = 1 << lg
+        x = torch.empty(n, dtype=torch.int32, device=dev)
+        best = None
+        for r in range(reps + 1):
+            x.copy_(big[:n])
+            flush.fill_(r)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sr.sort_keys(x)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if r:
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+        st = sr.stats()
+        out[f"2^{lg}"] = {"ms": best, "gkeys_s": n / (best / 1e3) / 1e9,
+                          "passes_frac": st["bytes_moved"] / (best / 1e3) / 1e9 / peak,
+                          "lower_bound_frac": 8 * n / (best / 1e3) / 1e9 / peak,
+                          "bytes_moved": st["bytes_moved"]}
+        del x
+    return out
+
+
+def run_profile_case(args):
+    """A small, fixed case for ncu captures: one warm-up sort, then one sort."""
+    import numpy as np
+    import torch
+    import paper_1609_04471_gb300 as sr
+    import sortrace_inputs as si
+    torch.cuda.set_device(0)
+    n = 1 << args.profile_case
+    if args.profile_pairs:
+        k, v = si.pairs_u64_zipf(n, SEED)
+        src_k = torch.from_numpy(k.view(np.int64)).cuda()
+        src_v = torch.from_numpy(v.view(np.int32)).cuda()
+        for _ in range(2):
+            xk, xv = src_k.clone(), src_v.clone()
+            sr.sort_pairs(xk, xv, key_type=sr.KEY_U64)
+    else:
+        src = torch.from_numpy(si.uniform_i32(n, SEED)).cuda()
+        for _ in range(2):
+            x = src.clone()
+            sr.sort_keys(x)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": args.profile_case, "pairs": bool(args.profile_pairs), "ok": True}))
+
+
+def main():
+    args = _args()
+    if args.profile_case:
+        run_profile_case(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

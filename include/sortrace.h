@@ -189,6 +189,36 @@ sr_status sr_stream_status(sr_stream stream);
 const char *sr_status_string(sr_status s);
 
 /* ---------------------------------------------------------------------------
+ * Instrumentation.  Every kernel the library launches belongs to one of these
+ * kinds.  sr_launch_count() is the number of kernels the library has launched
+ * in this process.  Between sr_profile_begin() and sr_profile_end() the calls
+ * made by this host thread bracket each launch with CUDA events on the
+ * launch's own stream; sr_profile_end() waits for them and returns, per kind,
+ * the launch count and the summed device time (ms).  Profiling cannot be
+ * used inside a stream capture.
+ * ------------------------------------------------------------------------- */
+enum {
+    SR_KERNEL_DETECT = 0,     /* run-detection scan */
+    SR_KERNEL_REVERSE = 1,    /* whole-input reversal */
+    SR_KERNEL_BLOCK_SORT = 2, /* shared-memory tile sort */
+    SR_KERNEL_PARTITION = 3,  /* merge-path partition */
+    SR_KERNEL_MERGE = 4,      /* global merge pass */
+    SR_KERNEL_COPY = 5,       /* copy-back / gather */
+    SR_KERNEL_SEGMENTED = 6,  /* segmented / bucket sorts */
+    SR_KERNEL_MODEL = 7,      /* learned router: train, predict, histogram, scatter */
+    SR_KERNEL_KINDS = 8
+};
+
+typedef struct {
+    uint64_t launches;
+    double ms;
+} sr_kernel_time;
+
+uint64_t sr_launch_count(void);
+sr_status sr_profile_begin(void);
+sr_status sr_profile_end(sr_kernel_time *out, int count);
+
+/* ---------------------------------------------------------------------------
  * The learned partitioner's model, exposed for tests and reuse.
  *
  * Network (H = SR_MODEL_HIDDEN hidden units, one input x = normalised key):

@@ -75,7 +75,16 @@ SIGNATURES = {
     "sr_model_loss_grad": (_i32, [_vp, _vp, _sz, _vp, _vp, _vp, _vp]),
     "sr_model_train": (_i32, [_vp, _vp, _sz, _vp, _u32, ctypes.c_float, _vp, _vp]),
     "sr_model_buckets": (_i32, [_vp, _sz, _i32, _vp, _u64, _u64, _u32, _vp, _vp]),
+    "sr_launch_count": (_u64, []),
+    "sr_profile_begin": (_i32, []),
+    "sr_profile_end": (_i32, [_vp, _i32]),
 }
+
+KERNEL_KINDS = ("detect", "reverse", "block_sort", "partition", "merge", "copy", "segmented", "model")
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64), ("ms", ctypes.c_double)]
 
 
 def load(path: str | None = None):
@@ -221,6 +230,23 @@ def stats() -> dict:
 def stream_status(stream=None) -> int:
     """Waits for the stream and returns (and clears) the device status word."""
     return int(load().sr_stream_status(_stream(stream)))
+
+
+def launch_count() -> int:
+    """Number of kernels the library has launched in this process."""
+    return int(load().sr_launch_count())
+
+
+def profile_begin() -> None:
+    """Brackets every following launch of this thread with CUDA events."""
+    _check(load().sr_profile_begin(), "sr_profile_begin")
+
+
+def profile_end() -> dict:
+    """Waits for the bracketed launches; returns {kind: (launches, ms)}."""
+    arr = (KernelTime * len(KERNEL_KINDS))()
+    _check(load().sr_profile_end(arr, len(KERNEL_KINDS)), "sr_profile_end")
+    return {k: (int(arr[i].launches), float(arr[i].ms)) for i, k in enumerate(KERNEL_KINDS)}
 
 
 def model_loss_grad(x, t, theta, stream=None):

@@ -1,7 +1,9 @@
 // sr_runtime.cu -- per-device state, scratch pool, status word and statistics.
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "sr_runtime.cuh"
 
@@ -12,7 +14,46 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 DeviceState g_dev[kMaxDevices];
 thread_local CallRecord g_rec;
+std::atomic<unsigned long long> g_launches{0};
+
+struct Timed {
+    int kind;
+    cudaEvent_t a, b;
+};
+thread_local bool g_prof_on = false;
+thread_local std::vector<Timed> g_prof;
+thread_local cudaEvent_t g_prof_pending = nullptr;
 }  // namespace
+
+void launch_begin(int kind, cudaStream_t s) {
+    (void)kind;
+    if (!g_prof_on) return;
+    cudaEvent_t a = nullptr;
+    if (cudaEventCreate(&a) == cudaSuccess && cudaEventRecord(a, s) == cudaSuccess) {
+        g_prof_pending = a;
+    } else {
+        if (a) cudaEventDestroy(a);
+        g_prof_pending = nullptr;
+        cudaGetLastError();
+    }
+}
+
+sr_status launch_end(int kind, cudaStream_t s) {
+    sr_status st = launch_status();
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (g_prof_on && g_prof_pending) {
+        cudaEvent_t b = nullptr;
+        if (cudaEventCreate(&b) == cudaSuccess && cudaEventRecord(b, s) == cudaSuccess) {
+            g_prof.push_back(Timed{kind, g_prof_pending, b});
+        } else {
+            cudaEventDestroy(g_prof_pending);
+            if (b) cudaEventDestroy(b);
+            cudaGetLastError();
+        }
+        g_prof_pending = nullptr;
+    }
+    return st;
+}
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -105,6 +146,37 @@ extern "C" const char *sr_status_string(sr_status s) {
     case SR_ERR_BAD_SEGMENTS: return "SR_ERR_BAD_SEGMENTS";
     default: return "SR_ERR_UNKNOWN";
     }
+}
+
+extern "C" uint64_t sr_launch_count(void) { return g_launches.load(); }
+
+extern "C" sr_status sr_profile_begin(void) {
+    for (auto &t : g_prof) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
+    g_prof.clear();
+    g_prof_on = true;
+    return SR_OK;
+}
+
+extern "C" sr_status sr_profile_end(sr_kernel_time *out, int count) {
+    g_prof_on = false;
+    if (out && count > 0) {
+        for (int k = 0; k < count; ++k) { out[k].launches = 0; out[k].ms = 0.0; }
+    }
+    sr_status st = SR_OK;
+    for (auto &t : g_prof) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(t.b) != cudaSuccess || cudaEventElapsedTime(&ms, t.a, t.b) != cudaSuccess) {
+            cudaGetLastError();
+            st = SR_ERR_CUDA;
+        } else if (out && t.kind >= 0 && t.kind < count) {
+            out[t.kind].launches += 1;
+            out[t.kind].ms += ms;
+        }
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    g_prof.clear();
+    return st;
 }
 
 extern "C" sr_status sr_stream_status(sr_stream stream) {

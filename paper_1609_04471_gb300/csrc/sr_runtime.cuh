@@ -44,6 +44,11 @@ struct CallRecord {
 };
 CallRecord &call_record();
 
+// Kernel instrumentation: every launch site calls launch_begin / launch_end
+// around its <<<>>> (see SR_LAUNCH).
+void launch_begin(int kind, cudaStream_t s);
+sr_status launch_end(int kind, cudaStream_t s);
+
 size_t align_up(size_t x, size_t a);
 int ceil_log2(unsigned long long x);
 size_t key_bytes_of(sr_key_type kt);
@@ -56,6 +61,17 @@ bool valid_key_type(int kt);
         sr_status _st = (expr);                    \
         if (_st != SR_OK) return _st;              \
     } while (0)
+
+// Launches `kernel<<<grid, block, smem, stream>>>(args...)`, counts it, times
+// it when profiling is on, and breaks out of the enclosing do/while with the
+// status in `st` if the launch failed.
+#define SR_LAUNCH(kind, kernel, grid, block, smem, stream, ...)          \
+    {                                                                     \
+        ::sr::launch_begin((kind), (stream));                             \
+        kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);       \
+        st = ::sr::launch_end((kind), (stream));                          \
+        if (st != SR_OK) break;                                           \
+    }
 
 #define SR_LAUNCHED()                              \
     do {                                           \

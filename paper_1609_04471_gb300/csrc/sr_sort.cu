@@ -345,32 +345,28 @@ static sr_status sort_impl(void *d_keys, uint32_t *d_vals, size_t n, cudaStream_
         if (cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s) != cudaSuccess) { st = launch_status(); break; }
         const size_t det_smem = (size_t)(TS + 1) * sizeof(U);
         if ((st = allow_smem(k_detect<KT, SNT, IPT>, det_smem)) != SR_OK) break;
-        k_detect<KT, SNT, IPT><<<(unsigned)tiles, SNT, det_smem, s>>>(uk, N, ctrl);
-        if ((st = launch_status()) != SR_OK) break;
-        k_reverse<KT, VALS><<<grid_for(N / 2, 256, 152 * 16), 256, 0, s>>>(uk, uv, N, ctrl);
-        if ((st = launch_status()) != SR_OK) break;
+        SR_LAUNCH(SR_KERNEL_DETECT, (k_detect<KT, SNT, IPT>), (unsigned)tiles, SNT, det_smem, s,
+                  uk, N, ctrl);
+        SR_LAUNCH(SR_KERNEL_REVERSE, (k_reverse<KT, VALS>), grid_for(N / 2, 256, 152 * 16), 256, 0, s,
+                  uk, uv, N, ctrl);
         const size_t bs_smem = (size_t)TS * (sizeof(U) + (VALS ? 4 : 0));
         if ((st = allow_smem(k_block_sort<KT, SNT, IPT, VALS>, bs_smem)) != SR_OK) break;
-        k_block_sort<KT, SNT, IPT, VALS><<<(unsigned)tiles, SNT, bs_smem, s>>>(
-            uk, uv, cur0 ? sk : uk, cur0 ? sv : uv, N, ctrl);
-        if ((st = launch_status()) != SR_OK) break;
+        SR_LAUNCH(SR_KERNEL_BLOCK_SORT, (k_block_sort<KT, SNT, IPT, VALS>), (unsigned)tiles, SNT,
+                  bs_smem, s, uk, uv, cur0 ? sk : uk, cur0 ? sv : uv, N, ctrl);
         const size_t m_smem = (size_t)NV * (sizeof(U) + (VALS ? 4 : 0));
         if ((st = allow_smem(k_merge<KT, NT, IPT, VALS>, m_smem)) != SR_OK) break;
         for (int p = 0; p < P; ++p) {
             const long long w = (long long)TS << p;
             const long long nb = mtiles + 1;
-            k_partition<KT><<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(uk, sk, N, w, NV, nb,
-                                                                         splits, ctrl, cur0, p);
-            if ((st = launch_status()) != SR_OK) break;
-            k_merge<KT, NT, IPT, VALS><<<(unsigned)mtiles, NT, m_smem, s>>>(uk, uv, sk, sv, N, w,
-                                                                           splits, ctrl, cur0, p);
-            if ((st = launch_status()) != SR_OK) break;
+            SR_LAUNCH(SR_KERNEL_PARTITION, (k_partition<KT>), (unsigned)((nb + 255) / 256), 256, 0, s,
+                      uk, sk, N, w, NV, nb, splits, ctrl, cur0, p);
+            SR_LAUNCH(SR_KERNEL_MERGE, (k_merge<KT, NT, IPT, VALS>), (unsigned)mtiles, NT, m_smem, s,
+                      uk, uv, sk, sv, N, w, splits, ctrl, cur0, p);
         }
         if (st != SR_OK) break;
         if (P > 0) {
-            k_copy_back<KT, VALS><<<grid_for(N, 256, 152 * 16), 256, 0, s>>>(uk, uv, sk, sv, N, ctrl,
-                                                                             cur0, P);
-            if ((st = launch_status()) != SR_OK) break;
+            SR_LAUNCH(SR_KERNEL_COPY, (k_copy_back<KT, VALS>), grid_for(N, 256, 152 * 16), 256, 0, s,
+                      uk, uv, sk, sv, N, ctrl, cur0, P);
         }
         if (cudaMemcpyAsync(ds->last_ctrl, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToDevice, s) !=
             cudaSuccess) {
@@ -419,8 +415,8 @@ static sr_status detect_impl(const void *d_keys, size_t n, sr_run_info *out, cud
         if (cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s) != cudaSuccess) { st = launch_status(); break; }
         const size_t smem = (size_t)(TS + 1) * sizeof(typename K::U);
         if ((st = allow_smem(k_detect<KT, SNT, IPT>, smem)) != SR_OK) break;
-        k_detect<KT, SNT, IPT><<<(unsigned)tiles, SNT, smem, s>>>((const T *)d_keys, N, ctrl);
-        if ((st = launch_status()) != SR_OK) break;
+        SR_LAUNCH(SR_KERNEL_DETECT, (k_detect<KT, SNT, IPT>), (unsigned)tiles, SNT, smem, s,
+                  (const T *)d_keys, N, ctrl);
         if (cudaMemcpyAsync(&h, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) {
             st = launch_status();
