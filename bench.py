@@ -78,7 +78,7 @@ def _ncu_traffic(kernel_tag: str):
     if not m or not h:
         return None
     src = b""
-    for fn in ("sr_sort.cu", "sr_device.cuh"):
+    for fn in ("sr_kernels.cuh", "sr_device.cuh"):
         with open(os.path.join(ROOT, "paper_1609_04471_gb300", "csrc", fn), "rb") as f:
             src += f.read()
     if hashlib.sha256(src).hexdigest()[:16] != h.group(1)[:16]:

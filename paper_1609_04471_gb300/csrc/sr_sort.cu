@@ -28,251 +28,10 @@
 #include <cstring>
 
 #include "sr_device.cuh"
+#include "sr_kernels.cuh"
 #include "sr_runtime.cuh"
 
 namespace sr {
-
-// ------------------------------------------------------------- kernels
-
-template <int KT, int NT, int IPT>
-__global__ void __launch_bounds__(NT) k_detect(const typename Key<KT>::T *__restrict__ keys,
-                                               long long n, Ctrl *__restrict__ c) {
-    typedef Key<KT> K;
-    typedef typename K::U U;
-    constexpr int NV = NT * IPT;
-    extern __shared__ __align__(16) unsigned char smem[];
-    U *s = reinterpret_cast<U *>(smem);
-    __shared__ unsigned int red[4];
-    const int t = threadIdx.x;
-    const long long base = (long long)blockIdx.x * NV;
-    const int cnt = (int)(n - base < (long long)NV + 1 ? n - base : (long long)NV + 1);   // one more for the pair across
-    if (t < 4) red[t] = 0;
-    for (int i = t; i < cnt; i += NT) s[i] = K::ord(keys[base + i]);
-    __syncthreads();
-    unsigned int d = 0, nd = 0, din = 0, ndin = 0;
-#pragma unroll
-    for (int i = 0; i < IPT; ++i) {
-        const int j = t * IPT + i;
-        if (j + 1 < cnt) {
-            const bool de = s[j] > s[j + 1];
-            d += de;
-            nd += !de;
-            if (j + 1 < NV) { din |= de; ndin |= !de; }
-        }
-    }
-    d = __reduce_add_sync(0xffffffffu, d);
-    nd = __reduce_add_sync(0xffffffffu, nd);
-    din = __reduce_or_sync(0xffffffffu, din);
-    ndin = __reduce_or_sync(0xffffffffu, ndin);
-    if ((t & 31) == 0) {
-        atomicAdd(&red[0], d);
-        atomicAdd(&red[1], nd);
-        atomicOr(&red[2], din);
-        atomicOr(&red[3], ndin);
-    }
-    __syncthreads();
-    if (t == 0) {
-        if (red[0]) atomicAdd(&c->descents, (unsigned long long)red[0]);
-        if (red[1]) atomicAdd(&c->nondescents, (unsigned long long)red[1]);
-        if (!red[2]) atomicAdd(&c->tiles_ascending, 1ull);
-        if (!red[3]) atomicAdd(&c->tiles_descending, 1ull);
-    }
-}
-
-template <int KT, bool VALS>
-__global__ void k_reverse(typename Key<KT>::T *__restrict__ k, uint32_t *__restrict__ v,
-                          long long n, const Ctrl *__restrict__ c) {
-    if (call_mode(c, n) != MODE_REVERSE) return;
-    const long long half = n / 2;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < half; i += stride) {
-        const long long j = n - 1 - i;
-        const typename Key<KT>::T a = k[i], b = k[j];
-        k[i] = b;
-        k[j] = a;
-        if (VALS) {
-            const uint32_t x = v[i], y = v[j];
-            v[i] = y;
-            v[j] = x;
-        }
-    }
-}
-
-template <int KT, int NT, int IPT, bool VALS>
-__global__ void __launch_bounds__(NT)
-k_block_sort(const typename Key<KT>::T *in_k, const uint32_t *in_v, typename Key<KT>::T *out_k,
-             uint32_t *out_v, long long n, const Ctrl *__restrict__ c) {
-    typedef Key<KT> K;
-    typedef typename K::U U;
-    constexpr int NV = NT * IPT;
-    if (c && call_mode(c, n) != MODE_SORT) return;
-    extern __shared__ __align__(16) unsigned char smem[];
-    U *s = reinterpret_cast<U *>(smem);
-    uint32_t *sv = reinterpret_cast<uint32_t *>(s + NV);
-    const int t = threadIdx.x;
-    const long long base = (long long)blockIdx.x * NV;
-    const int cnt = (int)(n - base < (long long)NV ? n - base : (long long)NV);
-#pragma unroll
-    for (int i = 0; i < IPT; ++i) {
-        const int idx = i * NT + t;
-        s[idx] = idx < cnt ? K::ord(in_k[base + idx]) : umax_of<U>();
-        if (VALS) sv[idx] = idx < cnt ? in_v[base + idx] : 0u;
-    }
-    __syncthreads();
-    // presortedness of the tile
-    int desc = 0, nondesc = 0;
-#pragma unroll
-    for (int i = 0; i < IPT; ++i) {
-        const int j = t * IPT + i;
-        if (j + 1 < cnt) {
-            desc |= s[j] > s[j + 1];
-            nondesc |= !(s[j] > s[j + 1]);
-        }
-    }
-    const int any_desc = __syncthreads_or(desc);
-    const int any_nondesc = __syncthreads_or(nondesc);
-    if (!any_desc) {                       // already ascending
-        if (out_k != in_k) {
-            for (int idx = t; idx < cnt; idx += NT) {
-                out_k[base + idx] = K::unord(s[idx]);
-                if (VALS) out_v[base + idx] = sv[idx];
-            }
-        }
-        return;
-    }
-    if (!any_nondesc) {                    // strictly descending: reverse
-        for (int idx = t; idx < cnt; idx += NT) {
-            out_k[base + idx] = K::unord(s[cnt - 1 - idx]);
-            if (VALS) out_v[base + idx] = sv[cnt - 1 - idx];
-        }
-        return;
-    }
-    U k[IPT];
-    uint32_t v[IPT];
-#pragma unroll
-    for (int i = 0; i < IPT; ++i) {
-        k[i] = s[t * IPT + i];
-        v[i] = VALS ? sv[t * IPT + i] : 0u;
-    }
-    __syncthreads();
-    block_sort<U, NT, IPT, VALS>(k, v, s, sv);
-#pragma unroll
-    for (int i = 0; i < IPT; ++i) {
-        s[t * IPT + i] = k[i];
-        if (VALS) sv[t * IPT + i] = v[i];
-    }
-    __syncthreads();
-    for (int idx = t; idx < cnt; idx += NT) {
-        out_k[base + idx] = K::unord(s[idx]);
-        if (VALS) out_v[base + idx] = sv[idx];
-    }
-}
-
-// One thread per merge-tile boundary b (0..tiles): splits[b] = the A index
-// where output position b*nv falls, for the pair of runs that contains it.
-template <int KT>
-__global__ void k_partition(const typename Key<KT>::T *__restrict__ uk,
-                            const typename Key<KT>::T *__restrict__ sk, long long n, long long w,
-                            int nv, long long nbound, long long *__restrict__ splits,
-                            Ctrl *__restrict__ c, int cur0, int p) {
-    typedef Key<KT> K;
-    typedef typename K::U U;
-    const long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nbound) return;
-    if (call_mode(c, n) != MODE_SORT) return;
-    const typename K::T *src = buffer_before_pass(c, cur0, p) ? sk : uk;
-    const long long out = min(b * (long long)nv, n);
-    const long long pb = (out / (2 * w)) * (2 * w);
-    const long long a_beg = pb, a_end = min(pb + w, n);
-    const long long b_beg = a_end, b_end = min(pb + 2 * w, n);
-    const long long diag = out - pb, na = a_end - a_beg, nb = b_end - b_beg;
-    if (diag == 0 && nb > 0 && K::ord(src[a_end - 1]) > K::ord(src[b_beg]))
-        atomicAdd(&c->unordered[p], 1);
-    long long lo = max(0ll, diag - nb), hi = min(diag, na);
-    while (lo < hi) {
-        const long long mid = (lo + hi) >> 1;
-        const U x = K::ord(src[a_beg + mid]);
-        const U y = K::ord(src[b_beg + diag - 1 - mid]);
-        if (!(y < x)) lo = mid + 1;
-        else hi = mid;
-    }
-    splits[b] = a_beg + lo;
-}
-
-template <int KT, int NT, int IPT, bool VALS>
-__global__ void __launch_bounds__(NT)
-k_merge(typename Key<KT>::T *uk, uint32_t *uv, typename Key<KT>::T *sk, uint32_t *svb, long long n,
-        long long w, const long long *__restrict__ splits, const Ctrl *__restrict__ c, int cur0,
-        int p) {
-    typedef Key<KT> K;
-    typedef typename K::U U;
-    typedef typename K::T T;
-    constexpr int NV = NT * IPT;
-    if (call_mode(c, n) != MODE_SORT || c->unordered[p] == 0) return;
-    __shared__ int s_cur;
-    if (threadIdx.x == 0) s_cur = buffer_before_pass(c, cur0, p);
-    extern __shared__ __align__(16) unsigned char smem[];
-    U *s = reinterpret_cast<U *>(smem);
-    uint32_t *sv = reinterpret_cast<uint32_t *>(s + NV);
-    __syncthreads();
-    const int cur = s_cur;
-    const T *src_k = cur ? sk : uk;
-    T *dst_k = cur ? uk : sk;
-    const uint32_t *src_v = cur ? svb : uv;
-    uint32_t *dst_v = cur ? uv : svb;
-    const int t = threadIdx.x;
-    const long long out0 = (long long)blockIdx.x * NV;
-    const long long out1 = min(out0 + NV, n);
-    const int cnt = (int)(out1 - out0);
-    const long long pb = (out0 / (2 * w)) * (2 * w);
-    const long long a_beg = pb, a_end = min(pb + w, n);
-    const long long b_beg = a_end, b_end = min(pb + 2 * w, n);
-    const long long a0 = splits[blockIdx.x];
-    const long long a1 = (out1 == b_end) ? a_end : splits[blockIdx.x + 1];
-    const long long b0 = b_beg + (out0 - pb) - (a0 - a_beg);
-    const int acnt = (int)(a1 - a0);
-    const int bcnt = cnt - acnt;
-    for (int i = t; i < cnt; i += NT) {
-        const long long g = i < acnt ? a0 + i : b0 + (i - acnt);
-        s[i] = K::ord(src_k[g]);
-        if (VALS) sv[i] = src_v[g];
-    }
-    __syncthreads();
-    const int diag = min(t * IPT, cnt);
-    const int sp = merge_path(s, acnt, s + acnt, bcnt, diag);
-    U k[IPT];
-    int ix[IPT];
-    serial_merge<U, IPT>(s, sp, acnt, acnt + diag - sp, cnt, k, ix);
-    uint32_t v[IPT];
-    if (VALS) {
-#pragma unroll
-        for (int i = 0; i < IPT; ++i) v[i] = (diag + i < cnt) ? sv[ix[i]] : 0u;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < IPT; ++i) {
-        s[t * IPT + i] = k[i];
-        if (VALS) sv[t * IPT + i] = v[i];
-    }
-    __syncthreads();
-    for (int i = t; i < cnt; i += NT) {
-        dst_k[out0 + i] = K::unord(s[i]);
-        if (VALS) dst_v[out0 + i] = sv[i];
-    }
-}
-
-template <int KT, bool VALS>
-__global__ void k_copy_back(typename Key<KT>::T *uk, uint32_t *uv, const typename Key<KT>::T *sk,
-                            const uint32_t *svb, long long n, const Ctrl *__restrict__ c,
-                            int cur0, int passes) {
-    if (call_mode(c, n) != MODE_SORT) return;
-    if (buffer_before_pass(c, cur0, passes) == 0) return;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        uk[i] = sk[i];
-        if (VALS) uv[i] = svb[i];
-    }
-}
 
 // --------------------------------------------------------------- host
 
