@@ -109,6 +109,26 @@ sr_status sr_sort_segmented(void *d_keys, const int64_t *d_offsets, size_t num_s
  */
 sr_status sr_sort_keys_host(void *h_keys, size_t n, sr_key_type kt, sr_stream stream);
 
+/*
+ * sr_sort_keys_noalloc -- sr_sort_keys for callers that must not allocate device
+ * memory while they sort (a service that reserves all of its memory up front
+ * so it can never hit out-of-memory mid-request, a framework that forbids
+ * allocations behind its back, a latency-critical path where an allocation
+ * could stall).  It allocates nothing: its scratch is one fixed device array
+ * inside this library, present on every GPU that loads the library until the
+ * process exits.  The paper has no counterpart; it is an interface variant.
+ *   n        at most SR_NOALLOC_MAX_KEYS keys (any key type); a larger n returns
+ *            SR_ERR_INVALID_ARG and leaves the keys untouched.
+ * Same result as sr_sort_keys.  All calls on a device share the one scratch
+ * array, which keeps the previous call's contents (each call clears what it
+ * needs zeroed): calls whose device work overlaps in time race and give wrong
+ * results -- keep them ordered on one stream.  The first call on each device
+ * looks up the array's device address and should come before any stream
+ * capture.  sr_get_stats does not report on these calls.
+ */
+#define SR_NOALLOC_MAX_KEYS (1u << 20)
+sr_status sr_sort_keys_noalloc(void *d_keys, size_t n, sr_key_type kt, sr_stream stream);
+
 /* Options of the learned-partition sort; zero fields take the defaults. */
 typedef struct {
     uint32_t num_buckets;    /* power of two in [2^4, 2^20]; default 2^16 */

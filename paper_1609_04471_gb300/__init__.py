@@ -67,6 +67,7 @@ SIGNATURES = {
     "sr_sort_pairs": (_i32, [_vp, _vp, _sz, _i32, _vp]),
     "sr_sort_segmented": (_i32, [_vp, _vp, _sz, _i32, _vp]),
     "sr_sort_keys_host": (_i32, [_vp, _sz, _i32, _vp]),
+    "sr_sort_keys_noalloc": (_i32, [_vp, _sz, _i32, _vp]),
     "sr_sort_keys_learned": (_i32, [_vp, _sz, _i32, _vp, _vp]),
     "sr_detect_runs": (_i32, [_vp, _sz, _i32, _vp, _vp]),
     "sr_get_stats": (_i32, [_vp]),
@@ -144,6 +145,19 @@ def sort_keys(x, key_type: int | None = None, stream=None):
     _cuda_contig(x, "keys")
     kt = key_type_of(x) if key_type is None else key_type
     _check(load().sr_sort_keys(x.data_ptr(), x.numel(), kt, _stream(stream)), "sr_sort_keys")
+    return x
+
+
+NOALLOC_MAX_KEYS = 1 << 20
+
+
+def sort_keys_noalloc(x, key_type: int | None = None, stream=None):
+    """sort_keys without any device allocation (at most NOALLOC_MAX_KEYS keys;
+    calls must not overlap on the device)."""
+    _cuda_contig(x, "keys")
+    kt = key_type_of(x) if key_type is None else key_type
+    _check(load().sr_sort_keys_noalloc(x.data_ptr(), x.numel(), kt, _stream(stream)),
+           "sr_sort_keys_noalloc")
     return x
 
 
