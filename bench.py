@@ -256,16 +256,19 @@ def run_ours(args):
     clocks = Clocks(torch.cuda.current_device())
     clocks.start()
     launches0 = sr.launch_count()
-    prof = []
     events = []
     wall0 = time.perf_counter()
-    for step in range(args.steps):
-        events.append(one_step(step, True, prof))
+    for step in range(args.steps):                   # timed region: the headline number
+        events.append(one_step(step, True, None))
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     launches = sr.launch_count() - launches0
     if ws > 1:
         torch.distributed.barrier()
+    torch.cuda.synchronize()
+    prof = []
+    for step in range(args.steps):                   # same steps again, every launch bracketed by events
+        one_step(step, True, prof)
     torch.cuda.synchronize()
     clk = clocks.stop()
 
@@ -313,6 +316,7 @@ def run_ours(args):
         "path_frac": (path_bytes / args.steps) / (ms_step / 1e3) / 1e9 / peak,
         "lower_bound_frac": (2 * 4 * keys_step) / (ms_step / 1e3) / 1e9 / peak,
         "kernel_ms_per_step": {k: v[1] / args.steps for k, v in kinds.items() if v[0]},
+        "timing": "per-launch events in a second pass over the same steps; value comes from the unbracketed pass",
     }
 
     # end to end through the host-buffer entry point (pinned host memory)

@@ -143,17 +143,21 @@ k_block_sort(const typename Key<KT>::T *in_k, const uint32_t *in_v, typename Key
     }
 }
 
-// One thread per merge-tile boundary b (0..tiles): splits[b] = the A index
-// where output position b*nv falls, for the pair of runs that contains it.
+// One warp per merge-tile boundary b (0..tiles): splits[b] = the A index where
+// output position b*nv falls, for the pair of runs that contains it.  The warp
+// searches the merge path 32 ways at a time: each lane tests one candidate
+// and a ballot keeps the 1/32 of the range that holds the answer, so a search
+// over 2^k candidates costs about k/5 dependent loads instead of k.
 template <int KT>
-__global__ void k_partition(const typename Key<KT>::T *__restrict__ uk,
-                            const typename Key<KT>::T *__restrict__ sk, long long n, long long w,
-                            int nv, long long nbound, long long *__restrict__ splits,
-                            Ctrl *__restrict__ c, int cur0, int p) {
+__global__ void __launch_bounds__(256)
+k_partition(const typename Key<KT>::T *__restrict__ uk, const typename Key<KT>::T *__restrict__ sk,
+            long long n, long long w, int nv, long long nbound, long long *__restrict__ splits,
+            Ctrl *__restrict__ c, int cur0, int p) {
     typedef Key<KT> K;
     typedef typename K::U U;
-    const long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nbound) return;
+    const int lane = threadIdx.x & 31;
+    const long long b = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (b >= nbound) return;                       // uniform across the warp
     if (call_mode(c, n) != MODE_SORT) return;
     const typename K::T *src = buffer_before_pass(c, cur0, p) ? sk : uk;
     const long long out = min(b * (long long)nv, n);
@@ -161,20 +165,41 @@ __global__ void k_partition(const typename Key<KT>::T *__restrict__ uk,
     const long long a_beg = pb, a_end = min(pb + w, n);
     const long long b_beg = a_end, b_end = min(pb + 2 * w, n);
     const long long diag = out - pb, na = a_end - a_beg, nb = b_end - b_beg;
-    if (diag == 0 && nb > 0 && K::ord(src[a_end - 1]) > K::ord(src[b_beg]))
+    if (lane == 0 && diag == 0 && nb > 0 && K::ord(src[a_end - 1]) > K::ord(src[b_beg]))
         atomicAdd(&c->unordered[p], 1);
+    // answer: the first m in [lo, hi) with A[m] > B[diag-1-m], else hi
     long long lo = max(0ll, diag - nb), hi = min(diag, na);
-    while (lo < hi) {
-        const long long mid = (lo + hi) >> 1;
-        const U x = K::ord(src[a_beg + mid]);
-        const U y = K::ord(src[b_beg + diag - 1 - mid]);
-        if (!(y < x)) lo = mid + 1;
-        else hi = mid;
+    while (hi > lo) {
+        const long long step = (hi - lo + 31) >> 5;
+        const long long m = lo + lane * step;
+        bool before = false;                       // answer > m
+        if (m < hi) {
+            const U x = K::ord(src[a_beg + m]);
+            const U y = K::ord(src[b_beg + diag - 1 - m]);
+            before = !(y < x);
+        }
+        const int cnt = __popc(__ballot_sync(0xffffffffu, before));
+        if (cnt == 0) {
+            hi = lo;
+        } else {
+            const long long nlo = lo + (long long)(cnt - 1) * step + 1;
+            hi = min(hi, lo + (long long)cnt * step);
+            lo = nlo;
+        }
     }
-    splits[b] = a_beg + lo;
+    if (lane == 0) splits[b] = a_beg + lo;
 }
 
-template <int KT, int NT, int IPT, bool VALS>
+// One CTA per output tile of NT*IPT keys of merge pass p.  The tile's A and B
+// ranges come from the split table; both are staged in shared memory, merged
+// by merge path (IPT outputs per thread) and written back.
+//
+// VEC (every buffer 16-byte aligned): the ranges are staged as windows of
+// 4-key groups starting on a group boundary, so every group moves with 128-bit
+// loads and shared-memory stores, all issued before the first is used; the
+// output tile (which starts on a group boundary) leaves with 128-bit stores.
+// Keys before a range's start inside its first group are staged and ignored.
+template <int KT, int NT, int IPT, bool VALS, bool VEC>
 __global__ void __launch_bounds__(NT)
 k_merge(typename Key<KT>::T *uk, uint32_t *uv, typename Key<KT>::T *sk, uint32_t *svb, long long n,
         long long w, const long long *__restrict__ splits, const Ctrl *__restrict__ c, int cur0,
@@ -183,12 +208,13 @@ k_merge(typename Key<KT>::T *uk, uint32_t *uv, typename Key<KT>::T *sk, uint32_t
     typedef typename K::U U;
     typedef typename K::T T;
     constexpr int NV = NT * IPT;
+    constexpr int SV = NV + 16;                    // staged keys, with room for window slack
     if (call_mode(c, n) != MODE_SORT || c->unordered[p] == 0) return;
     __shared__ int s_cur;
     if (threadIdx.x == 0) s_cur = buffer_before_pass(c, cur0, p);
     extern __shared__ __align__(16) unsigned char smem[];
     U *s = reinterpret_cast<U *>(smem);
-    uint32_t *sv = reinterpret_cast<uint32_t *>(s + NV);
+    uint32_t *sv = reinterpret_cast<uint32_t *>(s + SV);
     __syncthreads();
     const int cur = s_cur;
     const T *src_k = cur ? sk : uk;
@@ -207,17 +233,72 @@ k_merge(typename Key<KT>::T *uk, uint32_t *uv, typename Key<KT>::T *sk, uint32_t
     const long long b0 = b_beg + (out0 - pb) - (a0 - a_beg);
     const int acnt = (int)(a1 - a0);
     const int bcnt = cnt - acnt;
-    for (int i = t; i < cnt; i += NT) {
-        const long long g = i < acnt ? a0 + i : b0 + (i - acnt);
-        s[i] = K::ord(src_k[g]);
-        if (VALS) sv[i] = src_v[g];
+    int sa, sb;                                    // staged positions of A[a0] and B[b0]
+    if (VEC) {
+        const long long a0g = a0 & ~3ll, b0g = b0 & ~3ll;
+        const int nag = (int)((((a1 + 3) & ~3ll) - a0g) >> 2);
+        const int nbg = (int)((((b0 + bcnt + 3) & ~3ll) - b0g) >> 2);
+        sa = (int)(a0 - a0g);
+        const int offb = 4 * nag;
+        sb = offb + (int)(b0 - b0g);
+        constexpr int KMAX = (SV / 4 + NT - 1) / NT;
+        U r[KMAX][4];
+        uint4 rv[VALS ? KMAX : 1];
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) {
+            const int g = t + k * NT;
+            if (g < nag + nbg) {
+                const long long gb = g < nag ? a0g + 4ll * g : b0g + 4ll * (g - nag);
+                if (gb + 4 <= n) {
+                    if (sizeof(T) == 4) {
+                        const uint4 q = *reinterpret_cast<const uint4 *>(src_k + gb);
+                        r[k][0] = (U)q.x; r[k][1] = (U)q.y; r[k][2] = (U)q.z; r[k][3] = (U)q.w;
+                    } else {
+                        const uint4 q0 = *reinterpret_cast<const uint4 *>(src_k + gb);
+                        const uint4 q1 = *reinterpret_cast<const uint4 *>(src_k + gb + 2);
+                        r[k][0] = (U)(((unsigned long long)q0.y << 32) | q0.x);
+                        r[k][1] = (U)(((unsigned long long)q0.w << 32) | q0.z);
+                        r[k][2] = (U)(((unsigned long long)q1.y << 32) | q1.x);
+                        r[k][3] = (U)(((unsigned long long)q1.w << 32) | q1.z);
+                    }
+                    if (VALS) rv[k] = *reinterpret_cast<const uint4 *>(src_v + gb);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) r[k][e] = (gb + e < n) ? (U)src_k[gb + e] : U(0);
+                    if (VALS) {
+                        rv[k].x = (gb + 0 < n) ? src_v[gb + 0] : 0u;
+                        rv[k].y = (gb + 1 < n) ? src_v[gb + 1] : 0u;
+                        rv[k].z = (gb + 2 < n) ? src_v[gb + 2] : 0u;
+                        rv[k].w = (gb + 3 < n) ? src_v[gb + 3] : 0u;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) {
+            const int g = t + k * NT;
+            if (g < nag + nbg) {
+                const int o = g < nag ? 4 * g : offb + 4 * (g - nag);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) s[o + e] = K::ord((T)r[k][e]);
+                if (VALS) *reinterpret_cast<uint4 *>(sv + o) = rv[k];
+            }
+        }
+    } else {
+        sa = 0;
+        sb = acnt;
+        for (int i = t; i < cnt; i += NT) {
+            const long long g = i < acnt ? a0 + i : b0 + (i - acnt);
+            s[i] = K::ord(src_k[g]);
+            if (VALS) sv[i] = src_v[g];
+        }
     }
     __syncthreads();
     const int diag = min(t * IPT, cnt);
-    const int sp = merge_path(s, acnt, s + acnt, bcnt, diag);
+    const int sp = merge_path(s + sa, acnt, s + sb, bcnt, diag);
     U k[IPT];
     int ix[IPT];
-    serial_merge<U, IPT>(s, sp, acnt, acnt + diag - sp, cnt, k, ix);
+    serial_merge<U, IPT>(s, sa + sp, sa + acnt, sb + diag - sp, sb + bcnt, k, ix);
     uint32_t v[IPT];
     if (VALS) {
 #pragma unroll
@@ -230,9 +311,37 @@ k_merge(typename Key<KT>::T *uk, uint32_t *uv, typename Key<KT>::T *sk, uint32_t
         if (VALS) sv[t * IPT + i] = v[i];
     }
     __syncthreads();
-    for (int i = t; i < cnt; i += NT) {
-        dst_k[out0 + i] = K::unord(s[i]);
-        if (VALS) dst_v[out0 + i] = sv[i];
+    if (VEC) {
+        const int full = cnt >> 2;
+        for (int g = t; g < full; g += NT) {
+            if (sizeof(T) == 4) {
+                uint4 q;
+                q.x = (uint32_t)K::unord(s[4 * g + 0]);
+                q.y = (uint32_t)K::unord(s[4 * g + 1]);
+                q.z = (uint32_t)K::unord(s[4 * g + 2]);
+                q.w = (uint32_t)K::unord(s[4 * g + 3]);
+                *reinterpret_cast<uint4 *>(dst_k + out0 + 4 * g) = q;
+            } else {
+                const unsigned long long e0 = (unsigned long long)K::unord(s[4 * g + 0]);
+                const unsigned long long e1 = (unsigned long long)K::unord(s[4 * g + 1]);
+                const unsigned long long e2 = (unsigned long long)K::unord(s[4 * g + 2]);
+                const unsigned long long e3 = (unsigned long long)K::unord(s[4 * g + 3]);
+                *reinterpret_cast<uint4 *>(dst_k + out0 + 4 * g) =
+                    make_uint4((uint32_t)e0, (uint32_t)(e0 >> 32), (uint32_t)e1, (uint32_t)(e1 >> 32));
+                *reinterpret_cast<uint4 *>(dst_k + out0 + 4 * g + 2) =
+                    make_uint4((uint32_t)e2, (uint32_t)(e2 >> 32), (uint32_t)e3, (uint32_t)(e3 >> 32));
+            }
+            if (VALS) *reinterpret_cast<uint4 *>(dst_v + out0 + 4 * g) = *reinterpret_cast<const uint4 *>(sv + 4 * g);
+        }
+        for (int i = 4 * full + t; i < cnt; i += NT) {
+            dst_k[out0 + i] = K::unord(s[i]);
+            if (VALS) dst_v[out0 + i] = sv[i];
+        }
+    } else {
+        for (int i = t; i < cnt; i += NT) {
+            dst_k[out0 + i] = K::unord(s[i]);
+            if (VALS) dst_v[out0 + i] = sv[i];
+        }
     }
 }
 

@@ -87,6 +87,7 @@ sr_status noalloc_impl(void *d_keys, size_t n, cudaStream_t s, unsigned char *ba
     // every kernel below fits the default 48 KB of dynamic shared memory
     static_assert((TS + 1) * sizeof(U) <= 48 * 1024, "detect tile too large");
     static_assert(TS * sizeof(U) <= 48 * 1024, "block-sort tile too large");
+    static_assert((NV + 16) * sizeof(U) <= 48 * 1024, "merge tile too large");
     if (n < 2) return SR_OK;
     const long long N = (long long)n;
     const long long tiles = (N + TS - 1) / TS;
@@ -98,6 +99,7 @@ sr_status noalloc_impl(void *d_keys, size_t n, cudaStream_t s, unsigned char *ba
     T *sk = (T *)(base + kCtrlBytes + kSplitBytes);
     T *uk = (T *)d_keys;
     const int cur0 = P & 1;
+    const bool vec = ((uintptr_t)uk % 16) == 0;      // the scratch array is 256-byte aligned
     sr_status st = SR_OK;
     do {
         // the array keeps the previous call's contents: zero the counters
@@ -112,11 +114,17 @@ sr_status noalloc_impl(void *d_keys, size_t n, cudaStream_t s, unsigned char *ba
         for (int p = 0; p < P; ++p) {
             const long long w = (long long)TS << p;
             const long long nb = mtiles + 1;
-            SR_LAUNCH(SR_KERNEL_PARTITION, (k_partition<KT>), (unsigned)((nb + 255) / 256), 256, 0, s,
+            SR_LAUNCH(SR_KERNEL_PARTITION, (k_partition<KT>), (unsigned)((nb + 7) / 8), 256, 0, s,
                       uk, sk, N, w, NV, nb, splits, ctrl, cur0, p);
-            SR_LAUNCH(SR_KERNEL_MERGE, (k_merge<KT, NT, IPT, false>), (unsigned)mtiles, NT,
-                      (size_t)NV * sizeof(U), s, uk, (uint32_t *)nullptr, sk, (uint32_t *)nullptr, N, w,
-                      splits, ctrl, cur0, p);
+            if (vec) {
+                SR_LAUNCH(SR_KERNEL_MERGE, (k_merge<KT, NT, IPT, false, true>), (unsigned)mtiles, NT,
+                          (size_t)(NV + 16) * sizeof(U), s, uk, (uint32_t *)nullptr, sk, (uint32_t *)nullptr,
+                          N, w, splits, ctrl, cur0, p);
+            } else {
+                SR_LAUNCH(SR_KERNEL_MERGE, (k_merge<KT, NT, IPT, false, false>), (unsigned)mtiles, NT,
+                          (size_t)(NV + 16) * sizeof(U), s, uk, (uint32_t *)nullptr, sk, (uint32_t *)nullptr,
+                          N, w, splits, ctrl, cur0, p);
+            }
         }
         if (st != SR_OK) break;
         if (P > 0) {

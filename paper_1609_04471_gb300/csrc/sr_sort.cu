@@ -112,15 +112,22 @@ static sr_status sort_impl(void *d_keys, uint32_t *d_vals, size_t n, cudaStream_
         if ((st = allow_smem(k_block_sort<KT, SNT, IPT, VALS>, bs_smem)) != SR_OK) break;
         SR_LAUNCH(SR_KERNEL_BLOCK_SORT, (k_block_sort<KT, SNT, IPT, VALS>), (unsigned)tiles, SNT,
                   bs_smem, s, uk, uv, cur0 ? sk : uk, cur0 ? sv : uv, N, ctrl);
-        const size_t m_smem = (size_t)NV * (sizeof(U) + (VALS ? 4 : 0));
-        if ((st = allow_smem(k_merge<KT, NT, IPT, VALS>, m_smem)) != SR_OK) break;
+        const size_t m_smem = (size_t)(NV + 16) * (sizeof(U) + (VALS ? 4 : 0));
+        const bool vec = ((uintptr_t)uk % 16) == 0 && (!VALS || ((uintptr_t)uv % 16) == 0);
+        if ((st = allow_smem(k_merge<KT, NT, IPT, VALS, true>, m_smem)) != SR_OK) break;
+        if ((st = allow_smem(k_merge<KT, NT, IPT, VALS, false>, m_smem)) != SR_OK) break;
         for (int p = 0; p < P; ++p) {
             const long long w = (long long)TS << p;
             const long long nb = mtiles + 1;
-            SR_LAUNCH(SR_KERNEL_PARTITION, (k_partition<KT>), (unsigned)((nb + 255) / 256), 256, 0, s,
+            SR_LAUNCH(SR_KERNEL_PARTITION, (k_partition<KT>), (unsigned)((nb + 7) / 8), 256, 0, s,
                       uk, sk, N, w, NV, nb, splits, ctrl, cur0, p);
-            SR_LAUNCH(SR_KERNEL_MERGE, (k_merge<KT, NT, IPT, VALS>), (unsigned)mtiles, NT, m_smem, s,
-                      uk, uv, sk, sv, N, w, splits, ctrl, cur0, p);
+            if (vec) {
+                SR_LAUNCH(SR_KERNEL_MERGE, (k_merge<KT, NT, IPT, VALS, true>), (unsigned)mtiles, NT, m_smem,
+                          s, uk, uv, sk, sv, N, w, splits, ctrl, cur0, p);
+            } else {
+                SR_LAUNCH(SR_KERNEL_MERGE, (k_merge<KT, NT, IPT, VALS, false>), (unsigned)mtiles, NT, m_smem,
+                          s, uk, uv, sk, sv, N, w, splits, ctrl, cur0, p);
+            }
         }
         if (st != SR_OK) break;
         if (P > 0) {
