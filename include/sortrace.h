@@ -221,7 +221,7 @@ enum {
     SR_KERNEL_DETECT = 0,     /* run-detection scan */
     SR_KERNEL_REVERSE = 1,    /* whole-input reversal */
     SR_KERNEL_BLOCK_SORT = 2, /* shared-memory tile sort */
-    SR_KERNEL_PARTITION = 3,  /* merge-path partition */
+    SR_KERNEL_PARTITION = 3,  /* merge pass planning (which passes have pairs out of order) */
     SR_KERNEL_MERGE = 4,      /* global merge pass */
     SR_KERNEL_COPY = 5,       /* copy-back / gather */
     SR_KERNEL_SEGMENTED = 6,  /* segmented / bucket sorts */

@@ -65,15 +65,29 @@ template <> struct Key<SR_KEY_I64> {
 
 template <typename U> __device__ __forceinline__ U umax_of() { return ~U(0); }
 
+// Programmatic dependent launch: every kernel first lets the next kernel on
+// its stream be scheduled (its CTAs then wait in griddep_wait until this grid
+// has finished and its writes are visible), then waits for the previous one.
+__device__ __forceinline__ void griddep_wait() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // ---------------------------------------------------------- launch shapes
 //
 // IPT is odd so that thread t's IPT consecutive shared-memory words
 // t*IPT .. t*IPT+IPT-1 fall in distinct banks across a warp (gcd(IPT, 32) = 1).
 template <int KB, bool VALS> struct Shape;
-template <> struct Shape<4, false> { enum { NT = 256, IPT = 15, SORT_NT = 512 }; };
-template <> struct Shape<4, true>  { enum { NT = 256, IPT = 11, SORT_NT = 512 }; };
-template <> struct Shape<8, false> { enum { NT = 256, IPT = 11, SORT_NT = 512 }; };
-template <> struct Shape<8, true>  { enum { NT = 256, IPT = 9,  SORT_NT = 512 }; };
+// NT x IPT keys per merge CTA; SORT_NT x IPT keys per block-sort tile.  (A
+// 1024-thread block sort saves one global pass but its extra shared-memory
+// level costs more than that pass on GB300: 2.87 ms against 0.57 ms at 2^28.)
+#ifndef SR_MERGE_NT
+#define SR_MERGE_NT 256
+#endif
+template <> struct Shape<4, false> { enum { NT = SR_MERGE_NT, IPT = 15, SORT_NT = 512 }; };
+template <> struct Shape<4, true>  { enum { NT = SR_MERGE_NT, IPT = 11, SORT_NT = 512 }; };
+template <> struct Shape<8, false> { enum { NT = SR_MERGE_NT, IPT = 11, SORT_NT = 512 }; };
+template <> struct Shape<8, true>  { enum { NT = SR_MERGE_NT, IPT = 9,  SORT_NT = 512 }; };
 
 // ------------------------------------------------------------- merge path
 
@@ -87,6 +101,39 @@ __device__ __forceinline__ int merge_path(const U *a, int na, const U *b, int nb
         const int mid = (lo + hi) >> 1;
         if (!(b[diag - 1 - mid] < a[mid])) lo = mid + 1;
         else hi = mid;
+    }
+    return lo;
+}
+
+// The same split found by one warp over global memory: each round every lane
+// tests one of 32 evenly spaced candidates and a ballot keeps the stretch that
+// holds the answer, so 2^k candidates cost about k/5 dependent loads.  Returns
+// the number of A items among the first `diag` outputs of the stable merge of
+// src[a_beg .. a_beg+na) and src[b_beg .. b_beg+nb).  All lanes must call it
+// with the same arguments; all lanes return the answer.
+template <typename K>
+__device__ __forceinline__ long long warp_split(const typename K::T *__restrict__ src, long long a_beg,
+                                                long long na, long long b_beg, long long nb,
+                                                long long diag, int lane) {
+    typedef typename K::U U;
+    long long lo = max(0ll, diag - nb), hi = min(diag, na);
+    while (hi > lo) {
+        const long long step = (hi - lo + 31) >> 5;
+        const long long m = lo + lane * step;
+        bool before = false;                       // the answer is > m
+        if (m < hi) {
+            const U x = K::ord(src[a_beg + m]);
+            const U y = K::ord(src[b_beg + diag - 1 - m]);
+            before = !(y < x);
+        }
+        const int cnt = __popc(__ballot_sync(0xffffffffu, before));
+        if (cnt == 0) {
+            hi = lo;
+        } else {
+            const long long nlo = lo + (long long)(cnt - 1) * step + 1;
+            hi = min(hi, lo + (long long)cnt * step);
+            lo = nlo;
+        }
     }
     return lo;
 }
@@ -169,7 +216,7 @@ struct Ctrl {
     unsigned long long tiles_descending;
     int unordered[MAX_PASSES];          // per merge pass: run pairs not already in order
     int status;
-    int pad;
+    unsigned int plan_ticket;           // CTAs of the pass planner that finished
 };
 
 __device__ __forceinline__ int call_mode(const Ctrl *c, long long n) {

@@ -12,6 +12,7 @@ namespace sr {
 template <int KT, int NT, int IPT>
 __global__ void __launch_bounds__(NT) k_detect(const typename Key<KT>::T *__restrict__ keys,
                                                long long n, Ctrl *__restrict__ c) {
+    griddep_wait();
     typedef Key<KT> K;
     typedef typename K::U U;
     constexpr int NV = NT * IPT;
@@ -57,6 +58,7 @@ __global__ void __launch_bounds__(NT) k_detect(const typename Key<KT>::T *__rest
 template <int KT, bool VALS>
 __global__ void k_reverse(typename Key<KT>::T *__restrict__ k, uint32_t *__restrict__ v,
                           long long n, const Ctrl *__restrict__ c) {
+    griddep_wait();
     if (call_mode(c, n) != MODE_REVERSE) return;
     const long long half = n / 2;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -73,10 +75,14 @@ __global__ void k_reverse(typename Key<KT>::T *__restrict__ k, uint32_t *__restr
     }
 }
 
+// Sorts tile blockIdx.x of NT*IPT keys; records the tile's smallest and
+// largest key images in tile_lo / tile_hi (if given) for the pass planner.
 template <int KT, int NT, int IPT, bool VALS>
 __global__ void __launch_bounds__(NT)
 k_block_sort(const typename Key<KT>::T *in_k, const uint32_t *in_v, typename Key<KT>::T *out_k,
-             uint32_t *out_v, long long n, const Ctrl *__restrict__ c) {
+             uint32_t *out_v, long long n, const Ctrl *__restrict__ c,
+             typename Key<KT>::U *__restrict__ tile_lo, typename Key<KT>::U *__restrict__ tile_hi) {
+    griddep_wait();
     typedef Key<KT> K;
     typedef typename K::U U;
     constexpr int NV = NT * IPT;
@@ -107,6 +113,7 @@ k_block_sort(const typename Key<KT>::T *in_k, const uint32_t *in_v, typename Key
     const int any_desc = __syncthreads_or(desc);
     const int any_nondesc = __syncthreads_or(nondesc);
     if (!any_desc) {                       // already ascending
+        if (t == 0 && tile_lo) { tile_lo[blockIdx.x] = s[0]; tile_hi[blockIdx.x] = s[cnt - 1]; }
         if (out_k != in_k) {
             for (int idx = t; idx < cnt; idx += NT) {
                 out_k[base + idx] = K::unord(s[idx]);
@@ -116,6 +123,7 @@ k_block_sort(const typename Key<KT>::T *in_k, const uint32_t *in_v, typename Key
         return;
     }
     if (!any_nondesc) {                    // strictly descending: reverse
+        if (t == 0 && tile_lo) { tile_lo[blockIdx.x] = s[cnt - 1]; tile_hi[blockIdx.x] = s[0]; }
         for (int idx = t; idx < cnt; idx += NT) {
             out_k[base + idx] = K::unord(s[cnt - 1 - idx]);
             if (VALS) out_v[base + idx] = sv[cnt - 1 - idx];
@@ -137,57 +145,115 @@ k_block_sort(const typename Key<KT>::T *in_k, const uint32_t *in_v, typename Key
         if (VALS) sv[t * IPT + i] = v[i];
     }
     __syncthreads();
+    if (t == 0 && tile_lo) { tile_lo[blockIdx.x] = s[0]; tile_hi[blockIdx.x] = s[cnt - 1]; }
     for (int idx = t; idx < cnt; idx += NT) {
         out_k[base + idx] = K::unord(s[idx]);
         if (VALS) out_v[base + idx] = sv[idx];
     }
 }
 
-// One warp per merge-tile boundary b (0..tiles): splits[b] = the A index where
-// output position b*nv falls, for the pair of runs that contains it.  The warp
-// searches the merge path 32 ways at a time: each lane tests one candidate
-// and a ballot keeps the 1/32 of the range that holds the answer, so a search
-// over 2^k candidates costs about k/5 dependent loads instead of k.
+// Pass planner (after the block sort): a merged run's smallest and largest
+// keys are the smallest and largest of its tiles', so whether the two runs of a
+// pair at pass p are already in order (A.last <= B.first) is known for every
+// pass from the tile extremes alone.  Adds to c->unordered[p] the number of
+// pairs of pass p that must be merged; a pass with none is skipped (technique
+// (f) applied to whole passes).
+//
+// Each CTA reduces a chunk of PLAN_CHUNK tiles in shared memory, which settles
+// every pass whose pairs lie inside one chunk; the last CTA to finish (a ticket
+// taken after a fence) settles the remaining passes from the chunks' extremes.
+enum { PLAN_CHUNK = 2048, PLAN_LEVELS = 11 };   // 2^11 tiles per chunk
+
+template <int KT>
+__global__ void __launch_bounds__(1024)
+k_plan(const typename Key<KT>::U *__restrict__ lo, const typename Key<KT>::U *__restrict__ hi,
+       typename Key<KT>::U *__restrict__ chunk_lo, typename Key<KT>::U *__restrict__ chunk_hi,
+       long long n, long long tiles, int passes, Ctrl *__restrict__ c) {
+    griddep_wait();
+    typedef typename Key<KT>::U U;
+    if (call_mode(c, n) != MODE_SORT) return;
+    __shared__ U s_lo[PLAN_CHUNK], s_hi[PLAN_CHUNK];
+    __shared__ unsigned int s_cnt;
+    __shared__ int s_last;
+    const int t = threadIdx.x;
+    const long long base = (long long)blockIdx.x * PLAN_CHUNK;
+    const int cnt = (int)min((long long)PLAN_CHUNK, tiles - base);
+    for (int i = t; i < cnt; i += blockDim.x) { s_lo[i] = lo[base + i]; s_hi[i] = hi[base + i]; }
+    // run r of pass p is kept at index r << p: the pair of runs starting at
+    // ia = 2j << p and ib = ia + (1 << p) folds into ia
+    const int inner = passes < PLAN_LEVELS ? passes : PLAN_LEVELS;
+    for (int p = 0; p < inner; ++p) {
+        if (t == 0) s_cnt = 0;
+        __syncthreads();
+        const int stride = 1 << p;
+        unsigned int mine = 0;
+        for (int ia = 2 * stride * t; ia < cnt; ia += 2 * stride * blockDim.x) {
+            const int ib = ia + stride;
+            if (ib < cnt) {
+                mine += s_hi[ia] > s_lo[ib];
+                s_lo[ia] = s_lo[ia] < s_lo[ib] ? s_lo[ia] : s_lo[ib];
+                s_hi[ia] = s_hi[ia] > s_hi[ib] ? s_hi[ia] : s_hi[ib];
+            }
+        }
+        mine = __reduce_add_sync(0xffffffffu, mine);
+        if ((t & 31) == 0 && mine) atomicAdd(&s_cnt, mine);
+        __syncthreads();
+        if (t == 0 && s_cnt) atomicAdd(&c->unordered[p], (int)s_cnt);
+    }
+    if (passes <= PLAN_LEVELS) return;
+    // the chunk is fully reduced into index 0
+    if (t == 0) {
+        chunk_lo[blockIdx.x] = s_lo[0];
+        chunk_hi[blockIdx.x] = s_hi[0];
+        __threadfence();
+        s_last = atomicAdd(&c->plan_ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int chunks = (int)gridDim.x;            // at most PLAN_CHUNK chunks (2^22 tiles)
+    for (int i = t; i < chunks; i += blockDim.x) {
+        s_lo[i] = ((volatile U *)chunk_lo)[i];
+        s_hi[i] = ((volatile U *)chunk_hi)[i];
+    }
+    for (int p = PLAN_LEVELS; p < passes; ++p) {
+        if (t == 0) s_cnt = 0;
+        __syncthreads();
+        const int stride = 1 << (p - PLAN_LEVELS);
+        unsigned int mine = 0;
+        for (int ia = 2 * stride * t; ia < chunks; ia += 2 * stride * blockDim.x) {
+            const int ib = ia + stride;
+            if (ib < chunks) {
+                mine += s_hi[ia] > s_lo[ib];
+                s_lo[ia] = s_lo[ia] < s_lo[ib] ? s_lo[ia] : s_lo[ib];
+                s_hi[ia] = s_hi[ia] > s_hi[ib] ? s_hi[ia] : s_hi[ib];
+            }
+        }
+        mine = __reduce_add_sync(0xffffffffu, mine);
+        if ((t & 31) == 0 && mine) atomicAdd(&s_cnt, mine);
+        __syncthreads();
+        if (t == 0) c->unordered[p] = (int)s_cnt;
+    }
+}
+
 template <int KT>
 __global__ void __launch_bounds__(256)
 k_partition(const typename Key<KT>::T *__restrict__ uk, const typename Key<KT>::T *__restrict__ sk,
             long long n, long long w, int nv, long long nbound, long long *__restrict__ splits,
-            Ctrl *__restrict__ c, int cur0, int p) {
+            const Ctrl *__restrict__ c, int cur0, int p) {
+    griddep_wait();
     typedef Key<KT> K;
-    typedef typename K::U U;
     const int lane = threadIdx.x & 31;
     const long long b = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (b >= nbound) return;                       // uniform across the warp
-    if (call_mode(c, n) != MODE_SORT) return;
+    if (call_mode(c, n) != MODE_SORT || c->unordered[p] == 0) return;
     const typename K::T *src = buffer_before_pass(c, cur0, p) ? sk : uk;
     const long long out = min(b * (long long)nv, n);
     const long long pb = (out / (2 * w)) * (2 * w);
     const long long a_beg = pb, a_end = min(pb + w, n);
     const long long b_beg = a_end, b_end = min(pb + 2 * w, n);
-    const long long diag = out - pb, na = a_end - a_beg, nb = b_end - b_beg;
-    if (lane == 0 && diag == 0 && nb > 0 && K::ord(src[a_end - 1]) > K::ord(src[b_beg]))
-        atomicAdd(&c->unordered[p], 1);
-    // answer: the first m in [lo, hi) with A[m] > B[diag-1-m], else hi
-    long long lo = max(0ll, diag - nb), hi = min(diag, na);
-    while (hi > lo) {
-        const long long step = (hi - lo + 31) >> 5;
-        const long long m = lo + lane * step;
-        bool before = false;                       // answer > m
-        if (m < hi) {
-            const U x = K::ord(src[a_beg + m]);
-            const U y = K::ord(src[b_beg + diag - 1 - m]);
-            before = !(y < x);
-        }
-        const int cnt = __popc(__ballot_sync(0xffffffffu, before));
-        if (cnt == 0) {
-            hi = lo;
-        } else {
-            const long long nlo = lo + (long long)(cnt - 1) * step + 1;
-            hi = min(hi, lo + (long long)cnt * step);
-            lo = nlo;
-        }
-    }
-    if (lane == 0) splits[b] = a_beg + lo;
+    const long long sp = warp_split<K>(src, a_beg, a_end - a_beg, b_beg, b_end - b_beg, out - pb, lane);
+    if (lane == 0) splits[b] = a_beg + sp;
 }
 
 // One CTA per output tile of NT*IPT keys of merge pass p.  The tile's A and B
@@ -204,19 +270,17 @@ __global__ void __launch_bounds__(NT)
 k_merge(typename Key<KT>::T *uk, uint32_t *uv, typename Key<KT>::T *sk, uint32_t *svb, long long n,
         long long w, const long long *__restrict__ splits, const Ctrl *__restrict__ c, int cur0,
         int p) {
+    griddep_wait();
     typedef Key<KT> K;
     typedef typename K::U U;
     typedef typename K::T T;
     constexpr int NV = NT * IPT;
     constexpr int SV = NV + 16;                    // staged keys, with room for window slack
     if (call_mode(c, n) != MODE_SORT || c->unordered[p] == 0) return;
-    __shared__ int s_cur;
-    if (threadIdx.x == 0) s_cur = buffer_before_pass(c, cur0, p);
     extern __shared__ __align__(16) unsigned char smem[];
     U *s = reinterpret_cast<U *>(smem);
     uint32_t *sv = reinterpret_cast<uint32_t *>(s + SV);
-    __syncthreads();
-    const int cur = s_cur;
+    const int cur = buffer_before_pass(c, cur0, p);
     const T *src_k = cur ? sk : uk;
     T *dst_k = cur ? uk : sk;
     const uint32_t *src_v = cur ? svb : uv;
@@ -349,6 +413,7 @@ template <int KT, bool VALS>
 __global__ void k_copy_back(typename Key<KT>::T *uk, uint32_t *uv, const typename Key<KT>::T *sk,
                             const uint32_t *svb, long long n, const Ctrl *__restrict__ c,
                             int cur0, int passes) {
+    griddep_wait();
     if (call_mode(c, n) != MODE_SORT) return;
     if (buffer_before_pass(c, cur0, passes) == 0) return;
     const long long stride = (long long)gridDim.x * blockDim.x;

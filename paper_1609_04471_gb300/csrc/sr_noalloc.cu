@@ -30,19 +30,25 @@
 
 #include "sr_device.cuh"
 #include "sr_kernels.cuh"
+#include "sr_plain.cuh"
 #include "sr_runtime.cuh"
 
 namespace sr {
 namespace {
 
-// Layout of the scratch array: [control block | split table | key buffer].
-constexpr size_t kCtrlBytes = 256;
-constexpr size_t kMinMergeTile = Shape<8, false>::NT * Shape<8, false>::IPT;   // 2816 keys
-constexpr size_t kSplitBytes =
-    ((SR_NOALLOC_MAX_KEYS + kMinMergeTile - 1) / kMinMergeTile + 1) * 8 + 255 & ~size_t(255);
-constexpr size_t kKeyBytes = (size_t)SR_NOALLOC_MAX_KEYS * 8;
-constexpr size_t kScratchBytes = kCtrlBytes + kSplitBytes + kKeyBytes;
-static_assert(sizeof(Ctrl) <= kCtrlBytes, "control block does not fit");
+// Scratch for the largest n of the widest key type; PlainSort lays it out as
+// [control block | tile extremes for the pass planner | split table | key buffer].
+// (the same arithmetic as PlainSort's constructor, at compile time; every call
+// checks its own layout against this size).
+constexpr size_t up256(size_t x) { return (x + 255) / 256 * 256; }
+constexpr long long kTileKeys64 = (long long)Shape<8, false>::SORT_NT * Shape<8, false>::IPT;
+constexpr long long kTiles64 = (SR_NOALLOC_MAX_KEYS + kTileKeys64 - 1) / kTileKeys64;
+constexpr long long kMergeTile64 = (long long)Shape<8, false>::NT * Shape<8, false>::IPT;
+constexpr long long kMTiles64 = (SR_NOALLOC_MAX_KEYS + kMergeTile64 - 1) / kMergeTile64;
+constexpr size_t kScratchBytes = up256(sizeof(Ctrl)) +
+                                 up256((size_t)(2 * kTiles64 + 2 * ((kTiles64 + 1) / 2) + 2) * 8) +
+                                 up256((size_t)(kMTiles64 + 1) * 8) +
+                                 up256((size_t)SR_NOALLOC_MAX_KEYS * 8);
 
 // The scratch itself.  In host code this name is only a host-side stand-in
 // for the device symbol; host code must use the address from
@@ -77,62 +83,10 @@ sr_status scratch_base(unsigned char **out) {
 // The launch sequence of sr_sort_keys (keys only) over the fixed scratch.
 template <int KT>
 sr_status noalloc_impl(void *d_keys, size_t n, cudaStream_t s, unsigned char *base) {
-    typedef Key<KT> K;
-    typedef typename K::T T;
-    typedef typename K::U U;
-    typedef Shape<sizeof(T), false> S;
-    constexpr int NT = S::NT, IPT = S::IPT, SNT = S::SORT_NT;
-    constexpr int NV = NT * IPT;
-    constexpr int TS = SNT * IPT;
-    // every kernel below fits the default 48 KB of dynamic shared memory
-    static_assert((TS + 1) * sizeof(U) <= 48 * 1024, "detect tile too large");
-    static_assert(TS * sizeof(U) <= 48 * 1024, "block-sort tile too large");
-    static_assert((NV + 16) * sizeof(U) <= 48 * 1024, "merge tile too large");
-    if (n < 2) return SR_OK;
-    const long long N = (long long)n;
-    const long long tiles = (N + TS - 1) / TS;
-    const int P = ceil_log2((unsigned long long)tiles);
-    const long long mtiles = (N + NV - 1) / NV;
-    if ((size_t)(mtiles + 1) * 8 > kSplitBytes || n * sizeof(T) > kKeyBytes) return SR_ERR_INVALID_ARG;
-    Ctrl *ctrl = (Ctrl *)base;
-    long long *splits = (long long *)(base + kCtrlBytes);
-    T *sk = (T *)(base + kCtrlBytes + kSplitBytes);
-    T *uk = (T *)d_keys;
-    const int cur0 = P & 1;
-    const bool vec = ((uintptr_t)uk % 16) == 0;      // the scratch array is 256-byte aligned
-    sr_status st = SR_OK;
-    do {
-        // the array keeps the previous call's contents: zero the counters
-        if (cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s) != cudaSuccess) { st = launch_status(); break; }
-        SR_LAUNCH(SR_KERNEL_DETECT, (k_detect<KT, SNT, IPT>), (unsigned)tiles, SNT,
-                  (size_t)(TS + 1) * sizeof(U), s, uk, N, ctrl);
-        SR_LAUNCH(SR_KERNEL_REVERSE, (k_reverse<KT, false>), (unsigned)((N / 2 + 255) / 256 > 0 ? (N / 2 + 255) / 256 : 1),
-                  256, 0, s, uk, (uint32_t *)nullptr, N, ctrl);
-        SR_LAUNCH(SR_KERNEL_BLOCK_SORT, (k_block_sort<KT, SNT, IPT, false>), (unsigned)tiles, SNT,
-                  (size_t)TS * sizeof(U), s, uk, (const uint32_t *)nullptr, cur0 ? sk : uk,
-                  (uint32_t *)nullptr, N, ctrl);
-        for (int p = 0; p < P; ++p) {
-            const long long w = (long long)TS << p;
-            const long long nb = mtiles + 1;
-            SR_LAUNCH(SR_KERNEL_PARTITION, (k_partition<KT>), (unsigned)((nb + 7) / 8), 256, 0, s,
-                      uk, sk, N, w, NV, nb, splits, ctrl, cur0, p);
-            if (vec) {
-                SR_LAUNCH(SR_KERNEL_MERGE, (k_merge<KT, NT, IPT, false, true>), (unsigned)mtiles, NT,
-                          (size_t)(NV + 16) * sizeof(U), s, uk, (uint32_t *)nullptr, sk, (uint32_t *)nullptr,
-                          N, w, splits, ctrl, cur0, p);
-            } else {
-                SR_LAUNCH(SR_KERNEL_MERGE, (k_merge<KT, NT, IPT, false, false>), (unsigned)mtiles, NT,
-                          (size_t)(NV + 16) * sizeof(U), s, uk, (uint32_t *)nullptr, sk, (uint32_t *)nullptr,
-                          N, w, splits, ctrl, cur0, p);
-            }
-        }
-        if (st != SR_OK) break;
-        if (P > 0) {
-            SR_LAUNCH(SR_KERNEL_COPY, (k_copy_back<KT, false>), (unsigned)((N + 255) / 256), 256, 0, s,
-                      uk, (uint32_t *)nullptr, sk, (const uint32_t *)nullptr, N, ctrl, cur0, P);
-        }
-    } while (0);
-    return st;
+    typedef PlainSort<KT, false> PS;
+    const PS plan(n);
+    if (plan.bytes > kScratchBytes) return SR_ERR_INVALID_ARG;
+    return plan.launch((typename PS::T *)d_keys, nullptr, base, s);
 }
 
 }  // namespace

@@ -1,0 +1,124 @@
+// sr_plain.cuh -- the launch sequence of the plain sort over a given scratch
+// area, shared by sr_sort_keys / sr_sort_pairs (pool scratch) and
+// sr_sort_keys_noalloc (a fixed device array).
+//
+//   k_detect      run-detection scan: descents and non-descents (Run(A)).
+//   k_reverse     strictly descending input: one reversal, nothing else runs.
+//   k_block_sort  tiles of SORT_NT*IPT keys sorted in shared memory (ascending
+//                 tiles kept, strictly descending tiles reversed); records each
+//                 tile's smallest and largest key.
+//   k_plan        which merge passes have any run pair out of order.
+//   per pass p    k_partition (merge-path splits of every output tile) and
+//                 k_merge (policy e1); passes with every pair in order skip.
+//   k_copy_back   if skipped passes left the result in scratch, copy it home.
+#pragma once
+
+#include "sr_device.cuh"
+#include "sr_kernels.cuh"
+#include "sr_runtime.cuh"
+
+namespace sr {
+
+template <int KT, bool VALS> struct PlainSort {
+    typedef Key<KT> K;
+    typedef typename K::T T;
+    typedef typename K::U U;
+    typedef Shape<sizeof(T), VALS> S;
+    enum { NT = S::NT, IPT = S::IPT, SNT = S::SORT_NT, NV = S::NT * S::IPT, TS = S::SORT_NT * S::IPT };
+    static_assert(TS % NV == 0, "sort tile must be a whole number of merge tiles");
+
+    long long n = 0, tiles = 0, mtiles = 0;
+    int passes = 0;
+    // byte offsets inside the scratch area
+    size_t off_ctrl = 0, off_plan = 0, off_split = 0, off_keys = 0, off_vals = 0, bytes = 0;
+
+    explicit PlainSort(size_t n_) {
+        n = (long long)n_;
+        tiles = (n + TS - 1) / TS;
+        mtiles = (n + NV - 1) / NV;
+        passes = ceil_log2((unsigned long long)(tiles > 0 ? tiles : 1));
+        off_ctrl = 0;
+        off_plan = align_up(sizeof(Ctrl), 256);
+        const size_t plan_bytes = align_up((size_t)(2 * tiles + 2 * ((tiles + 1) / 2) + 2) * sizeof(U), 256);
+        off_split = off_plan + plan_bytes;
+        off_keys = off_split + align_up((size_t)(mtiles + 1) * 8, 256);
+        const size_t kb = passes > 0 ? align_up((size_t)n * sizeof(T), 256) : 0;
+        off_vals = off_keys + kb;
+        const size_t vb = (VALS && passes > 0) ? align_up((size_t)n * 4, 256) : 0;
+        bytes = off_vals + vb;
+    }
+
+    // Launches the whole sequence on stream s.  The block sort writes to the
+    // scratch copy when the number of passes is odd, so the last merge lands in
+    // the caller's buffer.
+    sr_status launch(T *uk, uint32_t *uv, unsigned char *scratch, cudaStream_t s) const {
+        Ctrl *ctrl = (Ctrl *)(scratch + off_ctrl);
+        U *plo = (U *)(scratch + off_plan);
+        U *phi = plo + tiles;
+        U *plo2 = phi + tiles;
+        U *phi2 = plo2 + (tiles + 1) / 2 + 1;
+        long long *splits = (long long *)(scratch + off_split);
+        T *sk = (T *)(scratch + off_keys);
+        uint32_t *sv = (uint32_t *)(scratch + off_vals);
+        const int P = passes;
+        const int cur0 = P & 1;
+        const bool vec = ((uintptr_t)uk % 16) == 0 && (!VALS || ((uintptr_t)uv % 16) == 0);
+        sr_status st = SR_OK;
+        do {
+            if (cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s) != cudaSuccess) { st = launch_status(); break; }
+            const size_t det_smem = (size_t)(TS + 1) * sizeof(U);
+            if ((st = allow_smem(k_detect<KT, SNT, IPT>, det_smem)) != SR_OK) break;
+            SR_LAUNCH(SR_KERNEL_DETECT, (k_detect<KT, SNT, IPT>), (unsigned)tiles, SNT, det_smem, s,
+                      uk, n, ctrl);
+            SR_LAUNCH(SR_KERNEL_REVERSE, (k_reverse<KT, VALS>), grid_for(n / 2, 256, 152 * 16), 256, 0, s,
+                      uk, uv, n, ctrl);
+            const size_t bs_smem = (size_t)TS * (sizeof(U) + (VALS ? 4 : 0));
+            if ((st = allow_smem(k_block_sort<KT, SNT, IPT, VALS>, bs_smem)) != SR_OK) break;
+            SR_LAUNCH(SR_KERNEL_BLOCK_SORT, (k_block_sort<KT, SNT, IPT, VALS>), (unsigned)tiles, SNT,
+                      bs_smem, s, uk, uv, cur0 ? sk : uk, cur0 ? sv : uv, n, ctrl, plo, phi);
+            if (P == 0) break;
+            if ((tiles + PLAN_CHUNK - 1) / PLAN_CHUNK > PLAN_CHUNK) { st = SR_ERR_UNSUPPORTED; break; }
+            SR_LAUNCH(SR_KERNEL_PARTITION, (k_plan<KT>), (unsigned)((tiles + PLAN_CHUNK - 1) / PLAN_CHUNK),
+                      1024, 0, s, plo, phi, plo2, phi2, n, tiles, P, ctrl);
+            const size_t m_smem = (size_t)(NV + 16) * (sizeof(U) + (VALS ? 4 : 0));
+            if ((st = allow_smem(k_merge<KT, NT, IPT, VALS, true>, m_smem)) != SR_OK) break;
+            if ((st = allow_smem(k_merge<KT, NT, IPT, VALS, false>, m_smem)) != SR_OK) break;
+            for (int p = 0; p < P; ++p) {
+                const long long w = (long long)TS << p;
+                const long long nb = mtiles + 1;
+                SR_LAUNCH(SR_KERNEL_PARTITION, (k_partition<KT>), (unsigned)((nb + 7) / 8), 256, 0, s,
+                          uk, sk, n, w, NV, nb, splits, ctrl, cur0, p);
+                if (vec) {
+                    SR_LAUNCH(SR_KERNEL_MERGE, (k_merge<KT, NT, IPT, VALS, true>), (unsigned)mtiles, NT,
+                              m_smem, s, uk, uv, sk, sv, n, w, splits, ctrl, cur0, p);
+                } else {
+                    SR_LAUNCH(SR_KERNEL_MERGE, (k_merge<KT, NT, IPT, VALS, false>), (unsigned)mtiles, NT,
+                              m_smem, s, uk, uv, sk, sv, n, w, splits, ctrl, cur0, p);
+                }
+            }
+            if (st != SR_OK) break;
+            SR_LAUNCH(SR_KERNEL_COPY, (k_copy_back<KT, VALS>), grid_for(n, 256, 152 * 16), 256, 0, s,
+                      uk, uv, sk, sv, n, ctrl, cur0, P);
+        } while (0);
+        return st;
+    }
+
+    static int grid_for(long long work, int per_block, int cap) {
+        long long g = (work + per_block - 1) / per_block;
+        if (g < 1) g = 1;
+        if (g > cap) g = cap;
+        return (int)g;
+    }
+
+    template <typename F>
+    static sr_status allow_smem(F *kernel, size_t bytes) {
+        if (bytes > 48 * 1024) {
+            if (cudaFuncSetAttribute((const void *)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)bytes) != cudaSuccess)
+                return launch_status();
+        }
+        return SR_OK;
+    }
+};
+
+}  // namespace sr

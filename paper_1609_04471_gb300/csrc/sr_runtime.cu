@@ -55,6 +55,14 @@ sr_status launch_end(int kind, cudaStream_t s) {
     return st;
 }
 
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char *e = std::getenv("SR_PDL");
+        return !(e && std::strcmp(e, "0") == 0);
+    }();
+    return on;
+}
+
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 int ceil_log2(unsigned long long x) {

@@ -62,15 +62,42 @@ bool valid_key_type(int kt);
         if (_st != SR_OK) return _st;              \
     } while (0)
 
-// Launches `kernel<<<grid, block, smem, stream>>>(args...)`, counts it, times
-// it when profiling is on, and breaks out of the enclosing do/while with the
+namespace sr {
+// Whether launches use programmatic dependent launch (on unless the
+// environment variable SR_PDL is "0").
+bool pdl_enabled();
+
+// Launches kernel on stream s.  With programmatic dependent launch the
+// kernel's CTAs may be scheduled while the previous kernel on the stream is
+// still finishing; every kernel of the library therefore begins with
+// griddep_wait() (see sr_device.cuh) before it touches memory the previous
+// kernel wrote.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_kernel(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                          Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, ((KArgs)args)...);
+}
+}  // namespace sr
+
+// Launches `kernel` with (grid, block, smem, stream, args...), counts it,
+// times it when profiling is on, and breaks out of the enclosing loop with the
 // status in `st` if the launch failed.
-#define SR_LAUNCH(kind, kernel, grid, block, smem, stream, ...)          \
-    {                                                                     \
-        ::sr::launch_begin((kind), (stream));                             \
-        kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);       \
-        st = ::sr::launch_end((kind), (stream));                          \
-        if (st != SR_OK) break;                                           \
+#define SR_LAUNCH(kind, kernel, grid, block, smem, stream, ...)                              \
+    {                                                                                         \
+        ::sr::launch_begin((kind), (stream));                                                 \
+        ::sr::launch_kernel(kernel, dim3(grid), dim3(block), (smem), (stream), __VA_ARGS__);  \
+        st = ::sr::launch_end((kind), (stream));                                              \
+        if (st != SR_OK) break;                                                               \
     }
 
 #define SR_LAUNCHED()                              \

@@ -173,7 +173,7 @@ def test_detect_runs_matches_oracle(gpu_lib):
 @pytest.mark.parametrize("dtype", [np.int32, np.float32, np.uint64, np.int64, np.uint32])
 def test_pairs_stable(gpu_lib, dtype):
     rng = np.random.default_rng(12)
-    for n in (0, 1, 2, 33, 2816, 2817, 5632, 5633, 30_001, 262_147):
+    for n in (0, 1, 2, 33, 2304, 2816, 2817, 9216, 9217, 11264, 11265, 30_001, 262_147):
         k = (rng.integers(0, 9, n).astype(dtype) if n % 2 else _random(rng, n, dtype))
         v = rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32)
         gk, gv = _gpu_pairs(gpu_lib, k, v)
