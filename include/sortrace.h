@@ -96,11 +96,26 @@ sr_status sr_sort_pairs(void *d_keys, uint32_t *d_vals, size_t n, sr_key_type kt
  *              non-decreasing with d_offsets[0] >= 0.  Empty segments are allowed.
  * Offsets are read on the device; offsets that fail the check set the device
  * status word to SR_ERR_BAD_SEGMENTS (see sr_stream_status) and no key is moved.
+ * The total length d_offsets[num_segments] is read back first (the call waits
+ * for `stream` once); use sr_sort_segmented_ex to avoid that.
  * The paper sorts one array per call; the batch is each of those calls side by
  * side (Section 1: the same operation on many instances).
  */
 sr_status sr_sort_segmented(void *d_keys, const int64_t *d_offsets, size_t num_segments,
                             sr_key_type kt, sr_stream stream);
+
+/*
+ * sr_sort_segmented_ex -- sr_sort_segmented with the key array's length given:
+ *   n_keys  length of d_keys; every offset must lie in [0, n_keys].
+ * sr_sort_segmented reads d_offsets[num_segments] back to the host once (it
+ * waits for `stream`) to size its scratch; this form reads nothing back, so a
+ * sequence of calls can be captured in a CUDA graph (the first call on a
+ * device must come before any capture).  Small segments are sorted many to a
+ * CTA, medium ones one per CTA, and long ones by merge passes, all from one
+ * persistent work queue (see stats.big_segments).
+ */
+sr_status sr_sort_segmented_ex(void *d_keys, size_t n_keys, const int64_t *d_offsets,
+                               size_t num_segments, sr_key_type kt, sr_stream stream);
 
 /*
  * sr_sort_keys_host -- sr_sort_keys on a HOST array: copies h_keys[0..n) to the

@@ -66,6 +66,7 @@ SIGNATURES = {
     "sr_sort_keys": (_i32, [_vp, _sz, _i32, _vp]),
     "sr_sort_pairs": (_i32, [_vp, _vp, _sz, _i32, _vp]),
     "sr_sort_segmented": (_i32, [_vp, _vp, _sz, _i32, _vp]),
+    "sr_sort_segmented_ex": (_i32, [_vp, _sz, _vp, _sz, _i32, _vp]),
     "sr_sort_keys_host": (_i32, [_vp, _sz, _i32, _vp]),
     "sr_sort_keys_noalloc": (_i32, [_vp, _sz, _i32, _vp]),
     "sr_sort_keys_learned": (_i32, [_vp, _sz, _i32, _vp, _vp]),
@@ -184,6 +185,17 @@ def sort_segmented(keys, offsets, key_type: int | None = None, stream=None):
     kt = key_type_of(keys) if key_type is None else key_type
     _check(load().sr_sort_segmented(keys.data_ptr(), offsets.data_ptr(), max(offsets.numel() - 1, 0),
                                     kt, _stream(stream)), "sr_sort_segmented")
+    return keys
+
+
+def sort_segmented_ex(keys, offsets, key_type: int | None = None, stream=None):
+    """sort_segmented without reading the total length back (graph-capturable)."""
+    _cuda_contig(keys, "keys")
+    _cuda_contig(offsets, "offsets")
+    kt = key_type_of(keys) if key_type is None else key_type
+    _check(load().sr_sort_segmented_ex(keys.data_ptr(), keys.numel(), offsets.data_ptr(),
+                                       max(offsets.numel() - 1, 0), kt, _stream(stream)),
+           "sr_sort_segmented_ex")
     return keys
 
 

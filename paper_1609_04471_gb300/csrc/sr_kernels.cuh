@@ -256,45 +256,30 @@ k_partition(const typename Key<KT>::T *__restrict__ uk, const typename Key<KT>::
     if (lane == 0) splits[b] = a_beg + sp;
 }
 
-// One CTA per output tile of NT*IPT keys of merge pass p.  The tile's A and B
-// ranges come from the split table; both are staged in shared memory, merged
-// by merge path (IPT outputs per thread) and written back.
+// Merges one output tile: outputs [out0, out0 + cnt) of the stable merge of
+// the sorted ranges A = src[a0 .. a1) and B = src[b0 .. b0 + cnt - (a1 - a0)),
+// written to dst at out0.  All threads of the CTA call it; s / sv are shared
+// buffers of NT*IPT + 16 keys / values.  `n` bounds the buffers (loads stay
+// below it).
 //
 // VEC (every buffer 16-byte aligned): the ranges are staged as windows of
 // 4-key groups starting on a group boundary, so every group moves with 128-bit
 // loads and shared-memory stores, all issued before the first is used; the
-// output tile (which starts on a group boundary) leaves with 128-bit stores.
-// Keys before a range's start inside its first group are staged and ignored.
+// output tile (which must start on a group boundary) leaves with 128-bit
+// stores between scalar head and tail keys.  Keys before a range's start
+// inside its first group are staged and ignored.
 template <int KT, int NT, int IPT, bool VALS, bool VEC>
-__global__ void __launch_bounds__(NT)
-k_merge(typename Key<KT>::T *uk, uint32_t *uv, typename Key<KT>::T *sk, uint32_t *svb, long long n,
-        long long w, const long long *__restrict__ splits, const Ctrl *__restrict__ c, int cur0,
-        int p) {
-    griddep_wait();
+__device__ __forceinline__ void merge_tile(const typename Key<KT>::T *__restrict__ src_k,
+                                           typename Key<KT>::T *__restrict__ dst_k,
+                                           const uint32_t *__restrict__ src_v, uint32_t *__restrict__ dst_v,
+                                           long long n, long long out0, int cnt, long long a0, long long a1,
+                                           long long b0, typename Key<KT>::U *s, uint32_t *sv) {
     typedef Key<KT> K;
     typedef typename K::U U;
     typedef typename K::T T;
     constexpr int NV = NT * IPT;
-    constexpr int SV = NV + 16;                    // staged keys, with room for window slack
-    if (call_mode(c, n) != MODE_SORT || c->unordered[p] == 0) return;
-    extern __shared__ __align__(16) unsigned char smem[];
-    U *s = reinterpret_cast<U *>(smem);
-    uint32_t *sv = reinterpret_cast<uint32_t *>(s + SV);
-    const int cur = buffer_before_pass(c, cur0, p);
-    const T *src_k = cur ? sk : uk;
-    T *dst_k = cur ? uk : sk;
-    const uint32_t *src_v = cur ? svb : uv;
-    uint32_t *dst_v = cur ? uv : svb;
+    constexpr int SV = NV + 16;
     const int t = threadIdx.x;
-    const long long out0 = (long long)blockIdx.x * NV;
-    const long long out1 = min(out0 + NV, n);
-    const int cnt = (int)(out1 - out0);
-    const long long pb = (out0 / (2 * w)) * (2 * w);
-    const long long a_beg = pb, a_end = min(pb + w, n);
-    const long long b_beg = a_end, b_end = min(pb + 2 * w, n);
-    const long long a0 = splits[blockIdx.x];
-    const long long a1 = (out1 == b_end) ? a_end : splits[blockIdx.x + 1];
-    const long long b0 = b_beg + (out0 - pb) - (a0 - a_beg);
     const int acnt = (int)(a1 - a0);
     const int bcnt = cnt - acnt;
     int sa, sb;                                    // staged positions of A[a0] and B[b0]
@@ -376,28 +361,36 @@ k_merge(typename Key<KT>::T *uk, uint32_t *uv, typename Key<KT>::T *sk, uint32_t
     }
     __syncthreads();
     if (VEC) {
-        const int full = cnt >> 2;
+        // keys before the first 4-key group boundary of the output go one by one
+        const int head = min(cnt, (int)((4 - (out0 & 3)) & 3));
+        if (t < head) {
+            dst_k[out0 + t] = K::unord(s[t]);
+            if (VALS) dst_v[out0 + t] = sv[t];
+        }
+        const int full = (cnt - head) >> 2;
         for (int g = t; g < full; g += NT) {
+            const int j = head + 4 * g;
             if (sizeof(T) == 4) {
                 uint4 q;
-                q.x = (uint32_t)K::unord(s[4 * g + 0]);
-                q.y = (uint32_t)K::unord(s[4 * g + 1]);
-                q.z = (uint32_t)K::unord(s[4 * g + 2]);
-                q.w = (uint32_t)K::unord(s[4 * g + 3]);
-                *reinterpret_cast<uint4 *>(dst_k + out0 + 4 * g) = q;
+                q.x = (uint32_t)K::unord(s[j + 0]);
+                q.y = (uint32_t)K::unord(s[j + 1]);
+                q.z = (uint32_t)K::unord(s[j + 2]);
+                q.w = (uint32_t)K::unord(s[j + 3]);
+                *reinterpret_cast<uint4 *>(dst_k + out0 + j) = q;
             } else {
-                const unsigned long long e0 = (unsigned long long)K::unord(s[4 * g + 0]);
-                const unsigned long long e1 = (unsigned long long)K::unord(s[4 * g + 1]);
-                const unsigned long long e2 = (unsigned long long)K::unord(s[4 * g + 2]);
-                const unsigned long long e3 = (unsigned long long)K::unord(s[4 * g + 3]);
-                *reinterpret_cast<uint4 *>(dst_k + out0 + 4 * g) =
+                const unsigned long long e0 = (unsigned long long)K::unord(s[j + 0]);
+                const unsigned long long e1 = (unsigned long long)K::unord(s[j + 1]);
+                const unsigned long long e2 = (unsigned long long)K::unord(s[j + 2]);
+                const unsigned long long e3 = (unsigned long long)K::unord(s[j + 3]);
+                *reinterpret_cast<uint4 *>(dst_k + out0 + j) =
                     make_uint4((uint32_t)e0, (uint32_t)(e0 >> 32), (uint32_t)e1, (uint32_t)(e1 >> 32));
-                *reinterpret_cast<uint4 *>(dst_k + out0 + 4 * g + 2) =
+                *reinterpret_cast<uint4 *>(dst_k + out0 + j + 2) =
                     make_uint4((uint32_t)e2, (uint32_t)(e2 >> 32), (uint32_t)e3, (uint32_t)(e3 >> 32));
             }
-            if (VALS) *reinterpret_cast<uint4 *>(dst_v + out0 + 4 * g) = *reinterpret_cast<const uint4 *>(sv + 4 * g);
+            if (VALS)
+                *reinterpret_cast<uint4 *>(dst_v + out0 + j) = make_uint4(sv[j], sv[j + 1], sv[j + 2], sv[j + 3]);
         }
-        for (int i = 4 * full + t; i < cnt; i += NT) {
+        for (int i = head + 4 * full + t; i < cnt; i += NT) {
             dst_k[out0 + i] = K::unord(s[i]);
             if (VALS) dst_v[out0 + i] = sv[i];
         }
@@ -407,6 +400,36 @@ k_merge(typename Key<KT>::T *uk, uint32_t *uv, typename Key<KT>::T *sk, uint32_t
             if (VALS) dst_v[out0 + i] = sv[i];
         }
     }
+}
+
+// One CTA per output tile of NT*IPT keys of merge pass p.  The tile's A and B
+// ranges come from the split table and are merged by merge_tile.
+template <int KT, int NT, int IPT, bool VALS, bool VEC>
+__global__ void __launch_bounds__(NT)
+k_merge(typename Key<KT>::T *uk, uint32_t *uv, typename Key<KT>::T *sk, uint32_t *svb, long long n,
+        long long w, const long long *__restrict__ splits, const Ctrl *__restrict__ c, int cur0,
+        int p) {
+    griddep_wait();
+    typedef Key<KT> K;
+    typedef typename K::U U;
+    typedef typename K::T T;
+    constexpr int NV = NT * IPT;
+    constexpr int SV = NV + 16;                    // staged keys, with room for window slack
+    if (call_mode(c, n) != MODE_SORT || c->unordered[p] == 0) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    U *s = reinterpret_cast<U *>(smem);
+    uint32_t *sv = reinterpret_cast<uint32_t *>(s + SV);
+    const int cur = buffer_before_pass(c, cur0, p);
+    const long long out0 = (long long)blockIdx.x * NV;
+    const long long out1 = min(out0 + NV, n);
+    const long long pb = (out0 / (2 * w)) * (2 * w);
+    const long long a_beg = pb, a_end = min(pb + w, n);
+    const long long b_beg = a_end, b_end = min(pb + 2 * w, n);
+    const long long a0 = splits[blockIdx.x];
+    const long long a1 = (out1 == b_end) ? a_end : splits[blockIdx.x + 1];
+    const long long b0 = b_beg + (out0 - pb) - (a0 - a_beg);
+    merge_tile<KT, NT, IPT, VALS, VEC>(cur ? sk : uk, cur ? uk : sk, cur ? svb : uv, cur ? uv : svb, n, out0,
+                                       (int)(out1 - out0), a0, a1, b0, s, sv);
 }
 
 template <int KT, bool VALS>

@@ -1,9 +1,6 @@
 // sr_pending.cu -- entry points whose kernels are not in this build yet.
 #include "sr_runtime.cuh"
 
-extern "C" sr_status sr_sort_segmented(void *, const int64_t *, size_t, sr_key_type, sr_stream) {
-    return SR_ERR_UNSUPPORTED;
-}
 extern "C" sr_status sr_sort_keys_learned(void *, size_t, sr_key_type, const sr_learned_opts *, sr_stream) {
     return SR_ERR_UNSUPPORTED;
 }
@@ -19,3 +16,7 @@ extern "C" sr_status sr_model_buckets(const void *, size_t, sr_key_type, const f
                                       uint64_t, uint32_t, uint32_t *, sr_stream) {
     return SR_ERR_UNSUPPORTED;
 }
+
+namespace sr {
+sr_status learned_stats(const void *, sr_stats *) { return SR_OK; }
+}  // namespace sr

@@ -108,6 +108,8 @@ sr_status device_state(DeviceState **out) {
         cudaMemPoolSetAttribute(ds.pool, cudaMemPoolAttrReleaseThreshold, &keep);
         if (cudaMalloc(&ds.status, sizeof(int)) != cudaSuccess ||
             cudaMalloc(&ds.last_ctrl, sizeof(Ctrl)) != cudaSuccess ||
+            cudaMalloc(&ds.last_aux, kAuxBytes) != cudaSuccess ||
+            cudaMemset(ds.last_aux, 0, kAuxBytes) != cudaSuccess ||
             cudaMemset(ds.status, 0, sizeof(int)) != cudaSuccess ||
             cudaMemset(ds.last_ctrl, 0, sizeof(Ctrl)) != cudaSuccess ||
             cudaDeviceSynchronize() != cudaSuccess) {
@@ -206,6 +208,18 @@ extern "C" sr_status sr_get_stats(sr_stats *out) {
     CallRecord &r = call_record();
     *out = r.host;
     out->abi_version = SR_ABI_VERSION;
+    if (r.aux_kind) {
+        DeviceState *ds = nullptr;
+        SR_TRY(device_state(&ds));
+        if (cudaStreamSynchronize(r.stream) != cudaSuccess) { cudaGetLastError(); return SR_ERR_CUDA; }
+        unsigned char aux[kAuxBytes];
+        if (cudaMemcpy(aux, ds->last_aux, kAuxBytes, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGetLastError();
+            return SR_ERR_CUDA;
+        }
+        if (r.aux_kind == 3) return segmented_stats(aux, out);
+        if (r.aux_kind == 4) return learned_stats(aux, out);
+    }
     if (!r.has_ctrl) return SR_OK;
     DeviceState *ds = nullptr;
     SR_TRY(device_state(&ds));

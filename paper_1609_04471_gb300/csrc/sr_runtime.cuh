@@ -18,7 +18,9 @@ struct DeviceState {
     cudaMemPool_t pool = nullptr;   // scratch: stream-ordered, kept cached
     int *status = nullptr;          // device status word (sr_status codes)
     Ctrl *last_ctrl = nullptr;      // copy of the last call's control block
+    void *last_aux = nullptr;       // copy of the last segmented / learned call's control block
 };
+constexpr size_t kAuxBytes = 512;
 
 // Per-device state of the current device, created on first use (the first
 // call on a device must not be inside a stream capture).
@@ -41,7 +43,12 @@ struct CallRecord {
     int key_bytes = 4;
     int val_bytes = 0;
     int cur0 = 0;
+    int aux_kind = 0;               // 3: last_aux holds a segmented call's block, 4: a learned call's
 };
+
+// Fill the stats fields of a segmented / learned call from its control block.
+sr_status segmented_stats(const void *aux, sr_stats *out);
+sr_status learned_stats(const void *aux, sr_stats *out);
 CallRecord &call_record();
 
 // Kernel instrumentation: every launch site calls launch_begin / launch_end
