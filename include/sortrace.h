@@ -211,6 +211,7 @@ typedef struct {
     uint64_t max_bucket;        /* learned: largest bucket */
     uint64_t big_segments;      /* segmented: segments longer than one tile */
     float model_loss;           /* learned: training loss after the last step */
+    float bucket_imbalance;     /* learned: B * sum(c_b^2) / n^2 over bucket sizes c_b; 1 = even */
 } sr_stats;
 
 /* sr_get_stats -- waits for the last call's stream and fills *out. */

@@ -9,10 +9,14 @@ namespace sr {
 
 // ------------------------------------------------------------- kernels
 
+// `gate` (optional): when it points at 0 the scan counts nothing, so the call
+// sees a "sorted" input and every later kernel of the sequence returns at once.
 template <int KT, int NT, int IPT>
 __global__ void __launch_bounds__(NT) k_detect(const typename Key<KT>::T *__restrict__ keys,
-                                               long long n, Ctrl *__restrict__ c) {
+                                               long long n, Ctrl *__restrict__ c,
+                                               const int *__restrict__ gate) {
     griddep_wait();
+    if (gate && *gate == 0) return;
     typedef Key<KT> K;
     typedef typename K::U U;
     constexpr int NV = NT * IPT;

@@ -51,7 +51,10 @@ template <int KT, bool VALS> struct PlainSort {
     // Launches the whole sequence on stream s.  The block sort writes to the
     // scratch copy when the number of passes is odd, so the last merge lands in
     // the caller's buffer.
-    sr_status launch(T *uk, uint32_t *uv, unsigned char *scratch, cudaStream_t s) const {
+    // `gate` (optional device flag): when it is 0 at run time the whole
+    // sequence does nothing.
+    sr_status launch(T *uk, uint32_t *uv, unsigned char *scratch, cudaStream_t s,
+                     const int *gate = nullptr) const {
         Ctrl *ctrl = (Ctrl *)(scratch + off_ctrl);
         U *plo = (U *)(scratch + off_plan);
         U *phi = plo + tiles;
@@ -69,7 +72,7 @@ template <int KT, bool VALS> struct PlainSort {
             const size_t det_smem = (size_t)(TS + 1) * sizeof(U);
             if ((st = allow_smem(k_detect<KT, SNT, IPT>, det_smem)) != SR_OK) break;
             SR_LAUNCH(SR_KERNEL_DETECT, (k_detect<KT, SNT, IPT>), (unsigned)tiles, SNT, det_smem, s,
-                      uk, n, ctrl);
+                      uk, n, ctrl, gate);
             SR_LAUNCH(SR_KERNEL_REVERSE, (k_reverse<KT, VALS>), grid_for(n / 2, 256, 152 * 16), 256, 0, s,
                       uk, uv, n, ctrl);
             const size_t bs_smem = (size_t)TS * (sizeof(U) + (VALS ? 4 : 0));

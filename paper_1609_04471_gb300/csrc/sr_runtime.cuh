@@ -20,7 +20,7 @@ struct DeviceState {
     Ctrl *last_ctrl = nullptr;      // copy of the last call's control block
     void *last_aux = nullptr;       // copy of the last segmented / learned call's control block
 };
-constexpr size_t kAuxBytes = 512;
+constexpr size_t kAuxBytes = 2048;
 
 // Per-device state of the current device, created on first use (the first
 // call on a device must not be inside a stream capture).
@@ -45,6 +45,12 @@ struct CallRecord {
     int cur0 = 0;
     int aux_kind = 0;               // 3: last_aux holds a segmented call's block, 4: a learned call's
 };
+
+// The segmented sort from `in` to `out` (in == out: in place), defined in
+// sr_segmented.cu; `record` makes it this thread's last call for sr_get_stats.
+template <int KT>
+sr_status segmented_run(const typename Key<KT>::T *in, typename Key<KT>::T *out, size_t n_keys,
+                        const int64_t *d_off, size_t nseg, cudaStream_t s, bool record);
 
 // Fill the stats fields of a segmented / learned call from its control block.
 sr_status segmented_stats(const void *aux, sr_stats *out);

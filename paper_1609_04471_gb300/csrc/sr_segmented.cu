@@ -239,9 +239,13 @@ __device__ __forceinline__ void sort_range(const typename Key<KT>::T *src, typen
     __syncthreads();
 }
 
+// Reads every segment from `in` and writes it sorted to `out` (in == out sorts
+// in place).  Tiles of big segments that need an odd number of merge passes go
+// to `alt`, the merge passes' other buffer (alt may be in when in != out).
 template <int KT>
 __global__ void __launch_bounds__(SegShape<sizeof(typename Key<KT>::T)>::SNT)
-k_seg_sort(typename Key<KT>::T *keys, typename Key<KT>::T *scratch, const int64_t *__restrict__ off,
+k_seg_sort(const typename Key<KT>::T *in, typename Key<KT>::T *out, typename Key<KT>::T *alt,
+           const int64_t *__restrict__ off,
            long long nchunks, const int *__restrict__ chunk_first, const unsigned int *__restrict__ medium,
            const unsigned int *__restrict__ big, const unsigned int *__restrict__ tile_base,
            SegCtrl *__restrict__ c) {
@@ -316,7 +320,7 @@ k_seg_sort(typename Key<KT>::T *keys, typename Key<KT>::T *scratch, const int64_
 #pragma unroll
             for (int i = 0; i < IPT_P; ++i) {
                 const int pos = t * IPT_P + i;
-                kc[i] = pos < cnt ? CP::make((unsigned int)(before + run[i]), K::ord(keys[g0 + pos]))
+                kc[i] = pos < cnt ? CP::make((unsigned int)(before + run[i]), K::ord(in[g0 + pos]))
                                   : umax_of<C>();
                 dv[i] = 0u;
             }
@@ -325,13 +329,13 @@ k_seg_sort(typename Key<KT>::T *keys, typename Key<KT>::T *scratch, const int64_
 #pragma unroll
             for (int i = 0; i < IPT_P; ++i) sc[t * IPT_P + i] = kc[i];
             __syncthreads();
-            for (int i = t; i < cnt; i += SNT) keys[g0 + i] = K::unord(CP::template key<U>(sc[i]));
+            for (int i = t; i < cnt; i += SNT) out[g0 + i] = K::unord(CP::template key<U>(sc[i]));
             __syncthreads();
         } else if (item < (unsigned long long)nchunks + n_medium) {
             // ---- a medium segment: one block sort in place
             const unsigned int sgi = medium[item - nchunks];
             const long long g0 = off[sgi];
-            sort_range<KT, SNT, IPT>(keys, keys, g0, (int)(off[sgi + 1] - g0), su);
+            sort_range<KT, SNT, IPT>(in, out, g0, (int)(off[sgi + 1] - g0), su);
         } else {
             // ---- one block-sort tile of a big segment
             const unsigned int j = (unsigned int)(item - nchunks - n_medium);
@@ -341,7 +345,7 @@ k_seg_sort(typename Key<KT>::T *keys, typename Key<KT>::T *scratch, const int64_
             const long long g0 = s0 + (long long)(j - tile_base[bi]) * TT;
             const int cnt = (int)min((long long)TT, s0 + len - g0);
             const int passes = dev_ceil_log2((len + TT - 1) / TT);
-            sort_range<KT, SNT, IPT>(keys, (passes & 1) ? scratch : keys, g0, cnt, su);
+            sort_range<KT, SNT, IPT>(in, (passes & 1) ? alt : out, g0, cnt, su);
         }
     }
 }
@@ -349,7 +353,7 @@ k_seg_sort(typename Key<KT>::T *keys, typename Key<KT>::T *scratch, const int64_
 // Merge pass p over the merge tiles of every big segment that needs it.
 template <int KT, int NT, int IPT, bool VEC>
 __global__ void __launch_bounds__(NT)
-k_seg_merge(typename Key<KT>::T *keys, typename Key<KT>::T *scratch, long long nkeys,
+k_seg_merge(typename Key<KT>::T *out, typename Key<KT>::T *alt, long long nkeys,
             const int64_t *__restrict__ off, const unsigned int *__restrict__ big,
             const unsigned int *__restrict__ mtile_base, int tile, int p, SegCtrl *__restrict__ c) {
     griddep_wait();
@@ -376,9 +380,9 @@ k_seg_merge(typename Key<KT>::T *keys, typename Key<KT>::T *scratch, long long n
         const long long pb = (lo0 / (2 * w)) * (2 * w);
         const long long a_beg = s0 + pb, a_end = s0 + min(pb + w, len);
         const long long b_beg = a_end, b_end = s0 + min(pb + 2 * w, len);
-        const int cur = (passes - p) & 1;                             // 1: the data is in scratch
-        const T *src = cur ? scratch : keys;
-        T *dst = cur ? keys : scratch;
+        const int cur = (passes - p) & 1;                             // 1: the data is in alt
+        const T *src = cur ? alt : out;
+        T *dst = cur ? out : alt;
         if (t < 64) {
             const int which = t >> 5;
             const long long out = which ? lo1 : lo0;
@@ -424,7 +428,8 @@ static int sm_count() {
 }
 
 template <int KT>
-static sr_status segmented_impl(void *d_keys, size_t n_keys, const int64_t *d_off, size_t nseg, cudaStream_t s) {
+sr_status segmented_run(const typename Key<KT>::T *in, typename Key<KT>::T *out, size_t n_keys,
+                        const int64_t *d_off, size_t nseg, cudaStream_t s, bool record) {
     typedef Key<KT> K;
     typedef typename K::T T;
     typedef typename K::U U;
@@ -434,7 +439,8 @@ static sr_status segmented_impl(void *d_keys, size_t n_keys, const int64_t *d_of
     constexpr int MNT = SS::MNT, MIPT = SS::MIPT, NV = MNT * MIPT;
     static_assert(TT % NV == 0, "merge tiles must divide the block-sort tile");
 
-    CallRecord &rec = call_record();
+    CallRecord dummy;
+    CallRecord &rec = record ? call_record() : dummy;
     rec = CallRecord();
     rec.host.call = 3;
     rec.host.n = n_keys;
@@ -451,7 +457,8 @@ static sr_status segmented_impl(void *d_keys, size_t n_keys, const int64_t *d_of
     const size_t cb = align_up(sizeof(SegCtrl), 256);
     const size_t fb = align_up((size_t)(nchunks + 2) * 4, 256);
     const size_t lb = align_up((nseg + 1) * 4, 256);
-    const size_t kb = align_up(n_keys * sizeof(T), 256);
+    const bool in_place = (const void *)in == (const void *)out;
+    const size_t kb = in_place ? align_up(n_keys * sizeof(T), 256) : 0;
     void *scratch = nullptr;
     SR_TRY(scratch_alloc(ds, &scratch, cb + fb + 4 * lb + kb, s));
     unsigned char *sp = (unsigned char *)scratch;
@@ -461,9 +468,8 @@ static sr_status segmented_impl(void *d_keys, size_t n_keys, const int64_t *d_of
     unsigned int *big = (unsigned int *)(sp + cb + fb + lb);
     unsigned int *tile_base = (unsigned int *)(sp + cb + fb + 2 * lb);
     unsigned int *mtile_base = (unsigned int *)(sp + cb + fb + 3 * lb);
-    T *sk = (T *)(sp + cb + fb + 4 * lb);
-    T *uk = (T *)d_keys;
-    const bool vec = ((uintptr_t)uk % 16) == 0;
+    T *alt = in_place ? (T *)(sp + cb + fb + 4 * lb) : const_cast<T *>(in);
+    const bool vec = ((uintptr_t)out % 16) == 0 && ((uintptr_t)alt % 16) == 0;
     sr_status st = SR_OK;
     do {
         if (cudaMemsetAsync(ctrl, 0, sizeof(SegCtrl), s) != cudaSuccess) { st = launch_status(); break; }
@@ -476,26 +482,28 @@ static sr_status segmented_impl(void *d_keys, size_t n_keys, const int64_t *d_of
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seg_sort<KT>, SNT, sort_smem);
         const int sort_grid = sm_count() * std::max(per_sm, 1);
-        SR_LAUNCH(SR_KERNEL_SEGMENTED, k_seg_sort<KT>, sort_grid, SNT, sort_smem, s, uk, sk, d_off, nchunks,
-                  chunk_first, medium, big, tile_base, ctrl);
+        SR_LAUNCH(SR_KERNEL_SEGMENTED, k_seg_sort<KT>, sort_grid, SNT, sort_smem, s, in, out, alt, d_off,
+                  nchunks, chunk_first, medium, big, tile_base, ctrl);
         const size_t m_smem = (size_t)(NV + 16) * sizeof(U);
         const int merge_grid = sm_count() * 8;
         for (int p = 0; p < passes_upper; ++p) {
             if (vec) {
-                SR_LAUNCH(SR_KERNEL_MERGE, (k_seg_merge<KT, MNT, MIPT, true>), merge_grid, MNT, m_smem, s, uk, sk,
-                          (long long)n_keys, d_off, big, mtile_base, TT, p, ctrl);
+                SR_LAUNCH(SR_KERNEL_MERGE, (k_seg_merge<KT, MNT, MIPT, true>), merge_grid, MNT, m_smem, s, out,
+                          alt, (long long)n_keys, d_off, big, mtile_base, TT, p, ctrl);
             } else {
-                SR_LAUNCH(SR_KERNEL_MERGE, (k_seg_merge<KT, MNT, MIPT, false>), merge_grid, MNT, m_smem, s, uk,
-                          sk, (long long)n_keys, d_off, big, mtile_base, TT, p, ctrl);
+                SR_LAUNCH(SR_KERNEL_MERGE, (k_seg_merge<KT, MNT, MIPT, false>), merge_grid, MNT, m_smem, s, out,
+                          alt, (long long)n_keys, d_off, big, mtile_base, TT, p, ctrl);
             }
         }
         if (st != SR_OK) break;
         SR_LAUNCH(SR_KERNEL_SEGMENTED, k_seg_finish, 1, 32, 0, s, ctrl, ds->status);
-        if (cudaMemcpyAsync(ds->last_aux, ctrl, sizeof(SegCtrl), cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
-            st = launch_status();
-            break;
+        if (record) {
+            if (cudaMemcpyAsync(ds->last_aux, ctrl, sizeof(SegCtrl), cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+                st = launch_status();
+                break;
+            }
+            rec.aux_kind = 3;
         }
-        rec.aux_kind = 3;
     } while (0);
     scratch_free(scratch, s);
     return st;
@@ -508,14 +516,32 @@ sr_status segmented_stats(const void *aux, sr_stats *out) {
     return SR_OK;
 }
 
+template <int KT>
+static sr_status seg_inplace(void *d_keys, size_t n_keys, const int64_t *d_off, size_t nseg, cudaStream_t s) {
+    typedef typename Key<KT>::T T;
+    return segmented_run<KT>((const T *)d_keys, (T *)d_keys, n_keys, d_off, nseg, s, true);
+}
+
+// instantiations used by the learned sort
+template sr_status segmented_run<SR_KEY_I32>(const uint32_t *, uint32_t *, size_t, const int64_t *, size_t,
+                                             cudaStream_t, bool);
+template sr_status segmented_run<SR_KEY_U32>(const uint32_t *, uint32_t *, size_t, const int64_t *, size_t,
+                                             cudaStream_t, bool);
+template sr_status segmented_run<SR_KEY_F32>(const uint32_t *, uint32_t *, size_t, const int64_t *, size_t,
+                                             cudaStream_t, bool);
+template sr_status segmented_run<SR_KEY_U64>(const unsigned long long *, unsigned long long *, size_t,
+                                             const int64_t *, size_t, cudaStream_t, bool);
+template sr_status segmented_run<SR_KEY_I64>(const unsigned long long *, unsigned long long *, size_t,
+                                             const int64_t *, size_t, cudaStream_t, bool);
+
 static sr_status segmented_dispatch(void *d_keys, size_t n_keys, const int64_t *d_off, size_t nseg,
                                     sr_key_type kt, cudaStream_t s) {
     switch (kt) {
-    case SR_KEY_I32: return segmented_impl<SR_KEY_I32>(d_keys, n_keys, d_off, nseg, s);
-    case SR_KEY_U32: return segmented_impl<SR_KEY_U32>(d_keys, n_keys, d_off, nseg, s);
-    case SR_KEY_F32: return segmented_impl<SR_KEY_F32>(d_keys, n_keys, d_off, nseg, s);
-    case SR_KEY_U64: return segmented_impl<SR_KEY_U64>(d_keys, n_keys, d_off, nseg, s);
-    case SR_KEY_I64: return segmented_impl<SR_KEY_I64>(d_keys, n_keys, d_off, nseg, s);
+    case SR_KEY_I32: return seg_inplace<SR_KEY_I32>(d_keys, n_keys, d_off, nseg, s);
+    case SR_KEY_U32: return seg_inplace<SR_KEY_U32>(d_keys, n_keys, d_off, nseg, s);
+    case SR_KEY_F32: return seg_inplace<SR_KEY_F32>(d_keys, n_keys, d_off, nseg, s);
+    case SR_KEY_U64: return seg_inplace<SR_KEY_U64>(d_keys, n_keys, d_off, nseg, s);
+    case SR_KEY_I64: return seg_inplace<SR_KEY_I64>(d_keys, n_keys, d_off, nseg, s);
     default: return SR_ERR_INVALID_ARG;
     }
 }
