@@ -24,9 +24,49 @@ Input classes (Section 2 of the paper, and the workload descriptions):
 """
 from __future__ import annotations
 
+import ctypes
 import math
+import os
+import subprocess
+import threading
 
 import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "_gen.c")
+_LIB = os.path.join(_HERE, "_build", "libsr_gen.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compiles the multi-threaded fills (_gen.c) with gcc."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=gnu99", "-Wall", "-shared", "-fPIC", "-pthread",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _c():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            u64, sz, vp = ctypes.c_uint64, ctypes.c_size_t, ctypes.c_void_p
+            lib.sg_key.argtypes = [u64, u64]
+            lib.sg_key.restype = u64
+            lib.sg_stream.argtypes = [u64, u64, vp, sz]
+            lib.sg_lognormal.argtypes = [u64, u64, u64, vp, vp, vp, ctypes.c_int, vp, sz]
+            lib.sg_zipf_pairs.argtypes = [u64, u64, u64, vp, sz, vp, sz, sz, vp, vp, vp]
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
 
 _GOLDEN = np.uint64(0x9E3779B97F4A7C15)
 _M1 = np.uint64(0xBF58476D1CE4E5B9)
@@ -47,16 +87,26 @@ def _mix(z: np.ndarray) -> np.ndarray:
     return z ^ (z >> np.uint64(31))
 
 
+def _key(seed: int, stream: str) -> int:
+    """key = mix(seed * golden + tag) of a named stream (64-bit wrap-around)."""
+    tag = _STREAMS[stream]
+    with np.errstate(over="ignore"):
+        return int(_mix(np.array([np.uint64(seed & 0xFFFFFFFFFFFFFFFF) * _GOLDEN + np.uint64(tag)],
+                                 dtype=np.uint64))[0])
+
+
 def u64_stream(seed: int, stream: str, count: int, offset: int = 0) -> np.ndarray:
     """``count`` SplitMix64 outputs of stream ``stream`` starting at counter
     ``offset``: out[i] = mix(key + (offset + i + 1) * golden), where
     key = mix(seed * golden + tag)."""
-    tag = _STREAMS[stream]
+    key = _key(seed, stream)
+    if count >= (1 << 16):
+        out = np.empty(count, dtype=np.uint64)
+        _c().sg_stream(key, offset, _ptr(out), count)
+        return out
     with np.errstate(over="ignore"):
-        key = _mix(np.array([np.uint64(seed & 0xFFFFFFFFFFFFFFFF) * _GOLDEN + np.uint64(tag)],
-                            dtype=np.uint64))[0]
         ctr = np.arange(offset + 1, offset + count + 1, dtype=np.uint64)
-        return _mix(key + ctr * _GOLDEN)
+        return _mix(np.uint64(key) + ctr * _GOLDEN)
 
 
 def _below(u: np.ndarray, m) -> np.ndarray:
@@ -151,27 +201,34 @@ def zipf_cdf(s: float = 1.1, support: int = 1 << 20) -> np.ndarray:
     return c / c[-1]
 
 
-def pairs_u64_zipf(n: int, seed: int = 1, s: float = 1.1, support: int = 1 << 20):
-    """uint64 keys: the first half uniform, the second half Zipf(s) ranks over
-    ``support`` distinct random uint64 values (rank r -> table[r-1]); the two
-    halves are then shuffled together by a seeded random permutation.  The
-    payload is the original index 0..n-1 (uint32)."""
-    nu = n // 2
-    nz = n - nu
-    uni = u64_stream(seed, "u64", nu)
+def zipf_table(seed: int = 1, support: int = 1 << 20) -> np.ndarray:
+    """``support`` distinct random uint64 values in a seeded order; rank r maps
+    to table[r - 1]."""
     table = np.unique(u64_stream(seed, "zipf_table", support + support // 8))
     if table.size < support:
         raise RuntimeError("zipf value table has too many collisions")
-    # a seeded subset of distinct values, in a seeded order
     order = np.argsort(u64_stream(seed, "zipf_table", table.size, offset=1 << 40), kind="stable")
-    table = table[order[:support]]
+    return table[order[:support]]
+
+
+def pairs_u64_zipf(n: int, seed: int = 1, s: float = 1.1, support: int = 1 << 20):
+    """uint64 keys, half uniform and half Zipf(s) over ``support`` distinct
+    random values, in uniformly random order; payload = original index.
+
+    n // 2 positions get uniform keys and the rest Zipf keys (rank by inverse
+    CDF on the cumulative table, in double); the Zipf positions are a
+    uniformly random subset of exactly that size (selection sampling, Knuth's
+    Algorithm S).  As every key is an independent draw, this is the two halves
+    concatenated and shuffled uniformly."""
+    nu = n // 2
+    nz = n - nu
+    table = zipf_table(seed, support)
     cdf = zipf_cdf(s, support)
-    ranks = np.searchsorted(cdf, _unit(u64_stream(seed, "zipf_u", nz)), side="right")
-    ranks = np.minimum(ranks, support - 1)
-    keys = np.concatenate([uni, table[ranks]])
-    perm = np.argsort(u64_stream(seed, "shuffle", n), kind="stable")
-    keys = keys[perm]
-    vals = np.arange(n, dtype=np.uint32)
+    keys = np.empty(n, dtype=np.uint64)
+    vals = np.empty(n, dtype=np.uint32)
+    flags = np.empty(n, dtype=np.uint8)
+    _c().sg_zipf_pairs(_key(seed, "shuffle"), _key(seed, "u64"), _key(seed, "zipf_u"), _ptr(cdf), support,
+                       _ptr(table), n, nz, _ptr(keys), _ptr(vals), _ptr(flags))
     return keys, vals
 
 
@@ -184,16 +241,15 @@ def lognormal_f32(n: int, seed: int = 1, mix=LOGNORMAL_MIX) -> np.ndarray:
     """float32 keys from a lognormal mixture: pick a component by its weight,
     then x = exp(mu + sigma*z), z standard normal by Box-Muller (double), then
     round to float32.  All keys are positive and finite."""
-    c = _unit(u64_stream(seed, "lognormal_c", n))
+    mu = np.array([m[0] for m in mix], dtype=np.float64)
+    sg = np.array([m[1] for m in mix], dtype=np.float64)
     w = np.cumsum([m[2] for m in mix])
-    comp = np.searchsorted(w / w[-1], c, side="right")
-    comp = np.minimum(comp, len(mix) - 1)
-    mu = np.array([m[0] for m in mix])[comp]
-    sg = np.array([m[1] for m in mix])[comp]
-    u1 = _unit(u64_stream(seed, "lognormal_u1", n))
-    u2 = _unit(u64_stream(seed, "lognormal_u2", n))
-    z = np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * np.pi * u2)
-    return np.exp(mu + sg * z).astype(np.float32)
+    cumw = (w / w[-1]).astype(np.float64)
+    out = np.empty(n, dtype=np.float32)
+    if n:
+        _c().sg_lognormal(_key(seed, "lognormal_c"), _key(seed, "lognormal_u1"), _key(seed, "lognormal_u2"),
+                          _ptr(mu), _ptr(sg), _ptr(cumw), len(mix), _ptr(out), n)
+    return out
 
 
 # ------------------------------------------------------- segmented batches
@@ -218,33 +274,46 @@ def segment_lengths(num: int, seed: int = 1, median: float = 512.0,
 def segmented_i32(num: int, seed: int = 1, **kw):
     """A batch of ``num`` int32 arrays stored back to back: returns
     (keys, offsets[num+1] int64, types[num] in 0..3 indexing SEG_TYPES).
-    Each array is drawn from its type's class with a seed derived from the
-    batch seed and the array's index."""
+    Each array follows its type's class, drawn from per-type streams indexed
+    by the global key position: uniform; strictly descending distinct values;
+    ascending distinct values with floor(0.01 len) exchanges; 16 values."""
     lens = segment_lengths(num, seed, **kw)
     types = _below(u64_stream(seed, "seg_type", num), 4)
     off = np.zeros(num + 1, dtype=np.int64)
     np.cumsum(lens, out=off[1:])
-    keys = np.empty(int(off[-1]), dtype=np.int32)
-    for t, kind in enumerate(SEG_TYPES):
-        idx = np.nonzero(types == t)[0]
-        if idx.size == 0:
+    n = int(off[-1])
+    keys = np.empty(n, dtype=np.int32)
+    seg = np.repeat(np.arange(num, dtype=np.int64), lens)
+    t = types[seg]
+    pos = np.nonzero(t == 0)[0]
+    keys[pos] = (u64_stream(seed * 7919 + 1, "uniform", n)[pos] >> np.uint64(32)).astype(np.uint32).view(np.int32)
+    pos = np.nonzero(t == 3)[0]
+    vals = few_unique_values(seed * 7919 + 2)
+    keys[pos] = vals[_below(u64_stream(seed * 7919 + 2, "few_pick", n)[pos], 16)]
+    for ty, stream in ((1, "reversed"), (2, "nearly")):
+        pos = np.nonzero(t == ty)[0]
+        if pos.size == 0:
             continue
-        if kind in ("uniform", "few_unique"):
-            # one long draw, cut into the arrays of this type
-            tot = int(lens[idx].sum())
-            sub = (uniform_i32(tot, seed * 7919 + 1) if kind == "uniform"
-                   else few_unique_i32(tot, seed * 7919 + 2))
-            pos = 0
-            for s in idx.tolist():
-                L = int(lens[s])
-                keys[off[s]:off[s] + L] = sub[pos:pos + L]
-                pos += L
-        else:
-            for s in idx.tolist():
-                L = int(lens[s])
-                sub_seed = (seed << 20) + s
-                keys[off[s]:off[s] + L] = (reversed_i32(L, sub_seed) if kind == "reversed"
-                                           else nearly_sorted_i32(L, sub_seed))
+        s_of = seg[pos]
+        L = lens[s_of]
+        i = pos - off[s_of]
+        q = (np.int64(1) << 32) // L
+        r = _below(u64_stream(seed * 7919 + 3 + ty, stream, n)[pos], np.minimum(q, (1 << 32) - 1))
+        r = np.where(q > 1, r, 0)
+        j = (L - 1 - i) if ty == 1 else i
+        keys[pos] = (-(1 << 31) + j * q + r).astype(np.int32)
+    # nearly sorted: floor(0.01 len) exchanges inside each such array, in order
+    near = np.nonzero(types == 2)[0]
+    m = np.floor(0.01 * lens[near]).astype(np.int64)
+    tot = int(m.sum())
+    if tot:
+        u = u64_stream(seed * 7919 + 5, "nearly_swap", 2 * tot)
+        segs = np.repeat(near, m)
+        base = off[segs]
+        Ls = lens[segs]
+        ii = base + _below(u[0::2], Ls)
+        jj = base + _below(u[1::2], Ls)
+        _apply_swaps(keys, ii, jj)
     return keys, off, types
 
 
