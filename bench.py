@@ -48,6 +48,8 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-sweep", action="store_true", help="skip the 2^24..2^28 size sweep")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the pairs / learned / batched measurements")
     ap.add_argument("--profile-case", type=int, default=0, metavar="LOG2N",
                     help="for ncu: sort a uniform int32 array of 2^LOG2N keys twice (warm-up + one) and exit")
     ap.add_argument("--profile-pairs", action="store_true",
@@ -348,6 +350,9 @@ def run_ours(args):
     sweep = None
     if not args.no_sweep:
         sweep = _sweep(sr, torch, dev, stream, peak)
+    forms = None
+    if not args.no_forms and rank == 0:
+        forms = _forms(sr, torch, dev, stream, peak)
 
     cpu = None
     if rank == 0:
@@ -371,6 +376,8 @@ def run_ours(args):
         }
         if sweep is not None:
             line["sweep"] = sweep
+        if forms is not None:
+            line["forms"] = forms
         print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -431,6 +438,112 @@ def run_profile_case(args):
             sr.sort_keys(x)
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": args.profile_case, "pairs": bool(args.profile_pairs), "ok": True}))
+
+
+def _timed(torch, stream, fn, restore, reps):
+    """Best device time (ms) of fn() over reps runs, each after restore()
+    (the restore is not timed) and an L2 flush."""
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    best = None
+    for r in range(reps + 1):
+        restore()
+        flush.fill_(r & 0xFF)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if r:
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+    return best
+
+
+def _forms(sr, torch, dev, stream, peak):
+    """The other forms of the sort on their own workloads:
+    pairs    2^28 stable uint64-key + uint32-payload sort (half uniform, half
+             Zipf 1.1 over 2^20 values);
+    learned  2^27 float32 keys of the lognormal mixture, learned partition
+             against the plain sort on the same input (and the model-free
+             equal-width ablation);
+    batched  200,000 int32 arrays (lognormal lengths, median 512, four
+             classes), the segmented sort replayed from a captured CUDA graph,
+             against one plain sort call per array (on the first 2,000 arrays,
+             scaled per key)."""
+    import numpy as np
+    import sortrace_inputs as si
+    out = {}
+    # pairs
+    k, v = si.pairs_u64_zipf(1 << 28, SEED)
+    pk = torch.from_numpy(k.view(np.int64)).to(dev)
+    pv = torch.from_numpy(v.view(np.int32)).to(dev)
+    del k, v
+    wk, wv = torch.empty_like(pk), torch.empty_like(pv)
+    ms = _timed(torch, stream, lambda: sr.sort_pairs(wk, wv, key_type=sr.KEY_U64),
+                lambda: (wk.copy_(pk), wv.copy_(pv)), 2)
+    st = sr.stats()
+    n = 1 << 28
+    out["pairs_2^28_u64_u32"] = {"ms": ms, "gkeys_s": n / (ms / 1e3) / 1e9,
+                                 "passes_frac": st["bytes_moved"] / (ms / 1e3) / 1e9 / peak,
+                                 "lower_bound_frac": 24 * n / (ms / 1e3) / 1e9 / peak}
+    del pk, pv, wk, wv
+    torch.cuda.empty_cache()
+    # learned vs plain
+    a = si.lognormal_f32(1 << 27, SEED)
+    src = torch.from_numpy(a).to(dev)
+    del a
+    x = torch.empty_like(src)
+    n = 1 << 27
+    plain = _timed(torch, stream, lambda: sr.sort_keys(x), lambda: x.copy_(src), 3)
+    learned = _timed(torch, stream, lambda: sr.sort_keys_learned(x), lambda: x.copy_(src), 3)
+    stl = sr.stats()
+    ew = _timed(torch, stream, lambda: sr.sort_keys_learned(x, model=sr.MODEL_EQUAL_WIDTH), lambda: x.copy_(src), 2)
+    ste = sr.stats()
+    out["learned_2^27_f32_lognormal"] = {
+        "plain_ms": plain, "learned_ms": learned, "equal_width_ms": ew,
+        "plain_gkeys_s": n / (plain / 1e3) / 1e9, "learned_gkeys_s": n / (learned / 1e3) / 1e9,
+        "learned_over_plain": plain / learned,
+        "fallback": stl["fallback"], "model_loss": stl["model_loss"],
+        "bucket_imbalance": stl["bucket_imbalance"], "bucket_imbalance_equal_width": ste["bucket_imbalance"],
+        "max_bucket": stl["max_bucket"]}
+    del src, x
+    torch.cuda.empty_cache()
+    # batched segmented vs per-array
+    keys, off, _ = si.segmented_i32(200_000, SEED)
+    n = int(off[-1])
+    src = torch.from_numpy(keys).to(dev)
+    toff = torch.from_numpy(off).to(dev)
+    x = torch.empty_like(src)
+    x.copy_(src)
+    sr.sort_segmented_ex(x, toff)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    cs = torch.cuda.Stream()
+    with torch.cuda.stream(cs):
+        with torch.cuda.graph(g, stream=cs):
+            sr.sort_segmented_ex(x, toff)
+    torch.cuda.synchronize()
+    graph_ms = _timed(torch, stream, g.replay, lambda: x.copy_(src), 3)
+    eager_ms = _timed(torch, stream, lambda: sr.sort_segmented_ex(x, toff), lambda: x.copy_(src), 3)
+    sts = sr.stats()
+    sample = 2000
+    views = [x[int(off[i]):int(off[i + 1])] for i in range(sample)]
+    sample_keys = int(off[sample])
+
+    def per_array():
+        for v in views:
+            sr.sort_keys(v)
+    per_ms = _timed(torch, stream, per_array, lambda: x.copy_(src), 2)
+    out["batched_200k_arrays_i32"] = {
+        "keys": n, "graph_ms": graph_ms, "eager_ms": eager_ms,
+        "graph_gkeys_s": n / (graph_ms / 1e3) / 1e9,
+        "per_array_sample_arrays": sample, "per_array_sample_keys": sample_keys, "per_array_ms": per_ms,
+        "per_array_gkeys_s": sample_keys / (per_ms / 1e3) / 1e9,
+        "batched_over_per_array": (n / graph_ms) / (sample_keys / per_ms),
+        "big_segments": sts["big_segments"]}
+    del g
+    return out
 
 
 def main():
