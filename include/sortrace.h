@@ -148,8 +148,8 @@ sr_status sr_sort_keys_noalloc(void *d_keys, size_t n, sr_key_type kt, sr_stream
 typedef struct {
     uint32_t num_buckets;    /* power of two in [2^4, 2^20]; default 2^16 */
     uint32_t sample_stride;  /* one key in sample_stride is sampled; default 100 */
-    uint32_t train_points;   /* points of the sorted sample used in training; default 16384 */
-    uint32_t train_steps;    /* full-batch Adam steps; default 100 */
+    uint32_t train_points;   /* points of the sorted sample used in training; default 4096 */
+    uint32_t train_steps;    /* full-batch Adam steps; default 24 */
     float learning_rate;     /* Adam step size; default 3e-3 */
     uint32_t model;          /* SR_MODEL_* */
 } sr_learned_opts;
@@ -167,6 +167,7 @@ enum {
  * sample of the input, scattering them, sorting each bucket, and checking
  * that every bucket's largest key is <= the next bucket's smallest; if the
  * check fails the plain sort runs instead (the fallback is in stats.fallback).
+ * The call reads the check's verdict back, so it waits for `stream` once.
  * The paper has no learned component; this is the partition-then-sort form of
  * its quicksort (Section 4: split by pivots, then sort the parts), with the
  * pivots read off a learned CDF.

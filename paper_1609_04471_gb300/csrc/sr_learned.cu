@@ -3,21 +3,23 @@
 //
 // The paper has no learned component; this is the split-then-sort-the-parts
 // shape of its quicksort (Section 4) with the split points read off a small
-// monotone network that predicts each key's CDF.  Launch sequence, all on the
-// caller's stream, nothing read back to the host:
+// monotone network that predicts each key's CDF.  Launch sequence, on the
+// caller's stream:
 //
 //   k_sample      every stride-th key's order image -> sample
 //   (plain sort)  the sample, sorted as unsigned order images
 //   k_train       one CTA: training points = quantiles of the sorted sample,
 //                 quantile start, full-batch Adam steps (forward + backward),
 //                 then the routing tables
-//   k_hist        bucket of every key -> histogram
-//   k_bucket_scan bucket offsets, largest bucket
-//   k_scatter     every key to its bucket (scratch)
-//   (segmented)   every bucket sorted, scratch -> caller's buffer
+//   two-level split of the bucket id (coarse digit, then fine digit): per
+//                 level k_split_tiles, k_split_hist (shared-memory counts per
+//                 tile), k_scan_* (positions), k_split_scatter
+//   (segmented)   every bucket sorted, one CTA per bucket, scratch -> the
+//                 caller's buffer
 //   k_bucket_check every bucket's last key <= the next bucket's first key;
 //                 else the fallback flag is set
-//   (plain sort)  gated by that flag: runs only if the check failed
+//   (plain sort)  only if the check failed (the flag is read back: this call
+//                 waits for its stream once)
 //
 // The network (H = 32 hidden units; theta = [x0, delta[H], beta[H]]):
 //   d_j = softplus(delta_j), x_j = x0 + sum_{i<j} d_i, h_j = ramp((x - x_j)/d_j),
@@ -96,6 +98,54 @@ __device__ __forceinline__ int segment_of(const float *knot, float x) {
     return lo;
 }
 
+// Routing state a CTA keeps in shared memory: per segment k the float4
+// (x_k, 1/d_k, w_k, P_k), and the interior knots for the search.
+struct RouteSmem {
+    float4 seg[H];
+    float knot[H + 1];
+    unsigned long long lo;
+    float inv_span;
+    int model, nbuckets;
+};
+
+__device__ __forceinline__ void load_route(const Router &r, RouteSmem &rs) {
+    const int t = threadIdx.x;
+    if (t < H) rs.seg[t] = make_float4(r.knot[t], r.invd[t], r.w[t], r.P[t]);
+    if (t <= H) rs.knot[t] = r.knot[t];
+    if (t == 0) { rs.lo = r.lo; rs.inv_span = r.inv_span; rs.model = r.model; rs.nbuckets = r.nbuckets; }
+}
+
+// The same bucket as route_bucket (same operations in the same order), with
+// the segment found by an unrolled branch-free search and one 128-bit load.
+__device__ __forceinline__ int route_fast(const RouteSmem &rs, float x) {
+    float y;
+    if (rs.model == SR_MODEL_EQUAL_WIDTH) {
+        y = x;
+    } else {
+        int k = 0;                                   // largest k in [0, H-1] with x_k <= x
+#pragma unroll
+        for (int step = H / 2; step >= 1; step >>= 1) k += (rs.knot[k + step] <= x) ? step : 0;
+        const float4 g = rs.seg[k];
+        const float u = fminf(fmaxf(__fmul_rn(__fsub_rn(x, g.x), g.y), 0.f), 1.f);
+        y = __fmaf_rn(g.z, u, g.w);
+    }
+    const float yb = __fmul_rn(y, (float)rs.nbuckets);
+    int b = yb > 0.f ? (int)fminf(yb, (float)(rs.nbuckets - 1)) : 0;
+    if (b > rs.nbuckets - 1) b = rs.nbuckets - 1;
+    if (rs.model == SR_MODEL_FORCE_BAD) b = rs.nbuckets - 1 - b;
+    return b;
+}
+
+template <int KT>
+__device__ __forceinline__ float norm_key(typename Key<KT>::T key, const RouteSmem &rs) {
+    if (sizeof(typename Key<KT>::U) == 4) {
+        const uint32_t u = (uint32_t)Key<KT>::ord(key), lo = (uint32_t)rs.lo;
+        const float d = u >= lo ? __uint2float_rn(u - lo) : -__uint2float_rn(lo - u);
+        return __fmul_rn(d, rs.inv_span);
+    }
+    return norm_x((unsigned long long)Key<KT>::ord(key), rs.lo, rs.inv_span);
+}
+
 __device__ __forceinline__ int route_bucket(const Router &r, float x) {
     float y;
     if (r.model == SR_MODEL_EQUAL_WIDTH) {
@@ -118,7 +168,9 @@ struct Derived {
     float knot[H + 1], P[H + 1];
 };
 
-__device__ void derive(const float *theta, Derived &dv, int lane) {
+// `exact`: the knots and P as sequential float sums (what routing needs);
+// otherwise warp scans (the training steps, where only the gradient matters).
+__device__ void derive(const float *theta, Derived &dv, int lane, bool exact = true) {
     const float delta = theta[1 + lane], beta = theta[1 + H + lane];
     const float d = softplus_f(delta);
     dv.d[lane] = d;
@@ -131,6 +183,18 @@ __device__ void derive(const float *theta, Derived &dv, int lane) {
     for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     dv.w[lane] = e / sum;
     __syncwarp();
+    if (!exact) {
+        float xs = d, ps = dv.w[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const float a = __shfl_up_sync(0xffffffffu, xs, o), b = __shfl_up_sync(0xffffffffu, ps, o);
+            if (lane >= o) { xs += a; ps += b; }
+        }
+        dv.knot[lane] = theta[0] + xs - d;
+        dv.P[lane] = ps - dv.w[lane];
+        if (lane == 31) { dv.knot[H] = theta[0] + xs; dv.P[H] = ps; }
+        __syncwarp();
+        return;
+    }
     if (lane == 0) {
         // sequential float sums: the knots must not decrease and P must satisfy
         // P_{j+1} = fl(P_j + w_j) exactly (the monotonicity argument above)
@@ -222,9 +286,10 @@ k_train(const U *__restrict__ sample, long long m, float *__restrict__ px, float
     const long long p0 = min(S, (long long)t * ppt), p1 = min(S, p0 + ppt);
     const int total_steps = mode == TRAIN_GRAD ? 1 : steps + 1;   // the last pass only measures the loss
 
+    float b1t = 1.f, b2t = 1.f;                    // running powers of Adam's betas
+    if (wid == 0) derive(th, dv, lane, false);
+    __syncthreads();
     for (int it = 0; it < total_steps; ++it) {
-        if (wid == 0) derive(th, dv, lane);
-        __syncthreads();
         // forward and backward over this thread's (sorted) points
         float loss = 0.f, gw = 0.f, gs = 0.f, gkn = 0.f, gd = 0.f;
         int kc = -1;
@@ -295,12 +360,16 @@ k_train(const U *__restrict__ sample, long long m, float *__restrict__ px, float
             } else {
                 // Adam (Kingma and Ba, 2015), bias-corrected
                 const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-                const float c1 = 1.f - powf(b1, (float)(it + 1)), c2 = 1.f - powf(b2, (float)(it + 1));
+                b1t *= b1;
+                b2t *= b2;
+                const float c1 = 1.f - b1t, c2 = 1.f - b2t;
                 for (int q = lane; q < NPARAM; q += 32) {
                     am[q] = b1 * am[q] + (1.f - b1) * gr[q];
                     av[q] = b2 * av[q] + (1.f - b2) * gr[q] * gr[q];
                     th[q] -= lr * (am[q] / c1) / (sqrtf(av[q] / c2) + eps);
                 }
+                __syncwarp();
+                derive(th, dv, lane, false);       // the next step's tables
             }
             acc_w[lane] = 0.f; acc_s[lane] = 0.f; acc_kn[lane] = 0.f; acc_d[lane] = 0.f;
             if (lane == 0) s_loss = 0.f;
@@ -333,109 +402,364 @@ __global__ void k_sample(const typename Key<KT>::T *__restrict__ keys, long long
     if (i < m) sample[i] = Key<KT>::ord(keys[i * stride]);
 }
 
-template <int KT>
-__global__ void k_hist(const typename Key<KT>::T *__restrict__ keys, long long n, const LearnCtrl *__restrict__ lc,
-                       unsigned int *__restrict__ hist) {
-    griddep_wait();
-    __shared__ Router r;
-    if (threadIdx.x < sizeof(Router) / 4) ((uint32_t *)&r)[threadIdx.x] = ((const uint32_t *)&lc->r)[threadIdx.x];
-    __syncthreads();
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const float x = norm_x((unsigned long long)Key<KT>::ord(keys[i]), r.lo, r.inv_span);
-        atomicAdd(&hist[route_bucket(r, x)], 1u);
-    }
-}
+// ----------------------------------------------------- two-level split
+//
+// A key's bucket b (0 .. B-1) is split into two digits, b >> s2 and
+// b & (D2 - 1).  Each level moves every key once: tiles of SPLIT_T keys of
+// the level's input segments count their keys per digit in shared memory, one
+// exclusive scan over (segment, digit, tile) turns the counts into output
+// positions, and the tiles move their keys to those positions, taking slots
+// from shared-memory counters.  Level 1 has one segment (the whole input) and
+// produces D1 coarse buckets; level 2 splits every coarse bucket into D2 fine
+// ones, which are the buckets.  No key needs a global atomic.
+constexpr int SPLIT_T = 8192;
+constexpr int SPLIT_NT = 512;
+constexpr int SPLIT_BATCH = 8;
+constexpr int SCAN_PER_CTA = 8192;
 
-// Every key to the next free slot of its bucket.  A slot beyond the bucket's
-// end (impossible while routing is deterministic) is not written; it raises
-// the fallback flag and SR_ERR_INTERNAL in the status word instead.
-template <int KT>
-__global__ void k_scatter(const typename Key<KT>::T *__restrict__ keys, long long n,
-                          LearnCtrl *__restrict__ lc, unsigned long long *__restrict__ cursor,
-                          const long long *__restrict__ off, typename Key<KT>::T *__restrict__ out,
-                          int *__restrict__ status_word) {
-    griddep_wait();
-    __shared__ Router r;
-    if (threadIdx.x < sizeof(Router) / 4) ((uint32_t *)&r)[threadIdx.x] = ((const uint32_t *)&lc->r)[threadIdx.x];
-    __syncthreads();
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const typename Key<KT>::T key = keys[i];
-        const float x = norm_x((unsigned long long)Key<KT>::ord(key), r.lo, r.inv_span);
-        const int b = route_bucket(r, x);
-        const unsigned long long pos = atomicAdd(&cursor[b], 1ull);
-        if (pos < (unsigned long long)off[b + 1]) {
-            out[pos] = key;
-        } else {
-            atomicExch(&lc->fallback, 1);
-            atomicExch(status_word, (int)SR_ERR_INTERNAL);
-        }
-    }
-}
-
-// Exclusive scan of the histogram into offsets (one CTA); off[nb] = n.
+// Tile table of a level (one CTA; at most 1024 segments): tile_base[s] = first
+// tile of segment s, tile_base[S] = number of tiles; tile_seg / tile_local
+// give every tile's segment and its index inside the segment.
 __global__ void __launch_bounds__(1024)
-k_bucket_scan(const unsigned int *__restrict__ hist, int nb, long long n, long long *__restrict__ off,
-              unsigned long long *__restrict__ cursor, LearnCtrl *__restrict__ lc) {
+k_split_tiles(const long long *__restrict__ seg_off, int S, int *__restrict__ tile_base, int *__restrict__ tile_seg,
+              int *__restrict__ tile_local) {
     griddep_wait();
-    __shared__ unsigned long long s_warp[32];
-    __shared__ unsigned int s_max;
-    __shared__ unsigned long long s_sq;
+    __shared__ int s_warp[32];
+    __shared__ int s_cnt[1024];
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    const int per = (nb + 1023) / 1024;
-    const int b0 = min(nb, t * per), b1 = min(nb, b0 + per);
-    unsigned long long sum = 0, sq = 0;
-    unsigned int mx = 0;
-    for (int b = b0; b < b1; ++b) {
-        const unsigned long long h = hist[b];
-        sum += h;
-        sq += h * h;
-        mx = max(mx, hist[b]);
-    }
-    if (t == 0) { s_max = 0; s_sq = 0; }
-    unsigned long long x = sum;
+    const int cnt = t < S ? (int)((seg_off[t + 1] - seg_off[t] + SPLIT_T - 1) / SPLIT_T) : 0;
+    int x = cnt;
     for (int d = 1; d < 32; d <<= 1) {
-        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, d);
+        const int y = __shfl_up_sync(0xffffffffu, x, d);
         if (lane >= d) x += y;
     }
     if (lane == 31) s_warp[wid] = x;
     __syncthreads();
     if (wid == 0) {
-        unsigned long long w = s_warp[lane];
+        int w = s_warp[lane];
         for (int d = 1; d < 32; d <<= 1) {
-            const unsigned long long y = __shfl_up_sync(0xffffffffu, w, d);
+            const int y = __shfl_up_sync(0xffffffffu, w, d);
             if (lane >= d) w += y;
         }
         s_warp[lane] = w;
     }
-    atomicMax(&s_max, mx);
-    atomicAdd(&s_sq, sq);
     __syncthreads();
-    unsigned long long run = (wid ? s_warp[wid - 1] : 0ull) + x - sum;
-    for (int b = b0; b < b1; ++b) {
-        off[b] = (long long)run;
-        cursor[b] = run;
-        run += hist[b];
-    }
-    if (t == 0) {
-        off[nb] = n;
-        lc->max_bucket = s_max;
-        lc->bucket_sq = s_sq;
-        lc->nkeys = (unsigned long long)n;
-        lc->nbuckets = nb;
+    const int before = (wid ? s_warp[wid - 1] : 0) + x - cnt;
+    s_cnt[t] = before;
+    if (t < S) tile_base[t] = before;
+    if (t == S - 1) tile_base[S] = before + cnt;
+    __syncthreads();
+    for (int q = 0; q < S; ++q) {
+        const int base = s_cnt[q];
+        const int c = (q + 1 < S ? s_cnt[q + 1] : s_warp[31]) - base;
+        for (int tl = t; tl < c; tl += blockDim.x) { tile_seg[base + tl] = q; tile_local[base + tl] = tl; }
     }
 }
 
+__device__ __forceinline__ int digit_of(int b, int level, int s2, int mask2) {
+    return level == 1 ? (b >> s2) : (b & mask2);
+}
+
+// Level 1 counts: routes every key once, writes its bucket id (BT) beside it
+// and counts the coarse digit per tile.  Level 2 counts: reads the ids only.
+template <int KT, typename BT>
+__global__ void __launch_bounds__(SPLIT_NT)
+k_split_hist(const typename Key<KT>::T *__restrict__ in, const BT *__restrict__ bid_in, BT *__restrict__ bid_out,
+             const long long *__restrict__ seg_off, int S, const int *__restrict__ tile_base,
+             const int *__restrict__ tile_seg, const int *__restrict__ tile_local, int level, int D, int s2,
+             const LearnCtrl *__restrict__ lc, unsigned int *__restrict__ counts) {
+    griddep_wait();
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned int *hist = reinterpret_cast<unsigned int *>(smem);
+    __shared__ RouteSmem rs;
+    const int tile = blockIdx.x;
+    if (tile >= tile_base[S]) return;
+    if (level == 1) load_route(lc->r, rs);
+    for (int d = threadIdx.x; d < D; d += SPLIT_NT) hist[d] = 0u;
+    __syncthreads();
+    const int s = tile_seg[tile], tl = tile_local[tile];
+    const int nt = tile_base[s + 1] - tile_base[s];
+    const long long start = seg_off[s] + (long long)tl * SPLIT_T;
+    const long long end = min(start + SPLIT_T, seg_off[s + 1]);
+    const int mask2 = (1 << s2) - 1;
+    for (long long i0 = start + threadIdx.x; i0 < end; i0 += (long long)SPLIT_NT * SPLIT_BATCH) {
+        const bool full = i0 + (long long)(SPLIT_BATCH - 1) * SPLIT_NT < end;
+        if (level == 1) {
+            typename Key<KT>::T k[SPLIT_BATCH];
+#pragma unroll
+            for (int j = 0; j < SPLIT_BATCH; ++j) {
+                const long long i = i0 + (long long)j * SPLIT_NT;
+                k[j] = (full || i < end) ? in[i] : typename Key<KT>::T(0);
+            }
+#pragma unroll
+            for (int j = 0; j < SPLIT_BATCH; ++j) {
+                const long long i = i0 + (long long)j * SPLIT_NT;
+                if (full || i < end) {
+                    const int b = route_fast(rs, norm_key<KT>(k[j], rs));
+                    bid_out[i] = (BT)b;
+                    atomicAdd(&hist[b >> s2], 1u);
+                }
+            }
+        } else {
+            BT bb[SPLIT_BATCH];
+#pragma unroll
+            for (int j = 0; j < SPLIT_BATCH; ++j) {
+                const long long i = i0 + (long long)j * SPLIT_NT;
+                bb[j] = (full || i < end) ? bid_in[i] : BT(0);
+            }
+#pragma unroll
+            for (int j = 0; j < SPLIT_BATCH; ++j)
+                if (full || i0 + (long long)j * SPLIT_NT < end) atomicAdd(&hist[(int)bb[j] & mask2], 1u);
+        }
+    }
+    __syncthreads();
+    const long long base_e = (long long)D * tile_base[s];
+    for (int d = threadIdx.x; d < D; d += SPLIT_NT) counts[base_e + (long long)d * nt + tl] = hist[d];
+}
+
+// Moves one tile's keys (and, at level 1, their bucket ids) to the level's
+// output: first into shared memory grouped by digit (the tile's own counts,
+// scanned, give each digit's stretch; a shared counter hands out slots), then
+// out with every digit's stretch written contiguously at its scanned position.
+template <int KT, typename BT>
+__global__ void __launch_bounds__(SPLIT_NT)
+k_split_scatter(const typename Key<KT>::T *__restrict__ in, const BT *__restrict__ bid_in,
+                typename Key<KT>::T *__restrict__ out, BT *__restrict__ bid_out, const long long *__restrict__ seg_off,
+                int S, const int *__restrict__ tile_base, const int *__restrict__ tile_seg,
+                const int *__restrict__ tile_local, int level, int D, int s2, LearnCtrl *__restrict__ lc,
+                const unsigned int *__restrict__ counts, const unsigned long long *__restrict__ pos,
+                int *__restrict__ status_word) {
+    griddep_wait();
+    typedef typename Key<KT>::T T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T *stage_k = reinterpret_cast<T *>(smem);                                       // [SPLIT_T]
+    unsigned long long *gbase = reinterpret_cast<unsigned long long *>(stage_k + SPLIT_T);   // [D]
+    unsigned int *tstart = reinterpret_cast<unsigned int *>(gbase + D);             // [D + 1]
+    unsigned int *taken = tstart + D + 1;                                           // [D]
+    BT *stage_b = reinterpret_cast<BT *>(taken + D);                                // [SPLIT_T]
+    __shared__ unsigned int s_warp[32];
+    const int tile = blockIdx.x;
+    if (tile >= tile_base[S]) return;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int s = tile_seg[tile], tl = tile_local[tile];
+    const int nt = tile_base[s + 1] - tile_base[s];
+    const long long base_e = (long long)D * tile_base[s];
+    // exclusive scan of this tile's counts over the digits (D <= 1024, two per thread)
+    const int d0 = 2 * t, d1 = 2 * t + 1;
+    const unsigned int c0 = d0 < D ? counts[base_e + (long long)d0 * nt + tl] : 0u;
+    const unsigned int c1 = d1 < D ? counts[base_e + (long long)d1 * nt + tl] : 0u;
+    unsigned int x = c0 + c1;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned int w = lane < SPLIT_NT / 32 ? s_warp[lane] : 0u;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        s_warp[lane] = w;
+    }
+    __syncthreads();
+    const unsigned int before = (wid ? s_warp[wid - 1] : 0u) + x - (c0 + c1);
+    if (d0 < D) { tstart[d0] = before; taken[d0] = 0u; gbase[d0] = pos[base_e + (long long)d0 * nt + tl]; }
+    if (d1 < D) { tstart[d1] = before + c0; taken[d1] = 0u; gbase[d1] = pos[base_e + (long long)d1 * nt + tl]; }
+    if (t == 0) tstart[D] = s_warp[SPLIT_NT / 32 - 1];
+    __syncthreads();
+    const long long start = seg_off[s] + (long long)tl * SPLIT_T;
+    const long long end = min(start + SPLIT_T, seg_off[s + 1]);
+    const int cnt = (int)(end - start);
+    const int mask2 = (1 << s2) - 1;
+    for (int i0 = t; i0 < cnt; i0 += SPLIT_NT * SPLIT_BATCH) {
+        const bool full = i0 + (SPLIT_BATCH - 1) * SPLIT_NT < cnt;
+        T k[SPLIT_BATCH];
+        BT bb[SPLIT_BATCH];
+#pragma unroll
+        for (int j = 0; j < SPLIT_BATCH; ++j) {
+            const int i = i0 + j * SPLIT_NT;
+            if (full || i < cnt) { k[j] = in[start + i]; bb[j] = bid_in[start + i]; }
+        }
+#pragma unroll
+        for (int j = 0; j < SPLIT_BATCH; ++j) {
+            if (full || i0 + j * SPLIT_NT < cnt) {
+                const int d = level == 1 ? ((int)bb[j] >> s2) : ((int)bb[j] & mask2);
+                const unsigned int q = tstart[d] + atomicAdd(&taken[d], 1u);
+                if (q < tstart[d + 1]) {
+                    stage_k[q] = k[j];
+                    stage_b[q] = bb[j];
+                } else {
+                    // impossible: the counts came from the same ids
+                    atomicExch(&lc->fallback, 1);
+                    atomicExch(status_word, (int)SR_ERR_INTERNAL);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int q = t; q < cnt; q += SPLIT_NT) {
+        const BT b = stage_b[q];
+        const int d = level == 1 ? ((int)b >> s2) : ((int)b & mask2);
+        const unsigned long long g = gbase[d] + (q - tstart[d]);
+        out[g] = stage_k[q];
+        if (level == 1) bid_out[g] = b;
+    }
+}
+
+// Exclusive scan of counts[0 .. E) into pos[0 .. E] (pos[E] = total), in three
+// kernels: per-CTA sums, a scan of the sums, per-CTA rescans.
+__global__ void __launch_bounds__(1024)
+k_scan_sums(const unsigned int *__restrict__ counts, const int *__restrict__ tile_base, int S, int D,
+            unsigned long long *__restrict__ sums) {
+    griddep_wait();
+    __shared__ unsigned long long s_w[32];
+    const long long E = (long long)D * tile_base[S];
+    const long long e0 = (long long)blockIdx.x * SCAN_PER_CTA;
+    if (e0 >= E) return;
+    unsigned long long v = 0;
+    for (long long e = e0 + threadIdx.x; e < min(E, e0 + SCAN_PER_CTA); e += blockDim.x) v += counts[e];
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        v = s_w[threadIdx.x];
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) sums[blockIdx.x] = v;
+    }
+}
+
+__global__ void __launch_bounds__(1024)
+k_scan_top(unsigned long long *__restrict__ sums, const int *__restrict__ tile_base, int S, int D) {
+    griddep_wait();
+    __shared__ unsigned long long s_w[32];
+    __shared__ unsigned long long s_carry;
+    const long long E = (long long)D * tile_base[S];
+    const long long nb = (E + SCAN_PER_CTA - 1) / SCAN_PER_CTA;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    if (t == 0) s_carry = 0;
+    __syncthreads();
+    for (long long b0 = 0; b0 < nb; b0 += 1024) {
+        const long long i = b0 + t;
+        const unsigned long long v = i < nb ? sums[i] : 0ull;
+        unsigned long long x = v;
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += y;
+        }
+        if (lane == 31) s_w[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            unsigned long long w = s_w[lane];
+            for (int d = 1; d < 32; d <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, w, d);
+                if (lane >= d) w += y;
+            }
+            s_w[lane] = w;
+        }
+        __syncthreads();
+        const unsigned long long excl = s_carry + (wid ? s_w[wid - 1] : 0ull) + x - v;
+        if (i < nb) sums[i] = excl;
+        __syncthreads();
+        if (t == 0) s_carry += s_w[31];
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(1024)
+k_scan_apply(const unsigned int *__restrict__ counts, const int *__restrict__ tile_base, int S, int D,
+             const unsigned long long *__restrict__ sums, unsigned long long *__restrict__ pos) {
+    griddep_wait();
+    __shared__ unsigned long long s_w[32];
+    constexpr int PER = SCAN_PER_CTA / 1024;
+    const long long E = (long long)D * tile_base[S];
+    const long long e0 = (long long)blockIdx.x * SCAN_PER_CTA;
+    if (e0 >= E) return;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    unsigned long long v[PER], run = 0;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const long long e = e0 + (long long)t * PER + j;
+        v[j] = e < E ? counts[e] : 0u;
+        run += v[j];
+    }
+    unsigned long long x = run;
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) s_w[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned long long w = s_w[lane];
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, w, d);
+            if (lane >= d) w += y;
+        }
+        s_w[lane] = w;
+    }
+    __syncthreads();
+    unsigned long long p = sums[blockIdx.x] + (wid ? s_w[wid - 1] : 0ull) + x - run;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const long long e = e0 + (long long)t * PER + j;
+        if (e < E) pos[e] = p;
+        p += v[j];
+    }
+    if (e0 + SCAN_PER_CTA >= E && t == 1023) pos[E] = p;     // the block holding the last entry
+}
+
+__global__ void k_whole_range(long long *__restrict__ seg_off, long long n) {
+    griddep_wait();
+    if (threadIdx.x == 0) { seg_off[0] = 0; seg_off[1] = n; }
+}
+
+// Level 1 -> coarse bucket offsets: coff[c] = position of (digit c, tile 0).
+__global__ void k_coarse_off(const unsigned long long *__restrict__ pos, const int *__restrict__ tile_base,
+                             int D1, long long n, long long *__restrict__ coff) {
+    griddep_wait();
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c > D1) return;
+    const int nt = tile_base[1];
+    coff[c] = (c < D1 && nt > 0) ? (long long)pos[(long long)c * nt] : n;
+}
+
+// Level 2 -> bucket offsets: boff[c*D2 + f] = position of (coarse c, digit f, tile 0).
+__global__ void k_bucket_off(const unsigned long long *__restrict__ pos, const int *__restrict__ tile_base,
+                             const long long *__restrict__ coff, int D1, int D2, long long n,
+                             long long *__restrict__ boff) {
+    griddep_wait();
+    const long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long B = (long long)D1 * D2;
+    if (b > B) return;
+    if (b == B) { boff[B] = n; return; }
+    const int c = (int)(b / D2), f = (int)(b % D2);
+    const int nt = tile_base[c + 1] - tile_base[c];
+    boff[b] = nt > 0 ? (long long)pos[(long long)D2 * tile_base[c] + (long long)f * nt] : coff[c];
+}
+
 // Every bucket's last key <= the next bucket's first key (buckets sorted).
+// Also records the largest bucket and the sum of squared bucket sizes.
 template <int KT>
 __global__ void k_bucket_check(const typename Key<KT>::T *__restrict__ keys, const long long *__restrict__ off,
                                int nb, long long n, LearnCtrl *__restrict__ lc) {
     griddep_wait();
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < 1 || b >= nb) return;
+    if (b >= nb) return;                       // nb is a multiple of 16; whole warps return together
+    const unsigned long long len = (unsigned long long)(off[b + 1] - off[b]);
+    unsigned long long mx = len, sq = len * len;
+    for (int o = 16; o; o >>= 1) {
+        mx = max(mx, __shfl_xor_sync(__activemask(), mx, o));
+        sq += __shfl_xor_sync(__activemask(), sq, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&lc->max_bucket, mx);
+        atomicAdd(&lc->bucket_sq, sq);
+    }
+    if (b == 0) { lc->nkeys = (unsigned long long)n; lc->nbuckets = nb; }
     const long long p = off[b];
-    if (p > 0 && p < n && Key<KT>::ord(keys[p - 1]) > Key<KT>::ord(keys[p])) atomicExch(&lc->fallback, 1);
+    if (b > 0 && p > 0 && p < n && Key<KT>::ord(keys[p - 1]) > Key<KT>::ord(keys[p])) atomicExch(&lc->fallback, 1);
 }
 
 // ------------------------------------------------------------- host
@@ -455,7 +779,7 @@ template <int KB> struct UKey;
 template <> struct UKey<4> { enum { KT = SR_KEY_U32 }; };
 template <> struct UKey<8> { enum { KT = SR_KEY_U64 }; };
 
-template <int KT>
+template <int KT, typename BT>
 static sr_status learned_impl(void *d_keys, size_t n, const sr_learned_opts *o, cudaStream_t s) {
     typedef Key<KT> K;
     typedef typename K::T T;
@@ -463,8 +787,8 @@ static sr_status learned_impl(void *d_keys, size_t n, const sr_learned_opts *o, 
     constexpr int KTU = UKey<sizeof(U)>::KT;
     const uint32_t nb = o && o->num_buckets ? o->num_buckets : (1u << 16);
     const uint32_t stride = o && o->sample_stride ? o->sample_stride : 100u;
-    const uint32_t cap = o && o->train_points ? o->train_points : 8192u;
-    uint32_t steps = o && o->train_steps ? o->train_steps : 64u;
+    const uint32_t cap = o && o->train_points ? o->train_points : 4096u;
+    uint32_t steps = o && o->train_steps ? o->train_steps : 24u;
     const float lr = o && o->learning_rate > 0.f ? o->learning_rate : 3e-3f;
     const uint32_t model = o ? o->model : 0u;
     if (nb < 16 || nb > (1u << 20) || (nb & (nb - 1)) || model > SR_MODEL_FORCE_BAD || cap < 2 || cap > (1u << 20))
@@ -485,8 +809,16 @@ static sr_status learned_impl(void *d_keys, size_t n, const sr_learned_opts *o, 
     const long long m = (N + stride - 1) / stride;
     const PlainSort<KTU, false> sample_sort((size_t)m);
     const PlainSort<KT, false> fallback_sort(n);
-    // scratch: control | sample | sample-sort scratch | points | histogram |
-    //          offsets | cursors | bucketed keys | fallback scratch
+    int lb = 0;
+    while ((1u << lb) < nb) ++lb;
+    const int D2 = 1 << (lb / 2), D1 = (int)(nb >> (lb / 2)), s2 = lb / 2;
+    const long long tiles1 = (N + SPLIT_T - 1) / SPLIT_T;
+    const long long tiles_max = tiles1 + D1;
+    const long long E_max = (long long)std::max(D1, D2) * tiles_max;
+    const long long sums_max = (E_max + SCAN_PER_CTA - 1) / SCAN_PER_CTA + 1;
+    // scratch: control | sample | sample-sort scratch | points | split tables |
+    //          counts | positions | CTA sums | coarse and bucket offsets |
+    //          two key buffers | fallback scratch
     size_t off = 0;
     auto take = [&](size_t bytes) { const size_t at = off; off += align_up(bytes, 256); return at; };
     const size_t o_ctrl = take(sizeof(LearnCtrl));
@@ -494,10 +826,19 @@ static sr_status learned_impl(void *d_keys, size_t n, const sr_learned_opts *o, 
     const size_t o_ss = take(sample_sort.bytes);
     const size_t o_px = take((size_t)cap * 4);
     const size_t o_pt = take((size_t)cap * 4);
-    const size_t o_hist = take((size_t)nb * 4);
-    const size_t o_off = take((size_t)(nb + 1) * 8);
-    const size_t o_cur = take((size_t)nb * 8);
-    const size_t o_keys = take(n * sizeof(T));
+    const size_t o_range = take(2 * 8);
+    const size_t o_tb = take((size_t)(D1 + 2) * 4);
+    const size_t o_tseg = take((size_t)tiles_max * 4);
+    const size_t o_tloc = take((size_t)tiles_max * 4);
+    const size_t o_cnt = take((size_t)E_max * 4);
+    const size_t o_pos = take((size_t)(E_max + 1) * 8);
+    const size_t o_sums = take((size_t)sums_max * 8);
+    const size_t o_coff = take((size_t)(D1 + 1) * 8);
+    const size_t o_boff = take((size_t)(nb + 1) * 8);
+    const size_t o_ka = take(n * sizeof(T));
+    const size_t o_kb = take(n * sizeof(T));
+    const size_t o_ba = take(n * sizeof(BT));
+    const size_t o_bb = take(n * sizeof(BT));
     const size_t o_fb = take(fallback_sort.bytes);
     void *scratch = nullptr;
     SR_TRY(scratch_alloc(ds, &scratch, off, s));
@@ -505,38 +846,81 @@ static sr_status learned_impl(void *d_keys, size_t n, const sr_learned_opts *o, 
     LearnCtrl *lc = (LearnCtrl *)(sp + o_ctrl);
     U *sample = (U *)(sp + o_sample);
     float *px = (float *)(sp + o_px), *pt = (float *)(sp + o_pt);
-    unsigned int *hist = (unsigned int *)(sp + o_hist);
-    long long *boff = (long long *)(sp + o_off);
-    unsigned long long *cursor = (unsigned long long *)(sp + o_cur);
-    T *bucketed = (T *)(sp + o_keys);
+    long long *range = (long long *)(sp + o_range);
+    int *tb = (int *)(sp + o_tb), *tseg = (int *)(sp + o_tseg), *tloc = (int *)(sp + o_tloc);
+    unsigned int *cnt = (unsigned int *)(sp + o_cnt);
+    unsigned long long *pos = (unsigned long long *)(sp + o_pos), *sums = (unsigned long long *)(sp + o_sums);
+    long long *coff = (long long *)(sp + o_coff), *boff = (long long *)(sp + o_boff);
+    T *ka = (T *)(sp + o_ka), *kb = (T *)(sp + o_kb);
+    BT *ba = (BT *)(sp + o_ba), *bb = (BT *)(sp + o_bb);
     T *uk = (T *)d_keys;
 
     sr_status st = SR_OK;
     do {
-        if (cudaMemsetAsync(lc, 0, sizeof(LearnCtrl), s) != cudaSuccess ||
-            cudaMemsetAsync(hist, 0, (size_t)nb * 4, s) != cudaSuccess) {
-            st = launch_status();
-            break;
-        }
+        if (cudaMemsetAsync(lc, 0, sizeof(LearnCtrl), s) != cudaSuccess) { st = launch_status(); break; }
         SR_LAUNCH(SR_KERNEL_MODEL, k_sample<KT>, (unsigned)((m + 255) / 256), 256, 0, s, uk, m, (long long)stride,
                   sample);
         if ((st = sample_sort.launch((typename PlainSort<KTU, false>::T *)sample, nullptr, sp + o_ss, s)) != SR_OK)
             break;
         SR_LAUNCH(SR_KERNEL_MODEL, k_train<U>, 1, TRAIN_NT, 0, s, sample, m, px, pt, (long long)0,
                   (int)TRAIN_PIPELINE, (int)steps, lr, (int)cap, (int)model, (int)nb, lc);
-        const int grid = sm_count_l() * 8;
-        SR_LAUNCH(SR_KERNEL_MODEL, k_hist<KT>, grid, 256, 0, s, uk, N, lc, hist);
-        SR_LAUNCH(SR_KERNEL_MODEL, k_bucket_scan, 1, 1024, 0, s, hist, (int)nb, N, boff, cursor, lc);
-        SR_LAUNCH(SR_KERNEL_MODEL, k_scatter<KT>, grid, 256, 0, s, uk, N, lc, cursor, boff, bucketed, ds->status);
-        if ((st = segmented_run<KT>(bucketed, uk, n, (const int64_t *)boff, nb, s, false)) != SR_OK) break;
+        // level 1: the whole input -> D1 coarse buckets (ka)
+        SR_LAUNCH(SR_KERNEL_MODEL, k_whole_range, 1, 32, 0, s, range, N);
+        for (int level = 1; level <= 2; ++level) {
+            const int S = level == 1 ? 1 : D1;
+            const int D = level == 1 ? D1 : D2;
+            const long long *segs = level == 1 ? range : coff;
+            const T *in = level == 1 ? uk : ka;
+            T *out = level == 1 ? ka : kb;
+            const unsigned grid = (unsigned)(level == 1 ? tiles1 : tiles_max);
+            const unsigned sgrid = (unsigned)(((long long)D * grid + SCAN_PER_CTA - 1) / SCAN_PER_CTA);
+            // level 1 writes the bucket ids (ba) beside the keys; they move with the keys (bb)
+            const BT *bin = level == 1 ? ba : bb;
+            SR_LAUNCH(SR_KERNEL_MODEL, k_split_tiles, 1, 1024, 0, s, segs, S, tb, tseg, tloc);
+            SR_LAUNCH(SR_KERNEL_MODEL, (k_split_hist<KT, BT>), grid, SPLIT_NT, (size_t)D * 4, s, in, bin, ba, segs,
+                      S, tb, tseg, tloc, level, D, s2, lc, cnt);
+            SR_LAUNCH(SR_KERNEL_MODEL, k_scan_sums, sgrid, 1024, 0, s, cnt, tb, S, D, sums);
+            SR_LAUNCH(SR_KERNEL_MODEL, k_scan_top, 1, 1024, 0, s, sums, tb, S, D);
+            SR_LAUNCH(SR_KERNEL_MODEL, k_scan_apply, sgrid, 1024, 0, s, cnt, tb, S, D, sums, pos);
+            const size_t sc_smem = (size_t)SPLIT_T * (sizeof(T) + sizeof(BT)) + (size_t)D * 16 + 4;
+            if (sc_smem > 48 * 1024 &&
+                cudaFuncSetAttribute((const void *)k_split_scatter<KT, BT>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc_smem) != cudaSuccess) {
+                st = launch_status();
+                break;
+            }
+            SR_LAUNCH(SR_KERNEL_MODEL, (k_split_scatter<KT, BT>), grid, SPLIT_NT, sc_smem, s, in, bin, out,
+                      level == 1 ? bb : (BT *)nullptr, segs, S, tb, tseg, tloc, level, D, s2, lc, cnt, pos,
+                      ds->status);
+            if (level == 1) {
+                SR_LAUNCH(SR_KERNEL_MODEL, k_coarse_off, (unsigned)((D1 + 1 + 255) / 256), 256, 0, s, pos, tb, D1, N,
+                          coff);
+            } else {
+                SR_LAUNCH(SR_KERNEL_MODEL, k_bucket_off, (unsigned)((nb + 1 + 255) / 256), 256, 0, s, pos, tb, coff,
+                          D1, D2, N, boff);
+            }
+        }
+        if (st != SR_OK) break;
+        // every bucket sorted, kb -> the caller's buffer
+        if ((st = segmented_run<KT>(kb, uk, n, (const int64_t *)boff, nb, s, false, true)) != SR_OK) break;
         SR_LAUNCH(SR_KERNEL_MODEL, k_bucket_check<KT>, (unsigned)((nb + 255) / 256), 256, 0, s, uk, boff, (int)nb,
                   N, lc);
-        if ((st = fallback_sort.launch(uk, nullptr, sp + o_fb, s, &lc->fallback)) != SR_OK) break;
         if (cudaMemcpyAsync(ds->last_aux, lc, sizeof(LearnCtrl), cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
             st = launch_status();
             break;
         }
         rec.aux_kind = 4;
+        // the check's verdict decides whether the plain sort runs: read it back
+        // (launching the plain sort gated on the device would still cost every
+        // one of its kernels a full grid of empty CTAs)
+        int fallback = 0;
+        if (cudaMemcpyAsync(&fallback, &lc->fallback, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            st = launch_status();
+            if (st == SR_OK) st = SR_ERR_CUDA;
+            break;
+        }
+        if (fallback && (st = fallback_sort.launch(uk, nullptr, sp + o_fb, s)) != SR_OK) break;
     } while (0);
     scratch_free(scratch, s);
     return st;
@@ -633,12 +1017,18 @@ extern "C" sr_status sr_sort_keys_learned(void *d_keys, size_t n, sr_key_type kt
     if (n > 1 && !d_keys) return SR_ERR_INVALID_ARG;
     if (n > 1 && ((uintptr_t)d_keys % key_bytes_of(kt)) != 0) return SR_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
+    const bool wide = opts && opts->num_buckets > (1u << 16);     // bucket ids need 32 bits
     switch (kt) {
-    case SR_KEY_I32: return learned_impl<SR_KEY_I32>(d_keys, n, opts, s);
-    case SR_KEY_U32: return learned_impl<SR_KEY_U32>(d_keys, n, opts, s);
-    case SR_KEY_F32: return learned_impl<SR_KEY_F32>(d_keys, n, opts, s);
-    case SR_KEY_U64: return learned_impl<SR_KEY_U64>(d_keys, n, opts, s);
-    case SR_KEY_I64: return learned_impl<SR_KEY_I64>(d_keys, n, opts, s);
+    case SR_KEY_I32: return wide ? learned_impl<SR_KEY_I32, uint32_t>(d_keys, n, opts, s)
+                                 : learned_impl<SR_KEY_I32, uint16_t>(d_keys, n, opts, s);
+    case SR_KEY_U32: return wide ? learned_impl<SR_KEY_U32, uint32_t>(d_keys, n, opts, s)
+                                 : learned_impl<SR_KEY_U32, uint16_t>(d_keys, n, opts, s);
+    case SR_KEY_F32: return wide ? learned_impl<SR_KEY_F32, uint32_t>(d_keys, n, opts, s)
+                                 : learned_impl<SR_KEY_F32, uint16_t>(d_keys, n, opts, s);
+    case SR_KEY_U64: return wide ? learned_impl<SR_KEY_U64, uint32_t>(d_keys, n, opts, s)
+                                 : learned_impl<SR_KEY_U64, uint16_t>(d_keys, n, opts, s);
+    case SR_KEY_I64: return wide ? learned_impl<SR_KEY_I64, uint32_t>(d_keys, n, opts, s)
+                                 : learned_impl<SR_KEY_I64, uint16_t>(d_keys, n, opts, s);
     default: return SR_ERR_INVALID_ARG;
     }
 }

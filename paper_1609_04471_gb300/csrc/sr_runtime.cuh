@@ -47,10 +47,12 @@ struct CallRecord {
 };
 
 // The segmented sort from `in` to `out` (in == out: in place), defined in
-// sr_segmented.cu; `record` makes it this thread's last call for sr_get_stats.
+// sr_segmented.cu; `record` makes it this thread's last call for sr_get_stats;
+// `bucket_mode` sorts small segments one per CTA instead of in packs (for
+// segments of moderate, similar sizes such as learned buckets).
 template <int KT>
 sr_status segmented_run(const typename Key<KT>::T *in, typename Key<KT>::T *out, size_t n_keys,
-                        const int64_t *d_off, size_t nseg, cudaStream_t s, bool record);
+                        const int64_t *d_off, size_t nseg, cudaStream_t s, bool record, bool bucket_mode);
 
 // Fill the stats fields of a segmented / learned call from its control block.
 sr_status segmented_stats(const void *aux, sr_stats *out);

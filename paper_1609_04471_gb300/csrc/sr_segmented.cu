@@ -83,6 +83,13 @@ template <> struct Comp<8> {
 template <int KB> struct SegShape;
 template <> struct SegShape<4> { enum { SNT = 512, IPT_P = 11, IPT = 15, MNT = 256, MIPT = 15 }; };
 template <> struct SegShape<8> { enum { SNT = 512, IPT_P = 7, IPT = 11, MNT = 256, MIPT = 11 }; };
+// Bucket mode (segments of similar, moderate sizes): a small segment gets one
+// CTA of the smallest shape that holds it, instead of sharing a pack.  Shapes
+// (threads x keys per thread, IPT odd): 128x9, 128x15, 256x9, 256x11, 256x15.
+enum { NSMALL = 5 };
+__host__ __device__ constexpr int small_cap(int c) {
+    return c == 0 ? 128 * 9 : c == 1 ? 128 * 15 : c == 2 ? 256 * 9 : c == 3 ? 256 * 11 : 256 * 15;
+}
 
 struct SegCtrl {
     int status;                  // SR_ERR_BAD_SEGMENTS when the offsets fail the check
@@ -92,8 +99,10 @@ struct SegCtrl {
     unsigned int n_big_mtiles;   // merge tiles of all big segments
     int max_passes;              // most merge passes any big segment needs
     unsigned int work_next;      // work queue of k_seg_sort
-    unsigned int pad;
+    unsigned int pad1;
     unsigned long long big_keys;
+    unsigned int n_small[NSMALL];  // bucket mode: segments per small shape
+    unsigned int pad2;
 };
 
 __device__ __forceinline__ int dev_ceil_log2(long long x) {
@@ -104,10 +113,13 @@ __device__ __forceinline__ int dev_ceil_log2(long long x) {
 
 // ----------------------------------------------------------- kernels
 
+// Packs mode: marks the first segment of every chunk and lists medium and big
+// segments.  Bucket mode: lists every segment under the smallest small shape
+// that holds it (lists[cls * nseg + i]), or as medium or big; no packs.
 __global__ void k_seg_classify(const int64_t *__restrict__ off, long long nseg, long long nkeys, int chunk,
                                int tile, long long nchunks, int *__restrict__ chunk_first,
                                unsigned int *__restrict__ medium, unsigned int *__restrict__ big,
-                               SegCtrl *__restrict__ c) {
+                               int bucket_mode, unsigned int *__restrict__ lists, SegCtrl *__restrict__ c) {
     griddep_wait();
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nseg) return;
@@ -117,13 +129,23 @@ __global__ void k_seg_classify(const int64_t *__restrict__ off, long long nseg, 
         atomicExch(&c->status, (int)SR_ERR_BAD_SEGMENTS);
         return;
     }
-    // chunks (chunk of the previous start, chunk of this start] begin with s
-    const long long cs = a / chunk;
-    const long long cp = s > 0 ? prev / chunk : -1;
-    for (long long q = cp + 1; q <= cs && q <= nchunks; ++q) chunk_first[q] = (int)s;
-    if (s == nseg - 1)
-        for (long long q = cs + 1; q <= nchunks; ++q) chunk_first[q] = (int)nseg;
     const long long len = b - a;
+    if (bucket_mode) {
+        if (len < 1) return;                       // (a single key still moves when in != out)
+        for (int cls = 0; cls < NSMALL; ++cls) {
+            if (len <= small_cap(cls)) {
+                lists[(long long)cls * nseg + atomicAdd(&c->n_small[cls], 1u)] = (unsigned int)s;
+                return;
+            }
+        }
+    } else {
+        // chunks (chunk of the previous start, chunk of this start] begin with s
+        const long long cs = a / chunk;
+        const long long cp = s > 0 ? prev / chunk : -1;
+        for (long long q = cp + 1; q <= cs && q <= nchunks; ++q) chunk_first[q] = (int)s;
+        if (s == nseg - 1)
+            for (long long q = cs + 1; q <= nchunks; ++q) chunk_first[q] = (int)nseg;
+    }
     if (len > chunk) {
         if (len <= tile) {
             medium[atomicAdd(&c->n_medium, 1u)] = (unsigned int)s;
@@ -284,7 +306,7 @@ k_seg_sort(const typename Key<KT>::T *in, typename Key<KT>::T *out, typename Key
             if (se - sb < 1) continue;
             const long long g0 = off[sb];
             const int cnt = (int)(off[se] - g0);
-            if (cnt < 2) continue;
+            if (cnt < 1) continue;                 // a single key still moves when in != out
             for (int i = t; i < PT; i += SNT) sf[i] = 0;
             __syncthreads();
             for (int q = sb + 1 + t; q < se; q += SNT) {
@@ -347,6 +369,24 @@ k_seg_sort(const typename Key<KT>::T *in, typename Key<KT>::T *out, typename Key
             const int passes = dev_ceil_log2((len + TT - 1) / TT);
             sort_range<KT, SNT, IPT>(in, (passes & 1) ? alt : out, g0, cnt, su);
         }
+    }
+}
+
+// Bucket mode: one CTA of NT threads per listed segment (at most NT*IPT keys).
+template <int KT, int NT, int IPT>
+__global__ void __launch_bounds__(NT)
+k_seg_small(const typename Key<KT>::T *in, typename Key<KT>::T *out, const int64_t *__restrict__ off,
+            const unsigned int *__restrict__ list, int cls, SegCtrl *__restrict__ c) {
+    griddep_wait();
+    typedef typename Key<KT>::U U;
+    extern __shared__ __align__(16) unsigned char smem[];
+    U *su = reinterpret_cast<U *>(smem);
+    if (c->status) return;
+    const unsigned int count = c->n_small[cls];
+    for (unsigned int i = blockIdx.x; i < count; i += gridDim.x) {
+        const unsigned int sgi = list[i];
+        const long long g0 = off[sgi];
+        sort_range<KT, NT, IPT>(in, out, g0, (int)(off[sgi + 1] - g0), su);
     }
 }
 
@@ -429,7 +469,7 @@ static int sm_count() {
 
 template <int KT>
 sr_status segmented_run(const typename Key<KT>::T *in, typename Key<KT>::T *out, size_t n_keys,
-                        const int64_t *d_off, size_t nseg, cudaStream_t s, bool record) {
+                        const int64_t *d_off, size_t nseg, cudaStream_t s, bool record, bool bucket_mode) {
     typedef Key<KT> K;
     typedef typename K::T T;
     typedef typename K::U U;
@@ -457,10 +497,12 @@ sr_status segmented_run(const typename Key<KT>::T *in, typename Key<KT>::T *out,
     const size_t cb = align_up(sizeof(SegCtrl), 256);
     const size_t fb = align_up((size_t)(nchunks + 2) * 4, 256);
     const size_t lb = align_up((nseg + 1) * 4, 256);
+    constexpr int SMAX = small_cap(NSMALL - 1);
     const bool in_place = (const void *)in == (const void *)out;
     const size_t kb = in_place ? align_up(n_keys * sizeof(T), 256) : 0;
     void *scratch = nullptr;
-    SR_TRY(scratch_alloc(ds, &scratch, cb + fb + 4 * lb + kb, s));
+    const size_t lsb = bucket_mode ? align_up((size_t)NSMALL * nseg * 4, 256) : 0;
+    SR_TRY(scratch_alloc(ds, &scratch, cb + fb + 4 * lb + lsb + kb, s));
     unsigned char *sp = (unsigned char *)scratch;
     SegCtrl *ctrl = (SegCtrl *)sp;
     int *chunk_first = (int *)(sp + cb);
@@ -468,13 +510,16 @@ sr_status segmented_run(const typename Key<KT>::T *in, typename Key<KT>::T *out,
     unsigned int *big = (unsigned int *)(sp + cb + fb + lb);
     unsigned int *tile_base = (unsigned int *)(sp + cb + fb + 2 * lb);
     unsigned int *mtile_base = (unsigned int *)(sp + cb + fb + 3 * lb);
-    T *alt = in_place ? (T *)(sp + cb + fb + 4 * lb) : const_cast<T *>(in);
+    unsigned int *lists = (unsigned int *)(sp + cb + fb + 4 * lb);
+    T *alt = in_place ? (T *)(sp + cb + fb + 4 * lb + lsb) : const_cast<T *>(in);
     const bool vec = ((uintptr_t)out % 16) == 0 && ((uintptr_t)alt % 16) == 0;
     sr_status st = SR_OK;
     do {
         if (cudaMemsetAsync(ctrl, 0, sizeof(SegCtrl), s) != cudaSuccess) { st = launch_status(); break; }
+        const int chunk = bucket_mode ? SMAX : CH;
         SR_LAUNCH(SR_KERNEL_SEGMENTED, k_seg_classify, (unsigned)((nseg + 255) / 256), 256, 0, s, d_off,
-                  (long long)nseg, (long long)n_keys, CH, TT, nchunks, chunk_first, medium, big, ctrl);
+                  (long long)nseg, (long long)n_keys, chunk, TT, nchunks, chunk_first, medium, big,
+                  bucket_mode ? 1 : 0, lists, ctrl);
         SR_LAUNCH(SR_KERNEL_SEGMENTED, k_seg_bigscan, 1, 1024, 0, s, d_off, big, TT, NV, tile_base, mtile_base,
                   ctrl);
         const size_t sort_smem = std::max((size_t)PT * (sizeof(C) + 4), (size_t)TT * sizeof(U));
@@ -482,8 +527,22 @@ sr_status segmented_run(const typename Key<KT>::T *in, typename Key<KT>::T *out,
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seg_sort<KT>, SNT, sort_smem);
         const int sort_grid = sm_count() * std::max(per_sm, 1);
+        if (bucket_mode) {
+#define SR_SMALL(cls, NT_, IPT_)                                                                          \
+    SR_LAUNCH(SR_KERNEL_SEGMENTED, (k_seg_small<KT, NT_, IPT_>), sm_count() * (2048 / NT_), NT_,           \
+              (size_t)(NT_ * IPT_) * sizeof(U), s, in, out, d_off, lists + (size_t)(cls) * nseg, cls, ctrl)
+            static_assert(small_cap(0) == 128 * 9 && small_cap(1) == 128 * 15 && small_cap(2) == 256 * 9 &&
+                              small_cap(3) == 256 * 11 && small_cap(4) == 256 * 15,
+                          "launch shapes must match small_cap");
+            SR_SMALL(0, 128, 9);
+            SR_SMALL(1, 128, 15);
+            SR_SMALL(2, 256, 9);
+            SR_SMALL(3, 256, 11);
+            SR_SMALL(4, 256, 15);
+#undef SR_SMALL
+        }
         SR_LAUNCH(SR_KERNEL_SEGMENTED, k_seg_sort<KT>, sort_grid, SNT, sort_smem, s, in, out, alt, d_off,
-                  nchunks, chunk_first, medium, big, tile_base, ctrl);
+                  bucket_mode ? 0ll : nchunks, chunk_first, medium, big, tile_base, ctrl);
         const size_t m_smem = (size_t)(NV + 16) * sizeof(U);
         const int merge_grid = sm_count() * 8;
         for (int p = 0; p < passes_upper; ++p) {
@@ -519,20 +578,20 @@ sr_status segmented_stats(const void *aux, sr_stats *out) {
 template <int KT>
 static sr_status seg_inplace(void *d_keys, size_t n_keys, const int64_t *d_off, size_t nseg, cudaStream_t s) {
     typedef typename Key<KT>::T T;
-    return segmented_run<KT>((const T *)d_keys, (T *)d_keys, n_keys, d_off, nseg, s, true);
+    return segmented_run<KT>((const T *)d_keys, (T *)d_keys, n_keys, d_off, nseg, s, true, false);
 }
 
 // instantiations used by the learned sort
 template sr_status segmented_run<SR_KEY_I32>(const uint32_t *, uint32_t *, size_t, const int64_t *, size_t,
-                                             cudaStream_t, bool);
+                                             cudaStream_t, bool, bool);
 template sr_status segmented_run<SR_KEY_U32>(const uint32_t *, uint32_t *, size_t, const int64_t *, size_t,
-                                             cudaStream_t, bool);
+                                             cudaStream_t, bool, bool);
 template sr_status segmented_run<SR_KEY_F32>(const uint32_t *, uint32_t *, size_t, const int64_t *, size_t,
-                                             cudaStream_t, bool);
+                                             cudaStream_t, bool, bool);
 template sr_status segmented_run<SR_KEY_U64>(const unsigned long long *, unsigned long long *, size_t,
-                                             const int64_t *, size_t, cudaStream_t, bool);
+                                             const int64_t *, size_t, cudaStream_t, bool, bool);
 template sr_status segmented_run<SR_KEY_I64>(const unsigned long long *, unsigned long long *, size_t,
-                                             const int64_t *, size_t, cudaStream_t, bool);
+                                             const int64_t *, size_t, cudaStream_t, bool, bool);
 
 static sr_status segmented_dispatch(void *d_keys, size_t n_keys, const int64_t *d_off, size_t nseg,
                                     sr_key_type kt, cudaStream_t s) {

@@ -85,6 +85,16 @@ def test_duplicates_and_presorted_segments(gpu_lib, dtype):
     assert _run(gpu_lib, keys, off).tobytes() == oracle.sort_segmented(keys, off).tobytes()
 
 
+def test_learned_style_out_of_place_singletons(gpu_lib):
+    """Many length-0 and length-1 segments among larger ones: every key must
+    still reach its place (exercised out of place by the learned sort)."""
+    rng = np.random.default_rng(36)
+    lens = rng.choice([0, 1, 1, 2, 3, 700, 2500, 4000], 3000).astype(np.int64)
+    off = _offsets(lens)
+    keys = _rand_keys(rng, int(off[-1]), np.int32)
+    assert _run(gpu_lib, keys, off).tobytes() == oracle.sort_segmented(keys, off).tobytes()
+
+
 def test_single_segment_and_all_empty(gpu_lib):
     rng = np.random.default_rng(33)
     for n in (0, 1, 2, 2816, 2817, 7680, 7681, 100_003):
