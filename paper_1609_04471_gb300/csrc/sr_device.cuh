@@ -81,13 +81,30 @@ template <int KB, bool VALS> struct Shape;
 // NT x IPT keys per merge CTA; SORT_NT x IPT keys per block-sort tile.  (A
 // 1024-thread block sort saves one global pass but its extra shared-memory
 // level costs more than that pass on GB300: 2.87 ms against 0.57 ms at 2^28.)
+// Defaults measured on GB300 (plain int32 sort, 2^24 and 2^28 keys); each
+// can be overridden at build time.
+#ifndef SR_K4_IPT
+#define SR_K4_IPT 25
+#endif
+#ifndef SR_K4V_IPT
+#define SR_K4V_IPT 11
+#endif
+#ifndef SR_K8_IPT
+#define SR_K8_IPT 13
+#endif
+#ifndef SR_K8V_IPT
+#define SR_K8V_IPT 13
+#endif
+#ifndef SR_SORT_NT
+#define SR_SORT_NT 512
+#endif
 #ifndef SR_MERGE_NT
 #define SR_MERGE_NT 256
 #endif
-template <> struct Shape<4, false> { enum { NT = SR_MERGE_NT, IPT = 15, SORT_NT = 512 }; };
-template <> struct Shape<4, true>  { enum { NT = SR_MERGE_NT, IPT = 11, SORT_NT = 512 }; };
-template <> struct Shape<8, false> { enum { NT = SR_MERGE_NT, IPT = 11, SORT_NT = 512 }; };
-template <> struct Shape<8, true>  { enum { NT = SR_MERGE_NT, IPT = 9,  SORT_NT = 512 }; };
+template <> struct Shape<4, false> { enum { NT = SR_MERGE_NT, IPT = SR_K4_IPT, SORT_NT = SR_SORT_NT }; };
+template <> struct Shape<4, true>  { enum { NT = SR_MERGE_NT, IPT = SR_K4V_IPT, SORT_NT = SR_SORT_NT }; };
+template <> struct Shape<8, false> { enum { NT = SR_MERGE_NT, IPT = SR_K8_IPT, SORT_NT = SR_SORT_NT }; };
+template <> struct Shape<8, true>  { enum { NT = SR_MERGE_NT, IPT = SR_K8V_IPT, SORT_NT = SR_SORT_NT }; };
 
 // ------------------------------------------------------------- merge path
 
@@ -105,37 +122,45 @@ __device__ __forceinline__ int merge_path(const U *a, int na, const U *b, int nb
     return lo;
 }
 
-// The same split found by one warp over global memory: each round every lane
-// tests one of 32 evenly spaced candidates and a ballot keeps the stretch that
-// holds the answer, so 2^k candidates cost about k/5 dependent loads.  Returns
-// the number of A items among the first `diag` outputs of the stable merge of
-// src[a_beg .. a_beg+na) and src[b_beg .. b_beg+nb).  All lanes must call it
-// with the same arguments; all lanes return the answer.
+// The same split found over global memory by a group of G = 2^lg lanes of
+// one warp (G = 1: plain binary search).  Each round the G lanes test G evenly
+// spaced candidates m and a ballot counts those with the answer above m, which
+// cuts the stretch holding the answer to 1/(G+1) of its length: about
+// log_{G+1}(range) dependent rounds of 2G scattered loads.  Returns the number
+// of A items among the first `diag` outputs of the stable merge of
+// src[a_beg .. a_beg+na) and src[b_beg .. b_beg+nb).  All lanes of a group
+// must call it with the same arguments; all of them return the answer.
 template <typename K>
-__device__ __forceinline__ long long warp_split(const typename K::T *__restrict__ src, long long a_beg,
-                                                long long na, long long b_beg, long long nb,
-                                                long long diag, int lane) {
+__device__ __forceinline__ long long group_split(const typename K::T *__restrict__ src, long long a_beg,
+                                                 long long na, long long b_beg, long long nb,
+                                                 long long diag, int lane, int lg) {
     typedef typename K::U U;
+    const int G = 1 << lg;
+    const int j = lane & (G - 1);
+    const unsigned mask = lg == 5 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
     long long lo = max(0ll, diag - nb), hi = min(diag, na);
     while (hi > lo) {
-        const long long step = (hi - lo + 31) >> 5;
-        const long long m = lo + lane * step;
-        bool before = false;                       // the answer is > m
+        const long long step = (hi - lo + G) / (G + 1);          // >= 1
+        const long long m = lo + (long long)(j + 1) * step - 1;
+        bool before = false;                                      // the answer is > m
         if (m < hi) {
             const U x = K::ord(src[a_beg + m]);
             const U y = K::ord(src[b_beg + diag - 1 - m]);
             before = !(y < x);
         }
-        const int cnt = __popc(__ballot_sync(0xffffffffu, before));
-        if (cnt == 0) {
-            hi = lo;
-        } else {
-            const long long nlo = lo + (long long)(cnt - 1) * step + 1;
-            hi = min(hi, lo + (long long)cnt * step);
-            lo = nlo;
-        }
+        const int cnt = __popc(__ballot_sync(mask, before));
+        const long long nhi = cnt == G ? hi : lo + (long long)(cnt + 1) * step - 1;
+        lo = lo + (long long)cnt * step;
+        hi = min(hi, nhi);
     }
     return lo;
+}
+
+template <typename K>
+__device__ __forceinline__ long long warp_split(const typename K::T *__restrict__ src, long long a_beg,
+                                                long long na, long long b_beg, long long nb,
+                                                long long diag, int lane) {
+    return group_split<K>(src, a_beg, na, b_beg, nb, diag, lane, 5);
 }
 
 // IPT outputs of the stable merge of s[a..a_end) and s[b..b_end) into
@@ -156,7 +181,9 @@ __device__ __forceinline__ void serial_merge(const U *s, int a, int a_end, int b
 }
 
 // Stable sort of a thread's IPT registers: odd-even transposition (only
-// neighbours swap, and only on a strict descent).
+// neighbours swap, and only on a strict descent).  (Batcher's odd-even merge
+// network needs fewer compare-exchanges, 59 against 105 for 15 keys, but
+// measured slower inside the block sort on GB300.)
 template <typename U, int IPT, bool VALS>
 __device__ __forceinline__ void thread_sort(U (&k)[IPT], uint32_t (&v)[IPT]) {
 #pragma unroll
@@ -172,9 +199,10 @@ __device__ __forceinline__ void thread_sort(U (&k)[IPT], uint32_t (&v)[IPT]) {
 }
 
 // Sorts the NT*IPT items held blocked in registers (thread t holds items
-// t*IPT .. t*IPT+IPT-1): a stable register sort, then log2(NT) rounds of
+// t*IPT .. t*IPT+IPT-1): a register sort, then log2(NT) rounds of stable
 // pairwise merges through shared memory (sk: NT*IPT keys, sv: NT*IPT values).
-// On return the registers hold the sorted tile, blocked.
+// Rounds whose runs lie inside one warp synchronise that warp only.  On
+// return the registers hold the sorted tile, blocked.
 template <typename U, int NT, int IPT, bool VALS>
 __device__ __forceinline__ void block_sort(U (&k)[IPT], uint32_t (&v)[IPT], U *sk, uint32_t *sv) {
     thread_sort<U, IPT, VALS>(k, v);
@@ -187,7 +215,7 @@ __device__ __forceinline__ void block_sort(U (&k)[IPT], uint32_t (&v)[IPT], U *s
 #pragma unroll
             for (int i = 0; i < IPT; ++i) sv[t * IPT + i] = v[i];
         }
-        __syncthreads();
+        if (coop <= 32) __syncwarp(); else __syncthreads();
         const int first = t & ~(coop - 1);
         const int run = (coop >> 1) * IPT;
         const int a0 = first * IPT, b0 = a0 + run;
@@ -199,7 +227,7 @@ __device__ __forceinline__ void block_sort(U (&k)[IPT], uint32_t (&v)[IPT], U *s
 #pragma unroll
             for (int i = 0; i < IPT; ++i) v[i] = sv[ix[i]];
         }
-        __syncthreads();
+        if (coop <= 32) __syncwarp(); else __syncthreads();
     }
 }
 
@@ -217,20 +245,15 @@ struct Ctrl {
     int unordered[MAX_PASSES];          // per merge pass: run pairs not already in order
     int status;
     unsigned int plan_ticket;           // CTAs of the pass planner that finished
+    // written by the pass planner once every unordered[p] is final: which
+    // buffer (0 = caller's, 1 = scratch) holds the data before pass p
+    signed char src_buf[MAX_PASSES + 1];
 };
 
 __device__ __forceinline__ int call_mode(const Ctrl *c, long long n) {
     if (c->descents == 0) return MODE_SORTED;
     if (c->nondescents == 0 && n > 1) return MODE_REVERSE;
     return MODE_SORT;
-}
-
-// Which buffer (0 = caller's, 1 = scratch) holds the data before merge pass p:
-// the block sort wrote buffer cur0, and every pass that was not skipped flips it.
-__device__ __forceinline__ int buffer_before_pass(const Ctrl *c, int cur0, int p) {
-    int flips = 0;
-    for (int q = 0; q < p; ++q) flips += c->unordered[q] != 0;
-    return cur0 ^ (flips & 1);
 }
 
 }  // namespace sr

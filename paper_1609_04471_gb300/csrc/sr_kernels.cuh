@@ -9,6 +9,12 @@ namespace sr {
 
 // ------------------------------------------------------------- kernels
 
+// Run detection over tile blockIdx.x of NT*IPT keys: counts the descents
+// a[i] > a[i+1] and non-descents of every pair whose left key lies in the tile
+// (so the pair across two tiles is counted once), and whether the tile alone
+// is ascending or strictly descending.  Keys arrive in 16-byte vectors when
+// the array is 16-byte aligned; the right neighbour of a vector's last key is
+// the next vector's first, read again through the read-only path.
 // `gate` (optional): when it points at 0 the scan counts nothing, so the call
 // sees a "sorted" input and every later kernel of the sequence returns at once.
 template <int KT, int NT, int IPT>
@@ -18,26 +24,46 @@ __global__ void __launch_bounds__(NT) k_detect(const typename Key<KT>::T *__rest
     griddep_wait();
     if (gate && *gate == 0) return;
     typedef Key<KT> K;
+    typedef typename K::T T;
     typedef typename K::U U;
-    constexpr int NV = NT * IPT;
-    extern __shared__ __align__(16) unsigned char smem[];
-    U *s = reinterpret_cast<U *>(smem);
+    constexpr int TS = NT * IPT;
+    constexpr int VW = 16 / sizeof(T);             // keys per 16-byte vector
     __shared__ unsigned int red[4];
     const int t = threadIdx.x;
-    const long long base = (long long)blockIdx.x * NV;
-    const int cnt = (int)(n - base < (long long)NV + 1 ? n - base : (long long)NV + 1);   // one more for the pair across
+    const long long base = (long long)blockIdx.x * TS;
+    const int cnt = (int)(n - base < (long long)TS ? n - base : (long long)TS);   // keys of the tile
+    const bool more = base + cnt < n;              // a key follows the tile
+    const bool vec = (((uintptr_t)(keys + base)) & 15) == 0;
     if (t < 4) red[t] = 0;
-    for (int i = t; i < cnt; i += NT) s[i] = K::ord(keys[base + i]);
     __syncthreads();
     unsigned int d = 0, nd = 0, din = 0, ndin = 0;
+    const int ng = (cnt + VW - 1) / VW;
+    for (int g = t; g < ng; g += NT) {
+        const int j0 = g * VW;                     // tile index of the vector's first key
+        U x[VW + 1];
+        if (vec && j0 + VW <= cnt) {
+            if constexpr (VW == 4) {
+                const uint4 q = __ldg(reinterpret_cast<const uint4 *>(keys + base + j0));
+                x[0] = K::ord((T)q.x); x[1] = K::ord((T)q.y); x[2] = K::ord((T)q.z); x[3] = K::ord((T)q.w);
+            } else {
+                const ulonglong2 q = __ldg(reinterpret_cast<const ulonglong2 *>(keys + base + j0));
+                x[0] = K::ord((T)q.x); x[1] = K::ord((T)q.y);
+            }
+        } else {
 #pragma unroll
-    for (int i = 0; i < IPT; ++i) {
-        const int j = t * IPT + i;
-        if (j + 1 < cnt) {
-            const bool de = s[j] > s[j + 1];
-            d += de;
-            nd += !de;
-            if (j + 1 < NV) { din |= de; ndin |= !de; }
+            for (int e = 0; e < VW; ++e) x[e] = j0 + e < cnt ? K::ord(__ldg(keys + base + j0 + e)) : U(0);
+        }
+        const bool has_next = j0 + VW < cnt || (j0 + VW == cnt && more);
+        x[VW] = has_next ? K::ord(__ldg(keys + base + j0 + VW)) : U(0);
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+            const int j = j0 + e;                  // pair (j, j+1)
+            if (j + 1 < cnt || (j + 1 == cnt && more)) {
+                const bool de = x[e] > x[e + 1];
+                d += de;
+                nd += !de;
+                if (j + 1 < cnt) { din |= de; ndin |= !de; }
+            }
         }
     }
     d = __reduce_add_sync(0xffffffffu, d);
@@ -45,10 +71,10 @@ __global__ void __launch_bounds__(NT) k_detect(const typename Key<KT>::T *__rest
     din = __reduce_or_sync(0xffffffffu, din);
     ndin = __reduce_or_sync(0xffffffffu, ndin);
     if ((t & 31) == 0) {
-        atomicAdd(&red[0], d);
-        atomicAdd(&red[1], nd);
-        atomicOr(&red[2], din);
-        atomicOr(&red[3], ndin);
+        if (d) atomicAdd(&red[0], d);
+        if (nd) atomicAdd(&red[1], nd);
+        if (din) atomicOr(&red[2], din);
+        if (ndin) atomicOr(&red[3], ndin);
     }
     __syncthreads();
     if (t == 0) {
@@ -168,11 +194,22 @@ k_block_sort(const typename Key<KT>::T *in_k, const uint32_t *in_v, typename Key
 // taken after a fence) settles the remaining passes from the chunks' extremes.
 enum { PLAN_CHUNK = 2048, PLAN_LEVELS = 11 };   // 2^11 tiles per chunk
 
+// Once every unordered[p] is final: the buffer before each pass (and after
+// the last), so later kernels read one byte instead of recounting flips.
+__device__ __forceinline__ void record_buffers(Ctrl *c, int cur0, int passes) {
+    int cur = cur0;
+    for (int p = 0; p < passes; ++p) {
+        c->src_buf[p] = (signed char)cur;
+        cur ^= (((volatile int *)c->unordered)[p] != 0);
+    }
+    c->src_buf[passes] = (signed char)cur;
+}
+
 template <int KT>
 __global__ void __launch_bounds__(1024)
 k_plan(const typename Key<KT>::U *__restrict__ lo, const typename Key<KT>::U *__restrict__ hi,
        typename Key<KT>::U *__restrict__ chunk_lo, typename Key<KT>::U *__restrict__ chunk_hi,
-       long long n, long long tiles, int passes, Ctrl *__restrict__ c) {
+       long long n, long long tiles, int passes, int cur0, Ctrl *__restrict__ c) {
     griddep_wait();
     typedef typename Key<KT>::U U;
     if (call_mode(c, n) != MODE_SORT) return;
@@ -204,7 +241,6 @@ k_plan(const typename Key<KT>::U *__restrict__ lo, const typename Key<KT>::U *__
         __syncthreads();
         if (t == 0 && s_cnt) atomicAdd(&c->unordered[p], (int)s_cnt);
     }
-    if (passes <= PLAN_LEVELS) return;
     // the chunk is fully reduced into index 0
     if (t == 0) {
         chunk_lo[blockIdx.x] = s_lo[0];
@@ -215,6 +251,10 @@ k_plan(const typename Key<KT>::U *__restrict__ lo, const typename Key<KT>::U *__
     __syncthreads();
     if (!s_last) return;
     __threadfence();
+    if (passes <= PLAN_LEVELS) {
+        if (t == 0) record_buffers(c, cur0, passes);
+        return;
+    }
     const int chunks = (int)gridDim.x;            // at most PLAN_CHUNK chunks (2^22 tiles)
     for (int i = t; i < chunks; i += blockDim.x) {
         s_lo[i] = ((volatile U *)chunk_lo)[i];
@@ -238,26 +278,39 @@ k_plan(const typename Key<KT>::U *__restrict__ lo, const typename Key<KT>::U *__
         __syncthreads();
         if (t == 0) c->unordered[p] = (int)s_cnt;
     }
+    if (t == 0) record_buffers(c, cur0, passes);
 }
 
+// Merge-path split of every merge tile boundary of pass p, one group of
+// 2^lg lanes per boundary (the host picks lg: wide groups take fewer
+// dependent rounds, narrow ones fewer scattered loads when there are many
+// boundaries).
 template <int KT>
 __global__ void __launch_bounds__(256)
 k_partition(const typename Key<KT>::T *__restrict__ uk, const typename Key<KT>::T *__restrict__ sk,
             long long n, long long w, int nv, long long nbound, long long *__restrict__ splits,
-            const Ctrl *__restrict__ c, int cur0, int p) {
+            const Ctrl *__restrict__ c, int p, int lg) {
     griddep_wait();
     typedef Key<KT> K;
     const int lane = threadIdx.x & 31;
-    const long long b = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (b >= nbound) return;                       // uniform across the warp
-    if (call_mode(c, n) != MODE_SORT || c->unordered[p] == 0) return;
-    const typename K::T *src = buffer_before_pass(c, cur0, p) ? sk : uk;
+    const long long b = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> lg;
+    if (b >= nbound) return;                       // uniform across the group
+    if (c->unordered[p] == 0) return;             // also 0 for every pass unless the input needs sorting
+    const typename K::T *src = c->src_buf[p] ? sk : uk;
     const long long out = min(b * (long long)nv, n);
     const long long pb = (out / (2 * w)) * (2 * w);
     const long long a_beg = pb, a_end = min(pb + w, n);
     const long long b_beg = a_end, b_end = min(pb + 2 * w, n);
-    const long long sp = warp_split<K>(src, a_beg, a_end - a_beg, b_beg, b_end - b_beg, out - pb, lane);
-    if (lane == 0) splits[b] = a_beg + sp;
+    const long long sp = group_split<K>(src, a_beg, a_end - a_beg, b_beg, b_end - b_beg, out - pb, lane, lg);
+    if ((lane & ((1 << lg) - 1)) == 0) splits[b] = a_beg + sp;
+}
+
+// Lanes per boundary for k_partition: about 160k searching lanes in all
+// (a single wave on 152 SMs), between 1 and 32 per boundary.
+inline int partition_lg(long long nbound) {
+    int lg = 5;
+    while (lg > 0 && (nbound << lg) > 160000) --lg;
+    return lg;
 }
 
 // Merges one output tile: outputs [out0, out0 + cnt) of the stable merge of
@@ -332,8 +385,17 @@ __device__ __forceinline__ void merge_tile(const typename Key<KT>::T *__restrict
             const int g = t + k * NT;
             if (g < nag + nbg) {
                 const int o = g < nag ? 4 * g : offb + 4 * (g - nag);
-#pragma unroll
-                for (int e = 0; e < 4; ++e) s[o + e] = K::ord((T)r[k][e]);
+                // one 16-byte shared store per 4-key group (o is a multiple of 4)
+                if (sizeof(U) == 4) {
+                    *reinterpret_cast<uint4 *>(s + o) =
+                        make_uint4((uint32_t)K::ord((T)r[k][0]), (uint32_t)K::ord((T)r[k][1]),
+                                   (uint32_t)K::ord((T)r[k][2]), (uint32_t)K::ord((T)r[k][3]));
+                } else {
+                    *reinterpret_cast<ulonglong2 *>(s + o) =
+                        make_ulonglong2((unsigned long long)K::ord((T)r[k][0]), (unsigned long long)K::ord((T)r[k][1]));
+                    *reinterpret_cast<ulonglong2 *>(s + o + 2) =
+                        make_ulonglong2((unsigned long long)K::ord((T)r[k][2]), (unsigned long long)K::ord((T)r[k][3]));
+                }
                 if (VALS) *reinterpret_cast<uint4 *>(sv + o) = rv[k];
             }
         }
@@ -372,7 +434,30 @@ __device__ __forceinline__ void merge_tile(const typename Key<KT>::T *__restrict
             if (VALS) dst_v[out0 + t] = sv[t];
         }
         const int full = (cnt - head) >> 2;
-        for (int g = t; g < full; g += NT) {
+        if (head == 0) {
+            // the tile starts on a group boundary: 16-byte shared loads as well
+            for (int g = t; g < full; g += NT) {
+                const int j = 4 * g;
+                if (sizeof(T) == 4) {
+                    const uint4 q = *reinterpret_cast<const uint4 *>(s + j);
+                    *reinterpret_cast<uint4 *>(dst_k + out0 + j) =
+                        make_uint4((uint32_t)K::unord((U)q.x), (uint32_t)K::unord((U)q.y),
+                                   (uint32_t)K::unord((U)q.z), (uint32_t)K::unord((U)q.w));
+                } else {
+                    const ulonglong2 q0 = *reinterpret_cast<const ulonglong2 *>(s + j);
+                    const ulonglong2 q1 = *reinterpret_cast<const ulonglong2 *>(s + j + 2);
+                    const unsigned long long e0 = (unsigned long long)K::unord((U)q0.x);
+                    const unsigned long long e1 = (unsigned long long)K::unord((U)q0.y);
+                    const unsigned long long e2 = (unsigned long long)K::unord((U)q1.x);
+                    const unsigned long long e3 = (unsigned long long)K::unord((U)q1.y);
+                    *reinterpret_cast<uint4 *>(dst_k + out0 + j) =
+                        make_uint4((uint32_t)e0, (uint32_t)(e0 >> 32), (uint32_t)e1, (uint32_t)(e1 >> 32));
+                    *reinterpret_cast<uint4 *>(dst_k + out0 + j + 2) =
+                        make_uint4((uint32_t)e2, (uint32_t)(e2 >> 32), (uint32_t)e3, (uint32_t)(e3 >> 32));
+                }
+                if (VALS) *reinterpret_cast<uint4 *>(dst_v + out0 + j) = *reinterpret_cast<const uint4 *>(sv + j);
+            }
+        } else for (int g = t; g < full; g += NT) {
             const int j = head + 4 * g;
             if (sizeof(T) == 4) {
                 uint4 q;
@@ -407,26 +492,26 @@ __device__ __forceinline__ void merge_tile(const typename Key<KT>::T *__restrict
 }
 
 // One CTA per output tile of NT*IPT keys of merge pass p.  The tile's A and B
-// ranges come from the split table and are merged by merge_tile.
+// ranges come from the split table and are merged by merge_tile.  A run pair
+// (2w keys) spans 2^lgt whole tiles.
 template <int KT, int NT, int IPT, bool VALS, bool VEC>
 __global__ void __launch_bounds__(NT)
 k_merge(typename Key<KT>::T *uk, uint32_t *uv, typename Key<KT>::T *sk, uint32_t *svb, long long n,
-        long long w, const long long *__restrict__ splits, const Ctrl *__restrict__ c, int cur0,
-        int p) {
+        long long w, int lgt, const long long *__restrict__ splits, const Ctrl *__restrict__ c, int p) {
     griddep_wait();
     typedef Key<KT> K;
     typedef typename K::U U;
     typedef typename K::T T;
     constexpr int NV = NT * IPT;
     constexpr int SV = NV + 16;                    // staged keys, with room for window slack
-    if (call_mode(c, n) != MODE_SORT || c->unordered[p] == 0) return;
+    if (c->unordered[p] == 0) return;              // also 0 for every pass unless the input needs sorting
     extern __shared__ __align__(16) unsigned char smem[];
     U *s = reinterpret_cast<U *>(smem);
     uint32_t *sv = reinterpret_cast<uint32_t *>(s + SV);
-    const int cur = buffer_before_pass(c, cur0, p);
+    const int cur = c->src_buf[p];
     const long long out0 = (long long)blockIdx.x * NV;
     const long long out1 = min(out0 + NV, n);
-    const long long pb = (out0 / (2 * w)) * (2 * w);
+    const long long pb = (long long)(((unsigned long long)blockIdx.x >> lgt) << lgt) * NV;
     const long long a_beg = pb, a_end = min(pb + w, n);
     const long long b_beg = a_end, b_end = min(pb + 2 * w, n);
     const long long a0 = splits[blockIdx.x];
@@ -438,11 +523,10 @@ k_merge(typename Key<KT>::T *uk, uint32_t *uv, typename Key<KT>::T *sk, uint32_t
 
 template <int KT, bool VALS>
 __global__ void k_copy_back(typename Key<KT>::T *uk, uint32_t *uv, const typename Key<KT>::T *sk,
-                            const uint32_t *svb, long long n, const Ctrl *__restrict__ c,
-                            int cur0, int passes) {
+                            const uint32_t *svb, long long n, const Ctrl *__restrict__ c, int passes) {
     griddep_wait();
     if (call_mode(c, n) != MODE_SORT) return;
-    if (buffer_before_pass(c, cur0, passes) == 0) return;
+    if (c->src_buf[passes] == 0) return;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         uk[i] = sk[i];

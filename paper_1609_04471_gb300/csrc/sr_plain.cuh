@@ -26,6 +26,8 @@ template <int KT, bool VALS> struct PlainSort {
     typedef Shape<sizeof(T), VALS> S;
     enum { NT = S::NT, IPT = S::IPT, SNT = S::SORT_NT, NV = S::NT * S::IPT, TS = S::SORT_NT * S::IPT };
     static_assert(TS % NV == 0, "sort tile must be a whole number of merge tiles");
+    enum { LG_TS_NV = TS / NV == 1 ? 0 : TS / NV == 2 ? 1 : TS / NV == 4 ? 2 : TS / NV == 8 ? 3 : -1 };
+    static_assert(LG_TS_NV >= 0, "merge tiles per sort tile must be a power of two up to 8");
 
     long long n = 0, tiles = 0, mtiles = 0;
     int passes = 0;
@@ -69,9 +71,7 @@ template <int KT, bool VALS> struct PlainSort {
         sr_status st = SR_OK;
         do {
             if (cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s) != cudaSuccess) { st = launch_status(); break; }
-            const size_t det_smem = (size_t)(TS + 1) * sizeof(U);
-            if ((st = allow_smem(k_detect<KT, SNT, IPT>, det_smem)) != SR_OK) break;
-            SR_LAUNCH(SR_KERNEL_DETECT, (k_detect<KT, SNT, IPT>), (unsigned)tiles, SNT, det_smem, s,
+            SR_LAUNCH(SR_KERNEL_DETECT, (k_detect<KT, SNT, IPT>), (unsigned)tiles, SNT, 0, s,
                       uk, n, ctrl, gate);
             SR_LAUNCH(SR_KERNEL_REVERSE, (k_reverse<KT, VALS>), grid_for(n / 2, 256, 152 * 16), 256, 0, s,
                       uk, uv, n, ctrl);
@@ -82,26 +82,28 @@ template <int KT, bool VALS> struct PlainSort {
             if (P == 0) break;
             if ((tiles + PLAN_CHUNK - 1) / PLAN_CHUNK > PLAN_CHUNK) { st = SR_ERR_UNSUPPORTED; break; }
             SR_LAUNCH(SR_KERNEL_PARTITION, (k_plan<KT>), (unsigned)((tiles + PLAN_CHUNK - 1) / PLAN_CHUNK),
-                      1024, 0, s, plo, phi, plo2, phi2, n, tiles, P, ctrl);
+                      1024, 0, s, plo, phi, plo2, phi2, n, tiles, P, cur0, ctrl);
             const size_t m_smem = (size_t)(NV + 16) * (sizeof(U) + (VALS ? 4 : 0));
             if ((st = allow_smem(k_merge<KT, NT, IPT, VALS, true>, m_smem)) != SR_OK) break;
             if ((st = allow_smem(k_merge<KT, NT, IPT, VALS, false>, m_smem)) != SR_OK) break;
             for (int p = 0; p < P; ++p) {
                 const long long w = (long long)TS << p;
+                const int lgt = LG_TS_NV + 1 + p;          // merge tiles per run pair: 2w / NV
                 const long long nb = mtiles + 1;
-                SR_LAUNCH(SR_KERNEL_PARTITION, (k_partition<KT>), (unsigned)((nb + 7) / 8), 256, 0, s,
-                          uk, sk, n, w, NV, nb, splits, ctrl, cur0, p);
+                const int lg = partition_lg(nb);
+                SR_LAUNCH(SR_KERNEL_PARTITION, (k_partition<KT>), (unsigned)(((nb << lg) + 255) / 256), 256, 0,
+                          s, uk, sk, n, w, NV, nb, splits, ctrl, p, lg);
                 if (vec) {
                     SR_LAUNCH(SR_KERNEL_MERGE, (k_merge<KT, NT, IPT, VALS, true>), (unsigned)mtiles, NT,
-                              m_smem, s, uk, uv, sk, sv, n, w, splits, ctrl, cur0, p);
+                              m_smem, s, uk, uv, sk, sv, n, w, lgt, splits, ctrl, p);
                 } else {
                     SR_LAUNCH(SR_KERNEL_MERGE, (k_merge<KT, NT, IPT, VALS, false>), (unsigned)mtiles, NT,
-                              m_smem, s, uk, uv, sk, sv, n, w, splits, ctrl, cur0, p);
+                              m_smem, s, uk, uv, sk, sv, n, w, lgt, splits, ctrl, p);
                 }
             }
             if (st != SR_OK) break;
             SR_LAUNCH(SR_KERNEL_COPY, (k_copy_back<KT, VALS>), grid_for(n, 256, 152 * 16), 256, 0, s,
-                      uk, uv, sk, sv, n, ctrl, cur0, P);
+                      uk, uv, sk, sv, n, ctrl, P);
         } while (0);
         return st;
     }

@@ -85,9 +85,7 @@ static sr_status detect_impl(const void *d_keys, size_t n, sr_run_info *out, cud
     sr_status st = SR_OK;
     do {
         if (cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s) != cudaSuccess) { st = launch_status(); break; }
-        const size_t smem = (size_t)(TS + 1) * sizeof(typename K::U);
-        if ((st = PlainSort<KT, false>::allow_smem(k_detect<KT, SNT, IPT>, smem)) != SR_OK) break;
-        SR_LAUNCH(SR_KERNEL_DETECT, (k_detect<KT, SNT, IPT>), (unsigned)tiles, SNT, smem, s,
+        SR_LAUNCH(SR_KERNEL_DETECT, (k_detect<KT, SNT, IPT>), (unsigned)tiles, SNT, 0, s,
                   (const T *)d_keys, N, ctrl, (const int *)nullptr);
         if (cudaMemcpyAsync(&h, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) {

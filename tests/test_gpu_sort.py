@@ -12,8 +12,23 @@ pytestmark = pytest.mark.gpu
 
 KT = {np.dtype(np.int32): 0, np.dtype(np.uint32): 1, np.dtype(np.float32): 2,
       np.dtype(np.uint64): 3, np.dtype(np.int64): 4}
-# tile shapes of the library: merge tiles of 256*IPT keys, block-sort tiles of 512*IPT
-TILES = {4: (3840, 7680), 8: (2816, 5632)}
+_TILES = {}
+
+
+def _tiles(sr, kb, vals=False):
+    """(merge tile, block-sort tile) of the library for keys of kb bytes, as
+    its statistics report them after a small sort."""
+    key = (kb, vals)
+    if key not in _TILES:
+        import torch
+        t = torch.zeros(1000, dtype={4: torch.int32, 8: torch.int64}[kb], device="cuda")
+        if vals:
+            sr.sort_pairs(t, torch.zeros(1000, dtype=torch.int32, device="cuda"), key_type=0 if kb == 4 else 3)
+        else:
+            sr.sort_keys(t, key_type=0 if kb == 4 else 3)
+        st = sr.stats()
+        _TILES[key] = (st["merge_tile"], st["tile"])
+    return _TILES[key]
 
 
 def _to_dev(a):
@@ -52,8 +67,8 @@ def _random(rng, n, dtype):
     return rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32).view(dtype)
 
 
-def _sizes(kb):
-    nv, ts = TILES[kb]
+def _sizes(sr, kb):
+    nv, ts = _tiles(sr, kb)
     return sorted({0, 1, 2, 3, 5, 31, 32, 33, 255, 1000, nv - 1, nv, nv + 1, ts - 1, ts, ts + 1,
                    2 * ts + 7, 4 * ts - 1, (1 << 16) + 1, 5 * ts + 3, 100_003, (1 << 20) - 1})
 
@@ -61,7 +76,7 @@ def _sizes(kb):
 @pytest.mark.parametrize("dtype", [np.int32, np.uint32, np.float32, np.uint64, np.int64])
 def test_keys_random_sizes(gpu_lib, dtype):
     rng = np.random.default_rng(10)
-    for n in _sizes(np.dtype(dtype).itemsize):
+    for n in _sizes(gpu_lib, np.dtype(dtype).itemsize):
         a = _random(rng, n, dtype)
         got = _gpu_sort(gpu_lib, a)
         want = oracle.sort_keys(a)
@@ -128,9 +143,9 @@ def test_reversed_input_one_pass(gpu_lib):
 
 def test_teeth_skip_passes(gpu_lib):
     """2-equal teeth whose teeth are whole numbers of block-sort tiles (128
-    tiles of 7680 int32 keys): every merge pass below the tooth length finds
-    all its run pairs in order and is skipped; only the last pass merges."""
-    n = 128 * TILES[4][1]
+    int32 tiles): every merge pass below the tooth length finds all its run
+    pairs in order and is skipped; only the last pass merges."""
+    n = 128 * _tiles(gpu_lib, 4)[1]
     a = si.k_equal_teeth(n, 2)
     t = _to_dev(a)
     gpu_lib.sort_keys(t, key_type=0)
@@ -173,7 +188,8 @@ def test_detect_runs_matches_oracle(gpu_lib):
 @pytest.mark.parametrize("dtype", [np.int32, np.float32, np.uint64, np.int64, np.uint32])
 def test_pairs_stable(gpu_lib, dtype):
     rng = np.random.default_rng(12)
-    for n in (0, 1, 2, 33, 2304, 2816, 2817, 9216, 9217, 11264, 11265, 30_001, 262_147):
+    nv, ts = _tiles(gpu_lib, np.dtype(dtype).itemsize, vals=True)
+    for n in sorted({0, 1, 2, 33, nv - 1, nv, nv + 1, ts, ts + 1, 2 * ts, 2 * ts + 1, 30_001, 262_147}):
         k = (rng.integers(0, 9, n).astype(dtype) if n % 2 else _random(rng, n, dtype))
         v = rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32)
         gk, gv = _gpu_pairs(gpu_lib, k, v)
