@@ -468,7 +468,8 @@ def _forms(sr, torch, dev, stream, peak):
              against the plain sort on the same input (and the model-free
              equal-width ablation);
     batched  200,000 int32 arrays (lognormal lengths, median 512, four
-             classes), the segmented sort replayed from a captured CUDA graph,
+             classes), the segmented sort under the autotuner's configuration
+             replayed from a captured CUDA graph,
              against one plain sort call per array (on the first 2,000 arrays,
              scaled per key)."""
     import numpy as np
@@ -509,24 +510,31 @@ def _forms(sr, torch, dev, stream, peak):
         "max_bucket": stl["max_bucket"]}
     del src, x
     torch.cuda.empty_cache()
-    # batched segmented vs per-array
+    # batched segmented vs per-array: the autotuner times every launch
+    # configuration on this batch (untimed here), the winner is captured in a
+    # CUDA graph and replayed
+    from paper_1609_04471_gb300 import autotune
     keys, off, _ = si.segmented_i32(200_000, SEED)
     n = int(off[-1])
     src = torch.from_numpy(keys).to(dev)
     toff = torch.from_numpy(off).to(dev)
     x = torch.empty_like(src)
+    cand = autotune.time_configs(src, toff, sr.KEY_I32, reps=2)
+    best = autotune.select_best(cand)
+    cfgs = {c["index"]: c for c in sr.segmented_configs(sr.KEY_I32)}
     x.copy_(src)
-    sr.sort_segmented_ex(x, toff)
+    sr.sort_segmented_cfg(x, toff, best)
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
     cs = torch.cuda.Stream()
     with torch.cuda.stream(cs):
         with torch.cuda.graph(g, stream=cs):
-            sr.sort_segmented_ex(x, toff)
+            sr.sort_segmented_cfg(x, toff, best)
     torch.cuda.synchronize()
     graph_ms = _timed(torch, stream, g.replay, lambda: x.copy_(src), 3)
-    eager_ms = _timed(torch, stream, lambda: sr.sort_segmented_ex(x, toff), lambda: x.copy_(src), 3)
     sts = sr.stats()
+    eager_ms = _timed(torch, stream, lambda: sr.sort_segmented_cfg(x, toff, best), lambda: x.copy_(src), 3)
+    default_ms = _timed(torch, stream, lambda: sr.sort_segmented_ex(x, toff), lambda: x.copy_(src), 3)
     sample = 2000
     views = [x[int(off[i]):int(off[i + 1])] for i in range(sample)]
     sample_keys = int(off[sample])
@@ -541,7 +549,12 @@ def _forms(sr, torch, dev, stream, peak):
         "per_array_sample_arrays": sample, "per_array_sample_keys": sample_keys, "per_array_ms": per_ms,
         "per_array_gkeys_s": sample_keys / (per_ms / 1e3) / 1e9,
         "batched_over_per_array": (n / graph_ms) / (sample_keys / per_ms),
-        "big_segments": sts["big_segments"]}
+        "big_segments": sts["big_segments"],
+        "autotuned": {"config": best,
+                      "shape": {k: cfgs[best][k] for k in ("strategy", "sort_threads", "pack_items",
+                                                           "tile_items", "fan_in", "ladder")},
+                      "candidates_ms": {str(c): round(v, 4) for c, v in sorted(cand.items())},
+                      "default_config_ms": default_ms}}
     del g
     return out
 

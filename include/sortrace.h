@@ -118,6 +118,59 @@ sr_status sr_sort_segmented_ex(void *d_keys, size_t n_keys, const int64_t *d_off
                                size_t num_segments, sr_key_type kt, sr_stream stream);
 
 /*
+ * Launch configurations of the segmented sort.  Each key width has a fixed
+ * list (sr_segmented_num_configs); sr_segmented_config_info describes entry
+ * `config`:
+ *   strategy       0: small segments (<= small_keys) are sorted many to a CTA
+ *                  as (segment, key) composites ("packs"); 1: one CTA of the
+ *                  smallest of five fixed shapes per small segment (<= 3840
+ *                  keys), from ladder `ladder`: 0 = 128x9, 128x15, 256x9,
+ *                  256x11, 256x15 (threads x keys per thread); 1 = 64x9,
+ *                  128x9, 128x15, 256x11, 256x15.
+ *   sort_threads   threads of the persistent sort CTA.
+ *   pack_items     composite keys per thread of a pack (strategy 0; else 0).
+ *   tile_items     keys per thread of a block-sort tile; tile_keys =
+ *                  sort_threads * tile_items.
+ *   fan_in         merge fan-in: block-sort tiles one CTA merges in shared
+ *                  memory, so one CTA sorts a segment of up to cta_keys =
+ *                  fan_in * tile_keys keys; longer segments go through global
+ *                  merge passes starting from runs of cta_keys keys.
+ *   merge_threads  threads of a global merge tile (tile_items keys each).
+ * Every configuration gives the same (unique) result; they differ in speed
+ * with the segment-length mix.  The package's autotuner times them on a
+ * workload and keeps the fastest.  SR_SEG_CONFIG_DEFAULT (-1) selects the
+ * library default (entry 0).  sr_segmented_config_info returns
+ * SR_ERR_INVALID_ARG for an unknown key type or entry or a null `out`.
+ */
+#define SR_SEG_CONFIG_DEFAULT (-1)
+typedef struct sr_segmented_config {
+    int32_t strategy;
+    int32_t sort_threads;
+    int32_t pack_items;
+    int32_t tile_items;
+    int32_t fan_in;
+    int32_t merge_threads;
+    int64_t tile_keys;
+    int64_t cta_keys;
+    int64_t small_keys;         /* longest segment sorted as a small one */
+    int32_t ladder;             /* strategy 1: small-shape ladder; else -1 */
+    int32_t reserved;
+} sr_segmented_config;
+
+int sr_segmented_num_configs(sr_key_type kt);
+sr_status sr_segmented_config_info(sr_key_type kt, int config, sr_segmented_config *out);
+
+/*
+ * sr_sort_segmented_cfg -- sr_sort_segmented_ex under launch configuration
+ * `config` (0 .. sr_segmented_num_configs(kt) - 1, or SR_SEG_CONFIG_DEFAULT);
+ * SR_ERR_INVALID_ARG for any other value.  Reads nothing back to the host
+ * (graph-capturable like sr_sort_segmented_ex, which is this call with
+ * SR_SEG_CONFIG_DEFAULT).
+ */
+sr_status sr_sort_segmented_cfg(void *d_keys, size_t n_keys, const int64_t *d_offsets,
+                                size_t num_segments, sr_key_type kt, int config, sr_stream stream);
+
+/*
  * sr_sort_keys_host -- sr_sort_keys on a HOST array: copies h_keys[0..n) to the
  * device, sorts it there and copies it back, then waits for `stream`.  Pinned
  * host memory gives the fastest copies; pageable memory also works.
@@ -152,6 +205,8 @@ typedef struct {
     uint32_t train_steps;    /* full-batch Adam steps; default 24 */
     float learning_rate;     /* Adam step size; default 3e-3 */
     uint32_t model;          /* SR_MODEL_* */
+    uint32_t bucket_config;  /* 1 + the segmented-sort configuration that sorts the
+                                buckets (sr_segmented_config_info); 0: the default */
 } sr_learned_opts;
 
 enum {

@@ -56,7 +56,8 @@ class Stats(ctypes.Structure):
 class LearnedOpts(ctypes.Structure):
     _fields_ = [("num_buckets", ctypes.c_uint32), ("sample_stride", ctypes.c_uint32),
                 ("train_points", ctypes.c_uint32), ("train_steps", ctypes.c_uint32),
-                ("learning_rate", ctypes.c_float), ("model", ctypes.c_uint32)]
+                ("learning_rate", ctypes.c_float), ("model", ctypes.c_uint32),
+                ("bucket_config", ctypes.c_uint32)]
 
 
 # name -> (restype, argtypes) of every entry point declared in include/sortrace.h
@@ -67,6 +68,9 @@ SIGNATURES = {
     "sr_sort_pairs": (_i32, [_vp, _vp, _sz, _i32, _vp]),
     "sr_sort_segmented": (_i32, [_vp, _vp, _sz, _i32, _vp]),
     "sr_sort_segmented_ex": (_i32, [_vp, _sz, _vp, _sz, _i32, _vp]),
+    "sr_sort_segmented_cfg": (_i32, [_vp, _sz, _vp, _sz, _i32, _i32, _vp]),
+    "sr_segmented_num_configs": (_i32, [_i32]),
+    "sr_segmented_config_info": (_i32, [_i32, _i32, _vp]),
     "sr_sort_keys_host": (_i32, [_vp, _sz, _i32, _vp]),
     "sr_sort_keys_noalloc": (_i32, [_vp, _sz, _i32, _vp]),
     "sr_sort_keys_learned": (_i32, [_vp, _sz, _i32, _vp, _vp]),
@@ -83,6 +87,17 @@ SIGNATURES = {
 }
 
 KERNEL_KINDS = ("detect", "reverse", "block_sort", "partition", "merge", "copy", "segmented", "model")
+
+
+class SegmentedConfig(ctypes.Structure):
+    _fields_ = [("strategy", ctypes.c_int32), ("sort_threads", ctypes.c_int32),
+                ("pack_items", ctypes.c_int32), ("tile_items", ctypes.c_int32),
+                ("fan_in", ctypes.c_int32), ("merge_threads", ctypes.c_int32),
+                ("tile_keys", ctypes.c_int64), ("cta_keys", ctypes.c_int64),
+                ("small_keys", ctypes.c_int64), ("ladder", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+SEG_CONFIG_DEFAULT = -1
 
 
 class KernelTime(ctypes.Structure):
@@ -199,10 +214,36 @@ def sort_segmented_ex(keys, offsets, key_type: int | None = None, stream=None):
     return keys
 
 
+def sort_segmented_cfg(keys, offsets, config: int, key_type: int | None = None, stream=None):
+    """sort_segmented_ex under launch configuration `config` (an index of
+    segmented_configs(key_type), or SEG_CONFIG_DEFAULT)."""
+    _cuda_contig(keys, "keys")
+    _cuda_contig(offsets, "offsets")
+    kt = key_type_of(keys) if key_type is None else key_type
+    _check(load().sr_sort_segmented_cfg(keys.data_ptr(), keys.numel(), offsets.data_ptr(),
+                                        max(offsets.numel() - 1, 0), kt, int(config), _stream(stream)),
+           "sr_sort_segmented_cfg")
+    return keys
+
+
+def segmented_configs(key_type: int) -> list:
+    """The segmented sort's launch configurations for a key type, as dicts."""
+    lib = load()
+    out = []
+    for i in range(lib.sr_segmented_num_configs(key_type)):
+        c = SegmentedConfig()
+        _check(lib.sr_segmented_config_info(key_type, i, ctypes.byref(c)), "sr_segmented_config_info")
+        d = {f: getattr(c, f) for f, _ in SegmentedConfig._fields_}
+        d["index"] = i
+        out.append(d)
+    return out
+
+
 def sort_keys_learned(x, key_type: int | None = None, stream=None, **opts):
     """Learned-partition sort of the CUDA tensor x in place; same output as
     sort_keys.  opts: num_buckets, sample_stride, train_points, train_steps,
-    learning_rate, model."""
+    learning_rate, model, bucket_config (1 + a segmented configuration
+    index; 0 for the default)."""
     _cuda_contig(x, "keys")
     kt = key_type_of(x) if key_type is None else key_type
     o = LearnedOpts()

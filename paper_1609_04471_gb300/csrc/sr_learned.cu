@@ -764,16 +764,6 @@ __global__ void k_bucket_check(const typename Key<KT>::T *__restrict__ keys, con
 
 // ------------------------------------------------------------- host
 
-static int sm_count_l() {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-    }
-    return n;
-}
 
 template <int KB> struct UKey;
 template <> struct UKey<4> { enum { KT = SR_KEY_U32 }; };
@@ -791,7 +781,9 @@ static sr_status learned_impl(void *d_keys, size_t n, const sr_learned_opts *o, 
     uint32_t steps = o && o->train_steps ? o->train_steps : 24u;
     const float lr = o && o->learning_rate > 0.f ? o->learning_rate : 3e-3f;
     const uint32_t model = o ? o->model : 0u;
-    if (nb < 16 || nb > (1u << 20) || (nb & (nb - 1)) || model > SR_MODEL_FORCE_BAD || cap < 2 || cap > (1u << 20))
+    const int seg_cfg = o && o->bucket_config ? (int)o->bucket_config - 1 : segmented_default_cfg((int)sizeof(T), true);
+    if (nb < 16 || nb > (1u << 20) || (nb & (nb - 1)) || model > SR_MODEL_FORCE_BAD || cap < 2 || cap > (1u << 20) ||
+        seg_cfg >= segmented_num_configs((int)sizeof(T)))
         return SR_ERR_INVALID_ARG;
     if (model == SR_MODEL_UNTRAINED || model == SR_MODEL_EQUAL_WIDTH) steps = 0;
 
@@ -902,7 +894,7 @@ static sr_status learned_impl(void *d_keys, size_t n, const sr_learned_opts *o, 
         }
         if (st != SR_OK) break;
         // every bucket sorted, kb -> the caller's buffer
-        if ((st = segmented_run<KT>(kb, uk, n, (const int64_t *)boff, nb, s, false, true)) != SR_OK) break;
+        if ((st = segmented_run_cfg<KT>(kb, uk, n, (const int64_t *)boff, nb, s, false, seg_cfg)) != SR_OK) break;
         SR_LAUNCH(SR_KERNEL_MODEL, k_bucket_check<KT>, (unsigned)((nb + 255) / 256), 256, 0, s, uk, boff, (int)nb,
                   N, lc);
         if (cudaMemcpyAsync(ds->last_aux, lc, sizeof(LearnCtrl), cudaMemcpyDeviceToDevice, s) != cudaSuccess) {

@@ -46,13 +46,21 @@ struct CallRecord {
     int aux_kind = 0;               // 3: last_aux holds a segmented call's block, 4: a learned call's
 };
 
-// The segmented sort from `in` to `out` (in == out: in place), defined in
-// sr_segmented.cu; `record` makes it this thread's last call for sr_get_stats;
-// `bucket_mode` sorts small segments one per CTA instead of in packs (for
-// segments of moderate, similar sizes such as learned buckets).
+// The segmented sort from `in` to `out` (in == out: in place) under launch
+// configuration `cfg` (an index into the configurations of the key width;
+// sr_seg_k4.cu / sr_seg_k8.cu); `record` makes it this thread's last call for
+// sr_get_stats.  SR_ERR_INVALID_ARG for an unknown cfg.
 template <int KT>
-sr_status segmented_run(const typename Key<KT>::T *in, typename Key<KT>::T *out, size_t n_keys,
-                        const int64_t *d_off, size_t nseg, cudaStream_t s, bool record, bool bucket_mode);
+sr_status segmented_run_cfg(const typename Key<KT>::T *in, typename Key<KT>::T *out, size_t n_keys,
+                            const int64_t *d_off, size_t nseg, cudaStream_t s, bool record, int cfg);
+// Configurations of the segmented sort per key width, and the two defaults:
+// small segments in packs (general batches) and one CTA per small segment
+// (segments of moderate, similar sizes such as learned buckets).
+int segmented_num_configs(int key_bytes);
+inline int segmented_default_cfg(int key_bytes, bool buckets) {
+    (void)key_bytes;
+    return buckets ? 2 : 0;
+}
 
 // Fill the stats fields of a segmented / learned call from its control block.
 sr_status segmented_stats(const void *aux, sr_stats *out);

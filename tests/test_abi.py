@@ -63,3 +63,27 @@ def test_argument_errors_need_no_device(lib):
     assert lib.sr_sort_pairs(None, None, 1, 0, None) == 0
     assert lib.sr_detect_runs(None, 4, 0, None, None) == 1
     assert lib.sr_get_stats(None) == 1
+
+
+def test_segmented_configs_described_without_gpu():
+    """The configuration table is host data: every entry is consistent and an
+    unknown entry is refused before anything reaches the GPU."""
+    import ctypes
+    import paper_1609_04471_gb300 as sr
+    lib = sr.load()
+    for kt in range(5):
+        n = lib.sr_segmented_num_configs(kt)
+        assert n >= 3
+        for i in range(n):
+            c = sr.SegmentedConfig()
+            assert lib.sr_segmented_config_info(kt, i, ctypes.byref(c)) == 0
+            assert c.tile_keys == c.sort_threads * c.tile_items
+            assert c.cta_keys == c.fan_in * c.tile_keys
+            assert c.fan_in in (1, 2, 4) and c.tile_items % 2 == 1
+            assert c.strategy in (0, 1) and (c.pack_items > 0) == (c.strategy == 0)
+            assert 0 < c.small_keys <= c.cta_keys
+        c = sr.SegmentedConfig()
+        assert lib.sr_segmented_config_info(kt, n, ctypes.byref(c)) == 1
+        assert lib.sr_segmented_config_info(kt, -1, ctypes.byref(c)) == 0     # the default
+        assert lib.sr_sort_segmented_cfg(None, 0, None, 0, kt, n, None) == 1
+    assert lib.sr_segmented_num_configs(9) == 0

@@ -165,3 +165,14 @@ def test_learned_full_size_matches_plain(gpu_lib):
     assert st["fallback"] == 0
     s = np.sort(a)
     assert got.tobytes() == s.tobytes()
+
+
+def test_every_bucket_config_exact(gpu_lib):
+    """The buckets can be sorted under any segmented-sort configuration; the
+    output is the same."""
+    a = si.lognormal_f32((1 << 21) + 5, 14)
+    want = oracle.sort_keys(a).view(np.uint32).tobytes()
+    for cfg in gpu_lib.segmented_configs(2):
+        got, st = _learned(gpu_lib, a, bucket_config=cfg["index"] + 1)
+        assert got.view(np.uint32).tobytes() == want, cfg
+        assert st["fallback"] == 0

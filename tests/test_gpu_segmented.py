@@ -171,3 +171,72 @@ def test_graph_capture_replay(gpu_lib):
         g.replay()
         torch.cuda.synchronize()
         assert work.cpu().numpy().tobytes() == want.tobytes()
+
+
+def _cfg_lengths(rng, cfg):
+    """Segment lengths around every class boundary of a configuration."""
+    small, tile, cta = cfg["small_keys"], cfg["tile_keys"], cfg["cta_keys"]
+    return np.concatenate([
+        rng.integers(0, 40, 200), rng.integers(1, small + 1, 40),
+        [small, small + 1, tile - 1, tile, tile + 1, cta - 1, cta, cta + 1],
+        rng.integers(small + 1, cta + 1, 8), [2 * cta + 5, 5 * cta - 3], [0, 1, 0, 2],
+    ]).astype(np.int64)
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.float32, np.uint64, np.int64])
+def test_every_config_exact(gpu_lib, dtype):
+    """Every launch configuration of the batched sort gives the oracle's
+    result bit for bit, with segments on both sides of each of its class
+    boundaries (small, one tile, one CTA's fan-in, several merge passes)."""
+    import torch
+    kt = KT[np.dtype(dtype)]
+    for cfg in gpu_lib.segmented_configs(kt):
+        rng = np.random.default_rng(50 + cfg["index"])
+        lens = _cfg_lengths(rng, cfg)
+        rng.shuffle(lens)
+        off = _offsets(lens)
+        keys = _rand_keys(rng, int(off[-1]), dtype)
+        tk = _dev(keys)
+        gpu_lib.sort_segmented_cfg(tk, torch.from_numpy(off).cuda(), cfg["index"], key_type=kt)
+        assert gpu_lib.stream_status() == 0
+        got = tk.cpu().numpy().view(dtype)
+        assert got.tobytes() == oracle.sort_segmented(keys, off).tobytes(), cfg
+        assert gpu_lib.stats()["big_segments"] == int(np.sum(lens > cfg["cta_keys"])), cfg
+
+
+def test_every_config_batch_workload(gpu_lib):
+    """The batch workload's shape (lognormal lengths, four input classes) at
+    a size the oracle checks quickly, under every configuration."""
+    import torch
+    keys, off, _ = si.segmented_i32(4000, 12, total=4000 * 600.0)
+    want = oracle.sort_segmented(keys, off).tobytes()
+    to = torch.from_numpy(off).cuda()
+    for cfg in gpu_lib.segmented_configs(0):
+        tk = _dev(keys)
+        gpu_lib.sort_segmented_cfg(tk, to, cfg["index"], key_type=0)
+        assert tk.cpu().numpy().tobytes() == want, cfg
+
+
+def test_autotuner_picks_caches_and_sorts(gpu_lib, tmp_path, monkeypatch):
+    import torch
+    from paper_1609_04471_gb300 import autotune as at
+    keys, off, _ = si.segmented_i32(3000, 13, total=3000 * 600.0)
+    src = _dev(keys)
+    to = torch.from_numpy(off).cuda()
+    path = str(tmp_path / "tune.json")
+    best = at.best_config(src, to, 0, cache_path=path, reps=2)
+    assert torch.equal(src, _dev(keys))            # the tuner sorts copies only
+    n = len(gpu_lib.segmented_configs(0))
+    assert 0 <= best < n
+    entries = at.load_cache(path)
+    (entry,) = entries.values()
+    assert entry["config"] == best and len(entry["ms"]) == n
+    assert min(entry["ms"], key=lambda c: (entry["ms"][c], int(c))) == str(best)
+
+    def no_timing(*a, **k):
+        raise AssertionError("a cached shape must not be timed again")
+    monkeypatch.setattr(at, "time_configs", no_timing)
+    assert at.best_config(src, to, 0, cache_path=path) == best
+    out, c = at.sort_segmented_auto(src, to, 0, cache_path=path)
+    assert c == best
+    assert out.cpu().numpy().tobytes() == oracle.sort_segmented(keys, off).tobytes()
