@@ -52,6 +52,9 @@ def _args():
                     help="skip the pairs / learned / batched measurements")
     ap.add_argument("--profile-case", type=int, default=0, metavar="LOG2N",
                     help="for ncu: sort a uniform int32 array of 2^LOG2N keys twice (warm-up + one) and exit")
+    ap.add_argument("--profile-form", choices=["keys", "learned", "batched"], default="keys",
+                    help="with --profile-case: the learned sort of 2^LOG2N lognormal float32 keys, or the "
+                         "batched sort of 200,000 arrays (LOG2N ignored), instead of the key sort")
     ap.add_argument("--profile-pairs", action="store_true",
                     help="with --profile-case: a stable uint64-key + uint32-payload sort instead")
     return ap.parse_args()
@@ -431,13 +434,28 @@ def run_profile_case(args):
         for _ in range(2):
             xk, xv = src_k.clone(), src_v.clone()
             sr.sort_pairs(xk, xv, key_type=sr.KEY_U64)
+    elif args.profile_form == "learned":
+        src = torch.from_numpy(si.lognormal_f32(n, SEED)).cuda()
+        for _ in range(2):
+            x = src.clone()
+            sr.sort_keys_learned(x)
+    elif args.profile_form == "batched":
+        from paper_1609_04471_gb300 import autotune
+        keys, off, _ = si.segmented_i32(200_000, SEED)
+        src = torch.from_numpy(keys).cuda()
+        toff = torch.from_numpy(off).cuda()
+        best = autotune.select_best(autotune.time_configs(src, toff, sr.KEY_I32, reps=1, warmup=0))
+        for _ in range(2):
+            x = src.clone()
+            sr.sort_segmented_cfg(x, toff, best)
     else:
         src = torch.from_numpy(si.uniform_i32(n, SEED)).cuda()
         for _ in range(2):
             x = src.clone()
             sr.sort_keys(x)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_case": args.profile_case, "pairs": bool(args.profile_pairs), "ok": True}))
+    print(json.dumps({"profile_case": args.profile_case, "pairs": bool(args.profile_pairs),
+                      "form": args.profile_form, "ok": True}))
 
 
 def _timed(torch, stream, fn, restore, reps):

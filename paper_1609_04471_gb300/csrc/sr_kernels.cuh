@@ -85,24 +85,40 @@ __global__ void __launch_bounds__(NT) k_detect(const typename Key<KT>::T *__rest
     }
 }
 
+// Reverses p[0 .. n): 16-byte vectors from both ends when the array is
+// aligned and a whole number of vectors, single elements otherwise.
+template <typename E>
+__device__ __forceinline__ void reverse_array(E *__restrict__ p, long long n, long long gtid, long long stride) {
+    constexpr int VW = 16 / sizeof(E);
+    if ((((uintptr_t)p) & 15) == 0 && n % VW == 0) {
+        uint4 *q = reinterpret_cast<uint4 *>(p);
+        const long long nv = n / VW;
+        for (long long i = gtid; i < (nv + 1) / 2; i += stride) {
+            const long long j = nv - 1 - i;
+            const uint4 x = q[i], y = q[j];
+            // reversed element order inside a vector (i == j: the middle vector, reversed in place)
+            q[i] = VW == 4 ? make_uint4(y.w, y.z, y.y, y.x) : make_uint4(y.z, y.w, y.x, y.y);
+            q[j] = VW == 4 ? make_uint4(x.w, x.z, x.y, x.x) : make_uint4(x.z, x.w, x.x, x.y);
+        }
+    } else {
+        for (long long i = gtid; i < n / 2; i += stride) {
+            const long long j = n - 1 - i;
+            const E a = p[i], b = p[j];
+            p[i] = b;
+            p[j] = a;
+        }
+    }
+}
+
 template <int KT, bool VALS>
 __global__ void k_reverse(typename Key<KT>::T *__restrict__ k, uint32_t *__restrict__ v,
                           long long n, const Ctrl *__restrict__ c) {
     griddep_wait();
     if (call_mode(c, n) != MODE_REVERSE) return;
-    const long long half = n / 2;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < half; i += stride) {
-        const long long j = n - 1 - i;
-        const typename Key<KT>::T a = k[i], b = k[j];
-        k[i] = b;
-        k[j] = a;
-        if (VALS) {
-            const uint32_t x = v[i], y = v[j];
-            v[i] = y;
-            v[j] = x;
-        }
-    }
+    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    reverse_array(k, n, gtid, stride);
+    if (VALS) reverse_array(v, n, gtid, stride);
 }
 
 // Sorts tile blockIdx.x of NT*IPT keys; records the tile's smallest and

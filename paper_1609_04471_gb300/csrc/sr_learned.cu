@@ -237,7 +237,7 @@ k_train(const U *__restrict__ sample, long long m, float *__restrict__ px, float
     __shared__ float th[NPARAM], am[NPARAM], av[NPARAM], gr[NPARAM];
     __shared__ Derived dv;
     __shared__ float acc_w[H], acc_s[H], acc_kn[H], acc_d[H];
-    __shared__ float s_loss;
+    __shared__ float s_lossw[TRAIN_NT / 32];
     __shared__ long long s_np;
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
 
@@ -279,7 +279,6 @@ k_train(const U *__restrict__ sample, long long m, float *__restrict__ px, float
     }
     if (t < NPARAM) { am[t] = 0.f; av[t] = 0.f; }
     if (t < H) { acc_w[t] = 0.f; acc_s[t] = 0.f; acc_kn[t] = 0.f; acc_d[t] = 0.f; }
-    if (t == 0) s_loss = 0.f;
     __syncthreads();
     const long long S = s_np;
     const long long ppt = (S + TRAIN_NT - 1) / TRAIN_NT;
@@ -287,16 +286,29 @@ k_train(const U *__restrict__ sample, long long m, float *__restrict__ px, float
     const int total_steps = mode == TRAIN_GRAD ? 1 : steps + 1;   // the last pass only measures the loss
 
     float b1t = 1.f, b2t = 1.f;                    // running powers of Adam's betas
+    // up to PREG points per thread stay in registers across the steps
+    constexpr int PREG = 8;
+    const bool in_regs = ppt <= PREG;
+    float rx[PREG], rt[PREG];
+#pragma unroll
+    for (int q = 0; q < PREG; ++q) {
+        const long long i = p0 + q;
+        rx[q] = (in_regs && i < p1) ? px[i] : 0.f;
+        rt[q] = (in_regs && i < p1) ? pt[i] : 0.f;
+    }
     if (wid == 0) derive(th, dv, lane, false);
     __syncthreads();
     for (int it = 0; it < total_steps; ++it) {
-        // forward and backward over this thread's (sorted) points
+        // forward and backward over this thread's points; per segment k of the
+        // run of points the thread is in, the partial sums (gw, gs, gkn, gd)
         float loss = 0.f, gw = 0.f, gs = 0.f, gkn = 0.f, gd = 0.f;
         int kc = -1;
         const float gscale = 2.f / (float)S;
-        for (long long i = p0; i < p1; ++i) {
-            const float x = px[i];
-            const int k = segment_of(dv.knot, x);
+        auto point = [&](float x, float tgt) {
+            // points arrive in ascending order: walk on from the last segment
+            int k = kc;
+            if (k < 0 || x < dv.knot[k]) k = segment_of(dv.knot, x);
+            while (k < H - 1 && dv.knot[k + 1] <= x) ++k;
             if (k != kc) {
                 if (kc >= 0) {
                     atomicAdd(&acc_w[kc], gw); atomicAdd(&acc_s[kc], gs);
@@ -308,7 +320,7 @@ k_train(const U *__restrict__ sample, long long m, float *__restrict__ px, float
             const float u = (x - dv.knot[k]) * dv.invd[k];
             const float h = fminf(fmaxf(u, 0.f), 1.f);
             const float y = fmaf(dv.w[k], h, dv.P[k]);
-            const float r = y - pt[i];
+            const float r = y - tgt;
             loss += r * r;
             const float g = gscale * r;
             gs += g;                                  // every unit before k is saturated at 1
@@ -318,16 +330,41 @@ k_train(const U *__restrict__ sample, long long m, float *__restrict__ px, float
                 gkn -= gu * dv.invd[k];               // d u / d x_k = -1/d_k
                 gd -= gu * u * dv.invd[k];            // d u / d d_k = -u/d_k
             }
+        };
+        if (in_regs) {
+#pragma unroll
+            for (int q = 0; q < PREG; ++q)
+                if (p0 + q < p1) point(rx[q], rt[q]);
+        } else {
+            for (long long i = p0; i < p1; ++i) point(px[i], pt[i]);
         }
-        if (kc >= 0) {
+        // the open run of every lane: lanes of one warp hold non-decreasing
+        // segments when the points are sorted, so equal segments are adjacent
+        // lanes; a segmented suffix sum leaves each run's total at its first
+        // lane, which adds it once (otherwise every lane adds its own)
+        const int kprev = __shfl_up_sync(0xffffffffu, kc, 1);
+        const bool ordered = __all_sync(0xffffffffu, lane == 0 || kc < 0 || (kprev >= 0 && kprev <= kc));
+        if (ordered) {
+            for (int o = 1; o < 32; o <<= 1) {
+                const int k2 = __shfl_down_sync(0xffffffffu, kc, o);
+                const float w2 = __shfl_down_sync(0xffffffffu, gw, o);
+                const float s2v = __shfl_down_sync(0xffffffffu, gs, o);
+                const float kn2 = __shfl_down_sync(0xffffffffu, gkn, o);
+                const float d2 = __shfl_down_sync(0xffffffffu, gd, o);
+                if (lane + o < 32 && k2 == kc) { gw += w2; gs += s2v; gkn += kn2; gd += d2; }
+            }
+        }
+        if (kc >= 0 && (!ordered || lane == 0 || kprev != kc)) {
             atomicAdd(&acc_w[kc], gw); atomicAdd(&acc_s[kc], gs);
             atomicAdd(&acc_kn[kc], gkn); atomicAdd(&acc_d[kc], gd);
         }
         for (int o = 16; o; o >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, o);
-        if (lane == 0) atomicAdd(&s_loss, loss);
+        if (lane == 0) s_lossw[wid] = loss;
         __syncthreads();
         if (wid == 0) {
-            const float Lmean = s_loss / (float)S;
+            float lsum = s_lossw[lane];
+            for (int o = 16; o; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+            const float Lmean = lsum / (float)S;
             // dL/dw_j = acc_w[j] + sum_{k > j} acc_s[k]
             float suf = acc_s[lane];
             for (int o = 1; o < 32; o <<= 1) {                 // inclusive suffix sum
@@ -372,7 +409,6 @@ k_train(const U *__restrict__ sample, long long m, float *__restrict__ px, float
                 derive(th, dv, lane, false);       // the next step's tables
             }
             acc_w[lane] = 0.f; acc_s[lane] = 0.f; acc_kn[lane] = 0.f; acc_d[lane] = 0.f;
-            if (lane == 0) s_loss = 0.f;
         }
         __syncthreads();
     }
@@ -445,14 +481,22 @@ k_split_tiles(const long long *__restrict__ seg_off, int S, int *__restrict__ ti
     }
     __syncthreads();
     const int before = (wid ? s_warp[wid - 1] : 0) + x - cnt;
-    s_cnt[t] = before;
+    s_cnt[t] = t < S ? before : s_warp[31];
     if (t < S) tile_base[t] = before;
     if (t == S - 1) tile_base[S] = before + cnt;
     __syncthreads();
-    for (int q = 0; q < S; ++q) {
-        const int base = s_cnt[q];
-        const int c = (q + 1 < S ? s_cnt[q + 1] : s_warp[31]) - base;
-        for (int tl = t; tl < c; tl += blockDim.x) { tile_seg[base + tl] = q; tile_local[base + tl] = tl; }
+    // every tile finds its segment: the last s with s_cnt[s] <= tile (bases are
+    // non-decreasing; empty segments share their base with the next one)
+    const int total = s_warp[31];
+    for (int tile = t; tile < total; tile += blockDim.x) {
+        int lo = 0, hi = S - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_cnt[mid] <= tile) lo = mid;
+            else hi = mid - 1;
+        }
+        tile_seg[tile] = lo;
+        tile_local[tile] = tile - s_cnt[lo];
     }
 }
 
@@ -470,12 +514,14 @@ k_split_hist(const typename Key<KT>::T *__restrict__ in, const BT *__restrict__ 
              const LearnCtrl *__restrict__ lc, unsigned int *__restrict__ counts) {
     griddep_wait();
     extern __shared__ __align__(16) unsigned char smem[];
-    unsigned int *hist = reinterpret_cast<unsigned int *>(smem);
+    constexpr int NW = SPLIT_NT / 32;
+    unsigned int *hall = reinterpret_cast<unsigned int *>(smem);     // [NW][D]: one histogram per warp
     __shared__ RouteSmem rs;
     const int tile = blockIdx.x;
     if (tile >= tile_base[S]) return;
     if (level == 1) load_route(lc->r, rs);
-    for (int d = threadIdx.x; d < D; d += SPLIT_NT) hist[d] = 0u;
+    for (int d = threadIdx.x; d < NW * D; d += SPLIT_NT) hall[d] = 0u;
+    unsigned int *hist = hall + (threadIdx.x >> 5) * D;
     __syncthreads();
     const int s = tile_seg[tile], tl = tile_local[tile];
     const int nt = tile_base[s + 1] - tile_base[s];
@@ -514,7 +560,12 @@ k_split_hist(const typename Key<KT>::T *__restrict__ in, const BT *__restrict__ 
     }
     __syncthreads();
     const long long base_e = (long long)D * tile_base[s];
-    for (int d = threadIdx.x; d < D; d += SPLIT_NT) counts[base_e + (long long)d * nt + tl] = hist[d];
+    for (int d = threadIdx.x; d < D; d += SPLIT_NT) {
+        unsigned int c = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) c += hall[w * D + d];
+        counts[base_e + (long long)d * nt + tl] = c;
+    }
 }
 
 // Moves one tile's keys (and, at level 1, their bucket ids) to the level's
@@ -565,8 +616,8 @@ k_split_scatter(const typename Key<KT>::T *__restrict__ in, const BT *__restrict
     }
     __syncthreads();
     const unsigned int before = (wid ? s_warp[wid - 1] : 0u) + x - (c0 + c1);
-    if (d0 < D) { tstart[d0] = before; taken[d0] = 0u; gbase[d0] = pos[base_e + (long long)d0 * nt + tl]; }
-    if (d1 < D) { tstart[d1] = before + c0; taken[d1] = 0u; gbase[d1] = pos[base_e + (long long)d1 * nt + tl]; }
+    if (d0 < D) { tstart[d0] = before; taken[d0] = before; gbase[d0] = pos[base_e + (long long)d0 * nt + tl]; }
+    if (d1 < D) { tstart[d1] = before + c0; taken[d1] = before + c0; gbase[d1] = pos[base_e + (long long)d1 * nt + tl]; }
     if (t == 0) tstart[D] = s_warp[SPLIT_NT / 32 - 1];
     __syncthreads();
     const long long start = seg_off[s] + (long long)tl * SPLIT_T;
@@ -586,10 +637,10 @@ k_split_scatter(const typename Key<KT>::T *__restrict__ in, const BT *__restrict
         for (int j = 0; j < SPLIT_BATCH; ++j) {
             if (full || i0 + j * SPLIT_NT < cnt) {
                 const int d = level == 1 ? ((int)bb[j] >> s2) : ((int)bb[j] & mask2);
-                const unsigned int q = tstart[d] + atomicAdd(&taken[d], 1u);
-                if (q < tstart[d + 1]) {
+                const unsigned int q = atomicAdd(&taken[d], 1u);     // taken[d] starts at the digit's stretch
+                if (q < (unsigned int)cnt) {
                     stage_k[q] = k[j];
-                    stage_b[q] = bb[j];
+                    if (level == 1) stage_b[q] = bb[j];
                 } else {
                     // impossible: the counts came from the same ids
                     atomicExch(&lc->fallback, 1);
@@ -599,12 +650,14 @@ k_split_scatter(const typename Key<KT>::T *__restrict__ in, const BT *__restrict
         }
     }
     __syncthreads();
-    for (int q = t; q < cnt; q += SPLIT_NT) {
-        const BT b = stage_b[q];
-        const int d = level == 1 ? ((int)b >> s2) : ((int)b & mask2);
-        const unsigned long long g = gbase[d] + (q - tstart[d]);
-        out[g] = stage_k[q];
-        if (level == 1) bid_out[g] = b;
+    // one warp per digit stretch: contiguous shared reads, contiguous global writes
+    for (int d = wid; d < D; d += SPLIT_NT / 32) {
+        const unsigned int q0 = tstart[d], q1 = tstart[d + 1];
+        const unsigned long long g0 = gbase[d];
+        for (unsigned int q = q0 + lane; q < q1; q += 32) {
+            out[g0 + (q - q0)] = stage_k[q];
+            if (level == 1) bid_out[g0 + (q - q0)] = stage_b[q];
+        }
     }
 }
 
@@ -869,7 +922,14 @@ static sr_status learned_impl(void *d_keys, size_t n, const sr_learned_opts *o, 
             // level 1 writes the bucket ids (ba) beside the keys; they move with the keys (bb)
             const BT *bin = level == 1 ? ba : bb;
             SR_LAUNCH(SR_KERNEL_MODEL, k_split_tiles, 1, 1024, 0, s, segs, S, tb, tseg, tloc);
-            SR_LAUNCH(SR_KERNEL_MODEL, (k_split_hist<KT, BT>), grid, SPLIT_NT, (size_t)D * 4, s, in, bin, ba, segs,
+            const size_t h_smem = (size_t)(SPLIT_NT / 32) * D * 4;
+            if (h_smem > 48 * 1024 &&
+                cudaFuncSetAttribute((const void *)k_split_hist<KT, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)h_smem) != cudaSuccess) {
+                st = launch_status();
+                break;
+            }
+            SR_LAUNCH(SR_KERNEL_MODEL, (k_split_hist<KT, BT>), grid, SPLIT_NT, h_smem, s, in, bin, ba, segs,
                       S, tb, tseg, tloc, level, D, s2, lc, cnt);
             SR_LAUNCH(SR_KERNEL_MODEL, k_scan_sums, sgrid, 1024, 0, s, cnt, tb, S, D, sums);
             SR_LAUNCH(SR_KERNEL_MODEL, k_scan_top, 1, 1024, 0, s, sums, tb, S, D);

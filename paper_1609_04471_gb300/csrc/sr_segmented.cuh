@@ -143,6 +143,20 @@ __device__ __forceinline__ int dev_ceil_log2(long long x) {
 // Packs mode: marks the first segment of every chunk and lists medium and big
 // segments.  Bucket mode: lists every segment under the smallest small shape
 // that holds it (lists[cls * nseg + i]), or as medium or big; no packs.
+// Appends s to a list through one atomic per warp and list: the lanes that
+// append to `counter` (all lanes of the warp call this with `take` set or not)
+// get consecutive slots from the lowest lane's single atomicAdd.
+__device__ __forceinline__ void warp_append(bool take, unsigned int *counter, unsigned int *list, unsigned int s) {
+    const unsigned int lanes = __ballot_sync(0xffffffffu, take);
+    if (!take) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(lanes) - 1;
+    unsigned int base = 0;
+    if (lane == leader) base = atomicAdd(counter, (unsigned int)__popc(lanes));
+    base = __shfl_sync(lanes, base, leader);
+    list[base + __popc(lanes & ((1u << lane) - 1u))] = s;
+}
+
 static __global__ void k_seg_classify(const int64_t *__restrict__ off, long long nseg, long long nkeys, int chunk,
                                int tile, long long nchunks, int *__restrict__ chunk_first,
                                unsigned int *__restrict__ medium, unsigned int *__restrict__ big,
@@ -150,23 +164,35 @@ static __global__ void k_seg_classify(const int64_t *__restrict__ off, long long
                                SegCtrl *__restrict__ c) {
     griddep_wait();
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= nseg) return;
-    const long long a = off[s], b = off[s + 1];
-    const long long prev = s > 0 ? off[s - 1] : 0;
-    if (b < a || a < 0 || b > nkeys || prev > a) {
-        atomicExch(&c->status, (int)SR_ERR_BAD_SEGMENTS);
-        return;
+    const bool live = s < nseg;                    // every lane stays to the end (warp-wide appends)
+    long long a = 0, b = 0, prev = 0;
+    if (live) {
+        a = off[s];
+        b = off[s + 1];
+        prev = s > 0 ? off[s - 1] : 0;
     }
+    const bool bad = live && (b < a || a < 0 || b > nkeys || prev > a);
+    if (bad) atomicExch(&c->status, (int)SR_ERR_BAD_SEGMENTS);
+    const bool ok = live && !bad;
     const long long len = b - a;
     if (bucket_mode) {
-        if (len < 1) return;                       // (a single key still moves when in != out)
-        for (int cls = 0; cls < NSMALL; ++cls) {
-            if (len <= small_cap(ladder, cls)) {
-                lists[(long long)cls * nseg + atomicAdd(&c->n_small[cls], 1u)] = (unsigned int)s;
-                return;
-            }
-        }
-    } else {
+        // (a single key still moves when in != out)
+        int cls = NSMALL;
+        if (ok && len >= 1)
+            for (int q = NSMALL - 1; q >= 0; --q)
+                if (len <= small_cap(ladder, q)) cls = q;
+#pragma unroll
+        for (int q = 0; q < NSMALL; ++q)
+            warp_append(cls == q, &c->n_small[q], lists + (long long)q * nseg, (unsigned int)s);
+        const bool med = ok && cls == NSMALL && len > chunk && len <= tile;
+        const bool bg = ok && cls == NSMALL && len > tile;
+        warp_append(med, &c->n_medium, medium, (unsigned int)s);
+        warp_append(bg, &c->n_big, big, (unsigned int)s);
+        if (bg) atomicAdd(&c->big_keys, (unsigned long long)len);
+        return;
+    }
+    if (!ok) return;
+    {
         // chunks (chunk of the previous start, chunk of this start] begin with s
         const long long cs = a / chunk;
         const long long cp = s > 0 ? prev / chunk : -1;
