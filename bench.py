@@ -55,6 +55,8 @@ def _args():
     ap.add_argument("--profile-form", choices=["keys", "learned", "batched"], default="keys",
                     help="with --profile-case: the learned sort of 2^LOG2N lognormal float32 keys, or the "
                          "batched sort of 200,000 arrays (LOG2N ignored), instead of the key sort")
+    ap.add_argument("--profile-config", type=int, default=-1,
+                    help="with --profile-form batched: this launch configuration instead of tuning")
     ap.add_argument("--profile-pairs", action="store_true",
                     help="with --profile-case: a stable uint64-key + uint32-payload sort instead")
     return ap.parse_args()
@@ -444,7 +446,9 @@ def run_profile_case(args):
         keys, off, _ = si.segmented_i32(200_000, SEED)
         src = torch.from_numpy(keys).cuda()
         toff = torch.from_numpy(off).cuda()
-        best = autotune.select_best(autotune.time_configs(src, toff, sr.KEY_I32, reps=1, warmup=0))
+        best = args.profile_config
+        if best < 0:
+            best = autotune.select_best(autotune.time_configs(src, toff, sr.KEY_I32, reps=1, warmup=0))
         for _ in range(2):
             x = src.clone()
             sr.sort_segmented_cfg(x, toff, best)
