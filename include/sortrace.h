@@ -260,7 +260,9 @@ typedef struct {
     int32_t merge_tile;         /* output keys per merge CTA */
     int32_t passes_planned;     /* merge passes launched */
     int32_t passes_skipped;     /* passes found already in order (no bytes moved) */
-    int32_t input_class;        /* 0 unsorted, 1 sorted, 2 strictly descending */
+    int32_t input_class;        /* 0 unsorted, 1 sorted, 2 strictly descending,
+                                   3 at most 64 distinct keys (4-byte keys, keys only:
+                                   counted per distinct key and written as runs) */
     int32_t fallback;           /* learned: 1 if the bucket check failed */
     uint64_t runs;              /* Run(A) of the input, from the scan */
     uint64_t bytes_moved;       /* DRAM bytes the executed passes read + wrote */

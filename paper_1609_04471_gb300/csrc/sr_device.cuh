@@ -233,8 +233,10 @@ __device__ __forceinline__ void block_sort(U (&k)[IPT], uint32_t (&v)[IPT], U *s
 
 // ------------------------------------------------------- per-call control
 
-enum { MODE_SORT = 0, MODE_SORTED = 1, MODE_REVERSE = 2 };
+enum { MODE_SORT = 0, MODE_SORTED = 1, MODE_REVERSE = 2, MODE_FEW = 3 };
 enum { MAX_PASSES = 48 };
+// Few distinct keys: at most FEW_MAX distinct order images (4-byte keys).
+enum { FEW_MAX = 64, FEW_SLOTS = 128 };
 
 // Lives in the call's scratch; zeroed at the start of every call.
 struct Ctrl {
@@ -248,12 +250,51 @@ struct Ctrl {
     // written by the pass planner once every unordered[p] is final: which
     // buffer (0 = caller's, 1 = scratch) holds the data before pass p
     signed char src_buf[MAX_PASSES + 1];
+    // Few distinct keys (4-byte keys, keys only): a sample of the keys goes
+    // into a hash set of order images (each slot holds image + 1; 0 is empty)
+    // until more than FEW_MAX appear (few_over); the counting pass then checks
+    // every key against it.
+    int few_over;
+    unsigned int few_n;                          // distinct images in the set
+    unsigned int few_ticket;                     // CTAs of the sampling kernel that finished
+    int few_cand;                                // the set is a candidate (sorted into few_sorted)
+    int few_miss;                                // some key is not in the set
+    int few_active;                              // the call took MODE_FEW (output written)
+    unsigned long long few_slot[FEW_SLOTS];
+    unsigned int few_sorted[FEW_MAX];            // the distinct images, ascending
+    unsigned long long few_count[FEW_MAX];       // keys equal to each
 };
 
 __device__ __forceinline__ int call_mode(const Ctrl *c, long long n) {
     if (c->descents == 0) return MODE_SORTED;
     if (c->nondescents == 0 && n > 1) return MODE_REVERSE;
+    if (c->few_active) return MODE_FEW;
     return MODE_SORT;
+}
+
+// Inserts order image u into the hash set `set` (FEW_SLOTS slots of image + 1,
+// 0 = empty) shared by the threads that can see it; `cnt` counts distinct
+// images and `over` is raised past `limit` of them (or after 16 probes, which
+// with at most 64 of 128 slots used is rare and only costs the fast path).  No
+// waiting on other threads.
+__device__ __forceinline__ void few_insert(unsigned long long *set, unsigned int *cnt, int *over, unsigned int u,
+                                           unsigned int limit = FEW_MAX) {
+    const unsigned long long v = (unsigned long long)u + 1ull;
+    const unsigned int h = (u * 2654435761u) >> 25;          // 7 bits: FEW_SLOTS = 128
+    for (int probe = 0; probe < 16; ++probe) {               // a longer probe counts as "too many"
+        const unsigned int i = (h + probe) & (FEW_SLOTS - 1);
+        const unsigned long long cur = ((volatile unsigned long long *)set)[i];
+        if (cur == v) return;
+        if (cur == 0ull) {
+            const unsigned long long prev = atomicCAS(set + i, 0ull, v);
+            if (prev == 0ull) {
+                if (atomicAdd(cnt, 1u) + 1u > limit) atomicExch(over, 1);
+                return;
+            }
+            if (prev == v) return;
+        }
+    }
+    atomicExch(over, 1);
 }
 
 }  // namespace sr

@@ -5,6 +5,10 @@
 
 #include "sr_device.cuh"
 
+#ifndef SR_FEW_KEYS
+#define SR_FEW_KEYS 1       // the few-distinct-keys path (4-byte keys, keys only)
+#endif
+
 namespace sr {
 
 // ------------------------------------------------------------- kernels
@@ -82,6 +86,155 @@ __global__ void __launch_bounds__(NT) k_detect(const typename Key<KT>::T *__rest
         if (red[1]) atomicAdd(&c->nondescents, (unsigned long long)red[1]);
         if (!red[2]) atomicAdd(&c->tiles_ascending, 1ull);
         if (!red[3]) atomicAdd(&c->tiles_descending, 1ull);
+    }
+}
+
+// Few distinct keys, step 1: FEW_SAMPLE keys spread over the whole array go
+// into the call's set of distinct order images (until more than FEW_MAX
+// appear); the last CTA to finish (a ticket after a fence) then, if the call
+// would sort and the set is small, sorts the set into few_sorted as the
+// candidate.  The counting pass checks every key against the set, so a
+// sample that misses a key only costs that pass.  This is the k-way form of
+// the fat (3-way) partition of the paper's quicksorts: keys equal to a pivot
+// need no further comparisons.
+enum { FEW_SAMPLE = 4096, FEW_NT = 256 };
+static_assert(FEW_NT >= FEW_SLOTS, "one thread per set slot");
+template <int KT>
+__global__ void __launch_bounds__(FEW_NT) k_few_sample(const typename Key<KT>::T *__restrict__ keys, long long n,
+                                                       Ctrl *__restrict__ c, const int *__restrict__ gate) {
+    griddep_wait();
+    __shared__ unsigned int s_v[FEW_MAX];
+    __shared__ unsigned int s_k;
+    __shared__ int s_last;
+    if (gate && *gate == 0) return;
+    const int t = threadIdx.x;
+    const long long i = (long long)blockIdx.x * FEW_NT + t;
+    if (i < FEW_SAMPLE && n > 0 && !((volatile int *)&c->few_over)[0])
+        few_insert(c->few_slot, &c->few_n, &c->few_over, (unsigned int)Key<KT>::ord(__ldg(keys + (i * n) / FEW_SAMPLE)));
+    __syncthreads();
+    if (t == 0) {
+        __threadfence();
+        s_last = atomicAdd(&c->few_ticket, 1u) == gridDim.x - 1;
+        s_k = 0u;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (call_mode(c, n) != MODE_SORT) return;
+    const int over = ((volatile int *)&c->few_over)[0];
+    const unsigned int nd = ((volatile unsigned int *)&c->few_n)[0];
+    if (over || nd == 0u || nd > (unsigned int)FEW_MAX) return;
+    if (t < FEW_SLOTS) {
+        const unsigned long long v = ((volatile unsigned long long *)c->few_slot)[t];
+        if (v != 0ull) {
+            const unsigned int q = atomicAdd(&s_k, 1u);
+            if (q < (unsigned int)FEW_MAX) s_v[q] = (unsigned int)(v - 1ull);
+        }
+    }
+    __syncthreads();
+    const unsigned int k = s_k;
+    if (k != nd) return;                           // cannot happen; the ordinary sort then runs
+    if (t < (int)k) {
+        unsigned int r = 0;
+        for (unsigned int q = 0; q < k; ++q) r += s_v[q] < s_v[t];
+        c->few_sorted[r] = s_v[t];
+    }
+    __syncthreads();
+    if (t == 0) c->few_cand = 1;
+}
+
+// Few distinct keys, step 2: counts the keys equal to each candidate image (a
+// binary search over at most FEW_MAX images per key, warp-aggregated adds);
+// a key outside the set raises few_miss and the ordinary sort runs instead.
+template <int KT>
+__global__ void __launch_bounds__(256) k_few_count(const typename Key<KT>::T *__restrict__ keys, long long n,
+                                                   Ctrl *__restrict__ c) {
+    griddep_wait();
+    typedef Key<KT> K;
+    __shared__ unsigned int s_v[FEW_MAX];
+    __shared__ unsigned int s_h[FEW_MAX];
+    if (!c->few_cand) return;
+    const int t = threadIdx.x;
+    const int k = (int)c->few_n;
+    if (t < FEW_MAX) { s_v[t] = t < k ? c->few_sorted[t] : 0xffffffffu; s_h[t] = 0u; }
+    __syncthreads();
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long nr = (n + 31) / 32 * 32;       // whole warps in every iteration
+    for (long long i = (long long)blockIdx.x * blockDim.x + t; i < nr; i += stride) {
+        int j = -1;
+        if (i < n) {
+            const unsigned int u = (unsigned int)K::ord(__ldg(keys + i));
+            int lo = 0, hi = k - 1;                // the last image <= u
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_v[mid] <= u) lo = mid;
+                else hi = mid - 1;
+            }
+            j = lo;
+            if (s_v[lo] != u) {                    // not in the sample's set
+                if (!((volatile int *)&c->few_miss)[0]) atomicExch(&c->few_miss, 1);
+                j = -1;
+            }
+        }
+        const unsigned int peers = __match_any_sync(0xffffffffu, j);
+        if (j >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&s_h[j], (unsigned int)__popc(peers));
+    }
+    __syncthreads();
+    if (t < k && s_h[t]) atomicAdd(&c->few_count[t], (unsigned long long)s_h[t]);
+}
+
+// Few distinct keys, step 3: when every key was in the set, writes the sorted
+// output, each distinct key repeated its count times (16-byte stores when the
+// array is aligned), and switches the call to MODE_FEW: every later kernel of
+// the ordinary sequence then returns at once.
+template <int KT>
+__global__ void __launch_bounds__(256) k_few_write(typename Key<KT>::T *__restrict__ keys, long long n,
+                                                   Ctrl *__restrict__ c) {
+    griddep_wait();
+    typedef Key<KT> K;
+    typedef typename K::T T;
+    __shared__ unsigned long long s_start[FEW_MAX + 1];
+    __shared__ T s_key[FEW_MAX];
+    if (!c->few_cand || c->few_miss) return;
+    const int t = threadIdx.x;
+    if (blockIdx.x == 0 && t == 0) c->few_active = 1;
+    const int k = (int)c->few_n;
+    if (t == 0) {
+        unsigned long long a = 0;
+        for (int q = 0; q < k; ++q) { s_start[q] = a; a += c->few_count[q]; }
+        for (int q = k; q <= FEW_MAX; ++q) s_start[q] = a;
+    }
+    if (t < k) s_key[t] = K::unord((typename K::U)c->few_sorted[t]);
+    __syncthreads();
+    // the last q with s_start[q] <= i
+    auto which = [&](long long i) {
+        int lo = 0, hi = k - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((long long)s_start[mid] <= i) lo = mid;
+            else hi = mid - 1;
+        }
+        return lo;
+    };
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long gtid = (long long)blockIdx.x * blockDim.x + t;
+    if ((((uintptr_t)keys) & 15) == 0) {
+        const long long nv = n / 4;
+        uint4 *q4 = reinterpret_cast<uint4 *>(keys);
+        for (long long v = gtid; v < nv; v += stride) {
+            const long long i = 4 * v;
+            int j = which(i);
+            uint32_t e[4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                while (j + 1 < k && (long long)s_start[j + 1] <= i + m) ++j;
+                e[m] = (uint32_t)s_key[j];
+            }
+            q4[v] = make_uint4(e[0], e[1], e[2], e[3]);
+        }
+        for (long long i = 4 * nv + gtid; i < n; i += stride) keys[i] = s_key[which(i)];
+    } else {
+        for (long long i = gtid; i < n; i += stride) keys[i] = s_key[which(i)];
     }
 }
 

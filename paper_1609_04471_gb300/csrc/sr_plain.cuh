@@ -3,6 +3,10 @@
 // sr_sort_keys_noalloc (a fixed device array).
 //
 //   k_detect      run-detection scan: descents and non-descents (Run(A)).
+//   k_few_sample  at most 64 distinct keys in a 4,096-key sample (4-byte
+//                 keys only): k_few_count checks every key against them and
+//                 counts each; if all were in the set, k_few_write writes the
+//                 runs and nothing else runs.
 //   k_reverse     strictly descending input: one reversal, nothing else runs.
 //   k_block_sort  tiles of SORT_NT*IPT keys sorted in shared memory (ascending
 //                 tiles kept, strictly descending tiles reversed); records each
@@ -73,8 +77,16 @@ template <int KT, bool VALS> struct PlainSort {
             if (cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s) != cudaSuccess) { st = launch_status(); break; }
             SR_LAUNCH(SR_KERNEL_DETECT, (k_detect<KT, SNT, IPT>), (unsigned)tiles, SNT, 0, s,
                       uk, n, ctrl, gate);
+            constexpr bool FEW = sizeof(T) == 4 && !VALS && SR_FEW_KEYS;   // few distinct keys: written as runs
+            if constexpr (FEW)
+                SR_LAUNCH(SR_KERNEL_DETECT, k_few_sample<KT>, FEW_SAMPLE / FEW_NT, FEW_NT, 0, s, uk, n, ctrl, gate);
             SR_LAUNCH(SR_KERNEL_REVERSE, (k_reverse<KT, VALS>), grid_for(n / 2, 256, 152 * 16), 256, 0, s,
                       uk, uv, n, ctrl);
+            if constexpr (FEW) {
+                SR_LAUNCH(SR_KERNEL_COPY, k_few_count<KT>, grid_for(n, 256, 152 * 8), 256, 0, s, uk, n, ctrl);
+                SR_LAUNCH(SR_KERNEL_COPY, k_few_write<KT>, grid_for(n / 4 + 1, 256, 152 * 8), 256, 0, s, uk, n,
+                          ctrl);
+            }
             const size_t bs_smem = (size_t)TS * (sizeof(U) + (VALS ? 4 : 0));
             if ((st = allow_smem(k_block_sort<KT, SNT, IPT, VALS>, bs_smem)) != SR_OK) break;
             SR_LAUNCH(SR_KERNEL_BLOCK_SORT, (k_block_sort<KT, SNT, IPT, VALS>), (unsigned)tiles, SNT,

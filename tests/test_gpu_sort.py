@@ -237,3 +237,42 @@ def test_oom_injection(gpu_lib, monkeypatch):
     monkeypatch.delenv("SR_INJECT_OOM")
     torch.cuda.synchronize()
     assert torch.equal(a, before)
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.uint32, np.float32])
+def test_few_distinct_keys(gpu_lib, dtype):
+    """At most 64 distinct keys (4-byte keys): a 4,096-key sample spread over
+    the array builds the set of distinct keys; when it holds every key the call
+    counts them and writes runs (input_class 3, 12 bytes per key moved).  65 or
+    more distinct keys, or a key the sample missed, take the ordinary sort.
+    Output bit-exact against the oracle either way, including float32 -0.0 /
+    +0.0 as distinct keys."""
+    rng = np.random.default_rng(60)
+    for d, n in ((2, 1000), (16, 1 << 20), (64, (1 << 20) + 3), (64, 12345), (65, 300_001), (1000, 300_001)):
+        vals = _random(rng, d, dtype)
+        if dtype == np.float32 and d >= 2:
+            vals[:2] = np.array([0x00000000, 0x80000000], np.uint32).view(np.float32)
+        vals = np.unique(vals.view({4: np.uint32}[4])).view(dtype)
+        a = vals[rng.integers(0, vals.size, n)]
+        got = _gpu_sort(gpu_lib, a)
+        assert got.tobytes() == oracle.sort_keys(a).tobytes(), (dtype, d, n)
+        st = gpu_lib.stats()
+        if vals.size <= 64 and n >= 1000 * vals.size:
+            # every distinct key is in the sample (4,096 draws)
+            assert st["input_class"] == 3 and st["bytes_moved"] == 12 * n, (d, n, st["input_class"])
+        elif vals.size > 64:
+            assert st["input_class"] == 0
+    # the 65th distinct key appears once, at the end: the sample misses it, the
+    # counting pass finds it and the ordinary sort runs
+    a = np.concatenate([np.repeat(np.arange(64, dtype=np.int32) * 7, 5000), np.array([3], np.int32)])
+    rng.shuffle(a[:-1])
+    got = _gpu_sort(gpu_lib, a)
+    assert got.tobytes() == oracle.sort_keys(a).tobytes()
+    assert gpu_lib.stats()["input_class"] == 0
+    # pairs never take this path (payloads must move with their keys)
+    k = np.repeat(np.arange(8, dtype=np.int32), 1000)[::-1].copy()
+    rng.shuffle(k)
+    v = np.arange(k.size, dtype=np.uint32)
+    gk, gv = _gpu_pairs(gpu_lib, k, v)
+    ok, ov = oracle.sort_pairs(k, v)
+    assert gk.tobytes() == ok.tobytes() and gv.tobytes() == ov.tobytes()
