@@ -126,7 +126,8 @@ sr_status sr_sort_segmented_ex(void *d_keys, size_t n_keys, const int64_t *d_off
  *                  smallest of five fixed shapes per small segment (<= 3840
  *                  keys), from ladder `ladder`: 0 = 128x9, 128x15, 256x9,
  *                  256x11, 256x15 (threads x keys per thread); 1 = 64x9,
- *                  128x9, 128x15, 256x11, 256x15.
+ *                  128x9, 128x15, 256x11, 256x15; 2 = 128x13, 128x17,
+ *                  128x19, 128x23, 256x15.
  *   sort_threads   threads of the persistent sort CTA.
  *   pack_items     composite keys per thread of a pack (strategy 0; else 0).
  *   tile_items     keys per thread of a block-sort tile; tile_keys =
@@ -201,9 +202,9 @@ sr_status sr_sort_keys_noalloc(void *d_keys, size_t n, sr_key_type kt, sr_stream
 typedef struct {
     uint32_t num_buckets;    /* power of two in [2^4, 2^20]; default 2^16 */
     uint32_t sample_stride;  /* one key in sample_stride is sampled; default 100 */
-    uint32_t train_points;   /* points of the sorted sample used in training; default 4096 */
-    uint32_t train_steps;    /* full-batch Adam steps; default 24 */
-    float learning_rate;     /* Adam step size; default 3e-3 */
+    uint32_t train_points;   /* points of the sorted sample used in training; default 2048 */
+    uint32_t train_steps;    /* full-batch Adam steps; default 16 */
+    float learning_rate;     /* Adam step size; default 1e-3 */
     uint32_t model;          /* SR_MODEL_* */
     uint32_t bucket_config;  /* 1 + the segmented-sort configuration that sorts the
                                 buckets (sr_segmented_config_info); 0: the default */

@@ -830,9 +830,9 @@ static sr_status learned_impl(void *d_keys, size_t n, const sr_learned_opts *o, 
     constexpr int KTU = UKey<sizeof(U)>::KT;
     const uint32_t nb = o && o->num_buckets ? o->num_buckets : (1u << 16);
     const uint32_t stride = o && o->sample_stride ? o->sample_stride : 100u;
-    const uint32_t cap = o && o->train_points ? o->train_points : 4096u;
-    uint32_t steps = o && o->train_steps ? o->train_steps : 24u;
-    const float lr = o && o->learning_rate > 0.f ? o->learning_rate : 3e-3f;
+    const uint32_t cap = o && o->train_points ? o->train_points : 2048u;
+    uint32_t steps = o && o->train_steps ? o->train_steps : 16u;
+    const float lr = o && o->learning_rate > 0.f ? o->learning_rate : 1e-3f;
     const uint32_t model = o ? o->model : 0u;
     const int seg_cfg = o && o->bucket_config ? (int)o->bucket_config - 1 : segmented_default_cfg((int)sizeof(T), true);
     if (nb < 16 || nb > (1u << 20) || (nb & (nb - 1)) || model > SR_MODEL_FORCE_BAD || cap < 2 || cap > (1u << 20) ||

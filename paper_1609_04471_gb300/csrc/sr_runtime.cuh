@@ -58,8 +58,8 @@ sr_status segmented_run_cfg(const typename Key<KT>::T *in, typename Key<KT>::T *
 // (segments of moderate, similar sizes such as learned buckets).
 int segmented_num_configs(int key_bytes);
 inline int segmented_default_cfg(int key_bytes, bool buckets) {
-    (void)key_bytes;
-    return buckets ? 2 : 0;
+    // buckets: 4-byte keys take the ladder sized for learned buckets (~2,048 keys)
+    return buckets ? (key_bytes == 4 ? 7 : 2) : 0;
 }
 
 // Fill the stats fields of a segmented / learned call from its control block.

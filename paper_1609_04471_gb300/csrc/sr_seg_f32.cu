@@ -15,10 +15,11 @@ static sr_status run_k4(const uint32_t *in, uint32_t *out, size_t n, const int64
     case 4: return segmented_run_t<KT, SegK4_4>(in, out, n, off, nseg, s, record);
     case 5: return segmented_run_t<KT, SegK4_5>(in, out, n, off, nseg, s, record);
     case 6: return segmented_run_t<KT, SegK4_6>(in, out, n, off, nseg, s, record);
+    case 7: return segmented_run_t<KT, SegK4_7>(in, out, n, off, nseg, s, record);
     default: return SR_ERR_INVALID_ARG;
     }
 }
-static_assert(SEG_NCFG_K4 == 7, "every configuration needs a case");
+static_assert(SEG_NCFG_K4 == 8, "every configuration needs a case");
 
 template <>
 sr_status segmented_run_cfg<SR_KEY_F32>(const uint32_t *in, uint32_t *out, size_t n, const int64_t *off, size_t nseg,

@@ -41,6 +41,7 @@ static sr_status describe_cfg(int key_bytes, int cfg, sr_segmented_config *out) 
         case 4: *out = describe<SegK4_4>(); return SR_OK;
         case 5: *out = describe<SegK4_5>(); return SR_OK;
         case 6: *out = describe<SegK4_6>(); return SR_OK;
+        case 7: *out = describe<SegK4_7>(); return SR_OK;
         default: return SR_ERR_INVALID_ARG;
         }
     }

@@ -103,19 +103,23 @@ template <int BUCKETS_, int SNT_, int IPT_P_, int IPT_, int F_, int LADDER_ = 0>
 // ladders of shapes (threads x keys per thread, IPT odd):
 //   ladder 0: 128x9, 128x15, 256x9, 256x11, 256x15
 //   ladder 1:  64x9, 128x9, 128x15, 256x11, 256x15
+//   ladder 2: 128x13, 128x17, 128x19, 128x23, 256x15 (segments of 1,200-3,000 keys:
+//             one merge level fewer than 256-thread shapes)
 enum { NSMALL = 5 };
 __host__ __device__ constexpr int small_nt(int ladder, int c) {
-    return ladder == 0 ? (c < 2 ? 128 : 256) : (c == 0 ? 64 : c < 3 ? 128 : 256);
+    return ladder == 0 ? (c < 2 ? 128 : 256) : ladder == 1 ? (c == 0 ? 64 : c < 3 ? 128 : 256) : (c < 4 ? 128 : 256);
 }
 __host__ __device__ constexpr int small_ipt(int ladder, int c) {
     return ladder == 0 ? (c == 0 || c == 2 ? 9 : c == 1 || c == 4 ? 15 : 11)
-                       : (c < 2 ? 9 : c == 2 ? 15 : c == 3 ? 11 : 15);
+         : ladder == 1 ? (c < 2 ? 9 : c == 2 ? 15 : c == 3 ? 11 : 15)
+                       : (c == 0 ? 13 : c == 1 ? 17 : c == 2 ? 19 : c == 3 ? 23 : 15);
 }
 __host__ __device__ constexpr int small_cap(int ladder, int c) { return small_nt(ladder, c) * small_ipt(ladder, c); }
 static_assert(small_cap(0, 0) == 1152 && small_cap(0, 1) == 1920 && small_cap(0, 2) == 2304 &&
                   small_cap(0, 3) == 2816 && small_cap(0, 4) == 3840 && small_cap(1, 0) == 576 &&
                   small_cap(1, 1) == 1152 && small_cap(1, 2) == 1920 && small_cap(1, 3) == 2816 &&
-                  small_cap(1, 4) == 3840,
+                  small_cap(1, 4) == 3840 && small_cap(2, 0) == 1664 && small_cap(2, 1) == 2176 &&
+                  small_cap(2, 2) == 2432 && small_cap(2, 3) == 2944 && small_cap(2, 4) == 3840,
               "small-shape ladders");
 
 struct SegCtrl {
@@ -684,7 +688,8 @@ typedef SegCfg<1, 256, 1, 15, 4, 0> SegK4_3;    // buckets (ladder 0), tiles 256
 typedef SegCfg<1, 512, 1, 15, 1, 1> SegK4_4;    // buckets (ladder 1), tiles 512x15, fan-in 1
 typedef SegCfg<1, 256, 1, 15, 2, 1> SegK4_5;    // buckets (ladder 1), tiles 256x15, fan-in 2
 typedef SegCfg<1, 512, 1, 15, 2, 1> SegK4_6;    // buckets (ladder 1), tiles 512x15, fan-in 2
-enum { SEG_NCFG_K4 = 7 };
+typedef SegCfg<1, 512, 1, 15, 1, 2> SegK4_7;    // buckets (ladder 2), tiles 512x15, fan-in 1
+enum { SEG_NCFG_K4 = 8 };
 typedef SegCfg<0, 512, 7, 11, 1> SegK8_0;
 typedef SegCfg<0, 256, 7, 11, 2> SegK8_1;
 typedef SegCfg<1, 512, 1, 11, 1, 0> SegK8_2;
