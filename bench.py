@@ -487,8 +487,9 @@ def _forms(sr, torch, dev, stream, peak):
     pairs    2^28 stable uint64-key + uint32-payload sort (half uniform, half
              Zipf 1.1 over 2^20 values);
     learned  2^27 float32 keys of the lognormal mixture, learned partition
-             against the plain sort on the same input (and the model-free
-             equal-width ablation);
+             against the plain sort on the same input (and the untrained
+             quantile start and the model-free equal-width ablation, the latter
+             also under its own best bucket-sort configuration);
     batched  200,000 int32 arrays (lognormal lengths, median 512, four
              classes), the segmented sort under the autotuner's configuration
              replayed from a captured CUDA graph,
@@ -521,13 +522,23 @@ def _forms(sr, torch, dev, stream, peak):
     plain = _timed(torch, stream, lambda: sr.sort_keys(x), lambda: x.copy_(src), 3)
     learned = _timed(torch, stream, lambda: sr.sort_keys_learned(x), lambda: x.copy_(src), 3)
     stl = sr.stats()
+    untrained = _timed(torch, stream, lambda: sr.sort_keys_learned(x, model=sr.MODEL_UNTRAINED),
+                       lambda: x.copy_(src), 2)
+    stu = sr.stats()
     ew = _timed(torch, stream, lambda: sr.sort_keys_learned(x, model=sr.MODEL_EQUAL_WIDTH), lambda: x.copy_(src), 2)
     ste = sr.stats()
+    # the ablation under its own best bucket-sort configuration, for a fair comparison
+    ew_cfg = {c["index"]: _timed(torch, stream,
+                                 lambda: sr.sort_keys_learned(x, model=sr.MODEL_EQUAL_WIDTH, bucket_config=c["index"] + 1),
+                                 lambda: x.copy_(src), 1)
+              for c in sr.segmented_configs(sr.KEY_F32) if c["strategy"] == 1}
     out["learned_2^27_f32_lognormal"] = {
-        "plain_ms": plain, "learned_ms": learned, "equal_width_ms": ew,
+        "plain_ms": plain, "learned_ms": learned, "untrained_ms": untrained, "equal_width_ms": ew,
+        "equal_width_best_ms": min(ew_cfg.values()),
+        "equal_width_best_bucket_config": min(ew_cfg, key=ew_cfg.get),
         "plain_gkeys_s": n / (plain / 1e3) / 1e9, "learned_gkeys_s": n / (learned / 1e3) / 1e9,
         "learned_over_plain": plain / learned,
-        "fallback": stl["fallback"], "model_loss": stl["model_loss"],
+        "fallback": stl["fallback"], "model_loss": stl["model_loss"], "model_loss_untrained": stu["model_loss"],
         "bucket_imbalance": stl["bucket_imbalance"], "bucket_imbalance_equal_width": ste["bucket_imbalance"],
         "max_bucket": stl["max_bucket"]}
     del src, x

@@ -106,11 +106,25 @@ __global__ void __launch_bounds__(FEW_NT) k_few_sample(const typename Key<KT>::T
     __shared__ unsigned int s_v[FEW_MAX];
     __shared__ unsigned int s_k;
     __shared__ int s_last;
+    __shared__ unsigned long long s_set[FEW_SLOTS];
+    __shared__ unsigned int s_n;
+    __shared__ int s_over;
     if (gate && *gate == 0) return;
     const int t = threadIdx.x;
+    if (t < FEW_SLOTS) s_set[t] = 0ull;
+    if (t == 0) { s_n = 0u; s_over = 0; }
+    __syncthreads();
+    // this CTA's samples go into a shared-memory set first; only a CTA that saw
+    // at most FEW_MAX distinct keys touches the call's set in global memory
     const long long i = (long long)blockIdx.x * FEW_NT + t;
-    if (i < FEW_SAMPLE && n > 0 && !((volatile int *)&c->few_over)[0])
-        few_insert(c->few_slot, &c->few_n, &c->few_over, (unsigned int)Key<KT>::ord(__ldg(keys + (i * n) / FEW_SAMPLE)));
+    if (i < FEW_SAMPLE && n > 0)
+        few_insert(s_set, &s_n, &s_over, (unsigned int)Key<KT>::ord(__ldg(keys + (i * n) / FEW_SAMPLE)));
+    __syncthreads();
+    if (s_over) {
+        if (t == 0) atomicExch(&c->few_over, 1);
+    } else if (t < FEW_SLOTS && s_set[t] != 0ull && !((volatile int *)&c->few_over)[0]) {
+        few_insert(c->few_slot, &c->few_n, &c->few_over, (unsigned int)(s_set[t] - 1ull));
+    }
     __syncthreads();
     if (t == 0) {
         __threadfence();
@@ -144,43 +158,58 @@ __global__ void __launch_bounds__(FEW_NT) k_few_sample(const typename Key<KT>::T
 }
 
 // Few distinct keys, step 2: counts the keys equal to each candidate image (a
-// binary search over at most FEW_MAX images per key, warp-aggregated adds);
-// a key outside the set raises few_miss and the ordinary sort runs instead.
+// binary search over at most FEW_MAX images per key, one shared-memory
+// histogram per warp); a key outside the set raises few_miss and the ordinary
+// sort runs instead.
 template <int KT>
 __global__ void __launch_bounds__(256) k_few_count(const typename Key<KT>::T *__restrict__ keys, long long n,
                                                    Ctrl *__restrict__ c) {
     griddep_wait();
     typedef Key<KT> K;
+    typedef typename K::T T;
+    constexpr int NW = 256 / 32;
     __shared__ unsigned int s_v[FEW_MAX];
-    __shared__ unsigned int s_h[FEW_MAX];
+    __shared__ unsigned int s_h[NW][FEW_MAX];    // one histogram per warp
     if (!c->few_cand) return;
     const int t = threadIdx.x;
     const int k = (int)c->few_n;
-    if (t < FEW_MAX) { s_v[t] = t < k ? c->few_sorted[t] : 0xffffffffu; s_h[t] = 0u; }
+    if (t < FEW_MAX) s_v[t] = t < k ? c->few_sorted[t] : 0xffffffffu;
+    for (int q = t; q < NW * FEW_MAX; q += 256) (&s_h[0][0])[q] = 0u;
     __syncthreads();
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    const long long nr = (n + 31) / 32 * 32;       // whole warps in every iteration
-    for (long long i = (long long)blockIdx.x * blockDim.x + t; i < nr; i += stride) {
-        int j = -1;
-        if (i < n) {
-            const unsigned int u = (unsigned int)K::ord(__ldg(keys + i));
-            int lo = 0, hi = k - 1;                // the last image <= u
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (s_v[mid] <= u) lo = mid;
-                else hi = mid - 1;
-            }
-            j = lo;
-            if (s_v[lo] != u) {                    // not in the sample's set
-                if (!((volatile int *)&c->few_miss)[0]) atomicExch(&c->few_miss, 1);
-                j = -1;
-            }
+    unsigned int *h = s_h[t >> 5];
+    bool miss = false;
+    auto count = [&](T key) {
+        const unsigned int u = (unsigned int)K::ord(key);
+        int lo = 0, hi = k - 1;                    // the last image <= u
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_v[mid] <= u) lo = mid;
+            else hi = mid - 1;
         }
-        const unsigned int peers = __match_any_sync(0xffffffffu, j);
-        if (j >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&s_h[j], (unsigned int)__popc(peers));
+        if (s_v[lo] != u) miss = true;             // not in the sample's set
+        else atomicAdd(&h[lo], 1u);
+    };
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long gtid = (long long)blockIdx.x * blockDim.x + t;
+    long long tail = 0;
+    if ((((uintptr_t)keys) & 15) == 0) {
+        const long long nv = n / 4;
+        const uint4 *q4 = reinterpret_cast<const uint4 *>(keys);
+        for (long long v = gtid; v < nv; v += stride) {
+            const uint4 q = __ldg(q4 + v);
+            count((T)q.x); count((T)q.y); count((T)q.z); count((T)q.w);
+        }
+        tail = 4 * nv;
     }
+    for (long long i = tail + gtid; i < n; i += stride) count(__ldg(keys + i));
+    if (miss && !((volatile int *)&c->few_miss)[0]) atomicExch(&c->few_miss, 1);
     __syncthreads();
-    if (t < k && s_h[t]) atomicAdd(&c->few_count[t], (unsigned long long)s_h[t]);
+    if (t < k) {
+        unsigned int sum = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) sum += s_h[w][t];
+        if (sum) atomicAdd(&c->few_count[t], (unsigned long long)sum);
+    }
 }
 
 // Few distinct keys, step 3: when every key was in the set, writes the sorted
