@@ -276,3 +276,60 @@ def test_few_distinct_keys(gpu_lib, dtype):
     gk, gv = _gpu_pairs(gpu_lib, k, v)
     ok, ov = oracle.sort_pairs(k, v)
     assert gk.tobytes() == ok.tobytes() and gv.tobytes() == ov.tobytes()
+
+
+def _order_statistic_ok(torch, src, out, positions):
+    """out[i] is the i-th smallest key of src for every sampled i: fewer than
+    i+1 keys are smaller and at least i+1 are smaller or equal (counted on the
+    device, one position at a time)."""
+    for i in positions:
+        v = out[i]
+        less = int((src < v).sum())
+        leq = int((src <= v).sum())
+        if not (less <= i < leq):
+            return False
+    return True
+
+
+def test_full_size_2_28_uniform(gpu_lib):
+    """2^28 uniform int32 keys (the top of the benchmark's size sweep), in the
+    launch configuration the benchmark times: non-decreasing, a permutation of
+    the input (sum, and sum of a mixing function, as int64), and 64 sampled
+    output positions equal to the order statistic of the input."""
+    import torch
+    a = si.uniform_i32(1 << 28, 1)
+    src = torch.from_numpy(a).cuda()
+    del a
+    x = src.clone()
+    gpu_lib.sort_keys(x, key_type=0)
+    assert gpu_lib.stream_status() == 0
+    assert bool((x[1:] >= x[:-1]).all())
+    for f in (lambda t: t.to(torch.int64), lambda t: (t.to(torch.int64) * 2654435761) % 1000003):
+        assert int(f(src).sum()) == int(f(x).sum())
+    rng = np.random.default_rng(61)
+    pos = [0, x.numel() - 1] + [int(p) for p in rng.integers(0, x.numel(), 62)]
+    assert _order_statistic_ok(torch, src, x, pos)
+
+
+def test_full_size_2_28_pairs(gpu_lib):
+    """The stable pairs workload at full size: 2^28 uint64 keys (half uniform,
+    half Zipf 1.1 over 2^20 values) with payload = original index.  Keys
+    non-decreasing; every output key equals the input key at its payload;
+    payloads a permutation; equal keys keep ascending payloads (stability)."""
+    import torch
+    k, v = si.pairs_u64_zipf(1 << 28, 1)
+    sk = torch.from_numpy(k.view(np.int64)).cuda()
+    del k, v
+    xk = sk.clone()
+    xv = torch.arange(1 << 28, dtype=torch.int32, device="cuda")
+    gpu_lib.sort_pairs(xk, xv, key_type=3)
+    assert gpu_lib.stream_status() == 0
+    # uint64 order on int64 storage: compare with the sign bit flipped
+    flip = torch.tensor(-(1 << 63), dtype=torch.int64, device="cuda")
+    ok = xk ^ flip
+    assert bool((ok[1:] >= ok[:-1]).all())
+    idx = xv.to(torch.int64)
+    assert bool((sk[idx] == xk).all())
+    assert int(torch.bincount(idx, minlength=1 << 28).max()) == 1
+    same = xk[1:] == xk[:-1]
+    assert bool((xv[1:][same] > xv[:-1][same]).all())
