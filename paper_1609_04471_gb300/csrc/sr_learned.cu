@@ -504,63 +504,111 @@ __device__ __forceinline__ int digit_of(int b, int level, int s2, int mask2) {
     return level == 1 ? (b >> s2) : (b & mask2);
 }
 
+// Loads/stores of VW consecutive bucket ids as one vector (VW * sizeof(BT) is
+// 4, 8 or 16 bytes; the address must be aligned to it).
+template <typename BT, int VW>
+__device__ __forceinline__ void load_ids(const BT *p, int (&b)[VW]) {
+    if constexpr (VW * sizeof(BT) == 16) {
+        const uint4 q = *reinterpret_cast<const uint4 *>(p);
+        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int e = 0; e < VW; ++e) b[e] = sizeof(BT) == 4 ? (int)w[e] : (int)((w[e / 2] >> (16 * (e & 1))) & 0xffffu);
+    } else if constexpr (VW * sizeof(BT) == 8) {
+        const uint2 q = *reinterpret_cast<const uint2 *>(p);
+        const uint32_t w[2] = {q.x, q.y};
+#pragma unroll
+        for (int e = 0; e < VW; ++e) b[e] = sizeof(BT) == 4 ? (int)w[e] : (int)((w[e / 2] >> (16 * (e & 1))) & 0xffffu);
+    } else {
+        const uint32_t w = *reinterpret_cast<const uint32_t *>(p);
+#pragma unroll
+        for (int e = 0; e < VW; ++e) b[e] = sizeof(BT) == 4 ? (int)w : (int)((w >> (16 * (e & 1))) & 0xffffu);
+    }
+}
+template <typename BT, int VW>
+__device__ __forceinline__ void store_ids(BT *p, const int (&b)[VW]) {
+    uint32_t w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+        if (sizeof(BT) == 4) w[e] = (uint32_t)b[e];
+        else w[e / 2] |= ((uint32_t)b[e] & 0xffffu) << (16 * (e & 1));
+    }
+    if constexpr (VW * sizeof(BT) == 16) *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+    else if constexpr (VW * sizeof(BT) == 8) *reinterpret_cast<uint2 *>(p) = make_uint2(w[0], w[1]);
+    else *reinterpret_cast<uint32_t *>(p) = w[0];
+}
+
 // Level 1 counts: routes every key once, writes its bucket id (BT) beside it
 // and counts the coarse digit per tile.  Level 2 counts: reads the ids only.
-template <int KT, typename BT>
+// Each thread takes 16-byte vectors of keys (and the ids beside them) where
+// the tile is aligned, single keys otherwise.
+template <int KT, typename BT, int LEVEL>
 __global__ void __launch_bounds__(SPLIT_NT)
 k_split_hist(const typename Key<KT>::T *__restrict__ in, const BT *__restrict__ bid_in, BT *__restrict__ bid_out,
              const long long *__restrict__ seg_off, int S, const int *__restrict__ tile_base,
-             const int *__restrict__ tile_seg, const int *__restrict__ tile_local, int level, int D, int s2,
+             const int *__restrict__ tile_seg, const int *__restrict__ tile_local, int D, int s2,
              const LearnCtrl *__restrict__ lc, unsigned int *__restrict__ counts) {
     griddep_wait();
+    typedef typename Key<KT>::T T;
+    constexpr int VW = 16 / sizeof(T);             // keys per 16-byte vector
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int NW = SPLIT_NT / 32;
     unsigned int *hall = reinterpret_cast<unsigned int *>(smem);     // [NW][D]: one histogram per warp
     __shared__ RouteSmem rs;
     const int tile = blockIdx.x;
     if (tile >= tile_base[S]) return;
-    if (level == 1) load_route(lc->r, rs);
-    for (int d = threadIdx.x; d < NW * D; d += SPLIT_NT) hall[d] = 0u;
-    unsigned int *hist = hall + (threadIdx.x >> 5) * D;
+    const int t = threadIdx.x;
+    if (LEVEL == 1) load_route(lc->r, rs);
+    for (int d = t; d < NW * D; d += SPLIT_NT) hall[d] = 0u;
+    unsigned int *hist = hall + (t >> 5) * D;
     __syncthreads();
     const int s = tile_seg[tile], tl = tile_local[tile];
     const int nt = tile_base[s + 1] - tile_base[s];
     const long long start = seg_off[s] + (long long)tl * SPLIT_T;
-    const long long end = min(start + SPLIT_T, seg_off[s + 1]);
+    const int cnt = (int)(min(start + SPLIT_T, seg_off[s + 1]) - start);
     const int mask2 = (1 << s2) - 1;
-    for (long long i0 = start + threadIdx.x; i0 < end; i0 += (long long)SPLIT_NT * SPLIT_BATCH) {
-        const bool full = i0 + (long long)(SPLIT_BATCH - 1) * SPLIT_NT < end;
-        if (level == 1) {
-            typename Key<KT>::T k[SPLIT_BATCH];
-#pragma unroll
-            for (int j = 0; j < SPLIT_BATCH; ++j) {
-                const long long i = i0 + (long long)j * SPLIT_NT;
-                k[j] = (full || i < end) ? in[i] : typename Key<KT>::T(0);
+    if constexpr (LEVEL == 1) {
+        const T *tin = in + start;
+        BT *tout = bid_out + start;
+        const bool vec = (((uintptr_t)tin) & 15) == 0 && (((uintptr_t)tout) & (VW * sizeof(BT) - 1)) == 0;
+        const int nvec = vec ? cnt / VW : 0;
+        for (int v = t; v < nvec; v += SPLIT_NT) {
+            T k[VW];
+            if constexpr (VW == 4) {
+                const uint4 q = __ldg(reinterpret_cast<const uint4 *>(tin) + v);
+                k[0] = (T)q.x; k[1] = (T)q.y; k[2] = (T)q.z; k[3] = (T)q.w;
+            } else {
+                const ulonglong2 q = __ldg(reinterpret_cast<const ulonglong2 *>(tin) + v);
+                k[0] = (T)q.x; k[1] = (T)q.y;
             }
+            int b[VW];
 #pragma unroll
-            for (int j = 0; j < SPLIT_BATCH; ++j) {
-                const long long i = i0 + (long long)j * SPLIT_NT;
-                if (full || i < end) {
-                    const int b = route_fast(rs, norm_key<KT>(k[j], rs));
-                    bid_out[i] = (BT)b;
-                    atomicAdd(&hist[b >> s2], 1u);
-                }
+            for (int e = 0; e < VW; ++e) {
+                b[e] = route_fast(rs, norm_key<KT>(k[e], rs));
+                atomicAdd(&hist[b[e] >> s2], 1u);
             }
-        } else {
-            BT bb[SPLIT_BATCH];
-#pragma unroll
-            for (int j = 0; j < SPLIT_BATCH; ++j) {
-                const long long i = i0 + (long long)j * SPLIT_NT;
-                bb[j] = (full || i < end) ? bid_in[i] : BT(0);
-            }
-#pragma unroll
-            for (int j = 0; j < SPLIT_BATCH; ++j)
-                if (full || i0 + (long long)j * SPLIT_NT < end) atomicAdd(&hist[(int)bb[j] & mask2], 1u);
+            store_ids<BT, VW>(tout + (long long)v * VW, b);
         }
+        for (int i = nvec * VW + t; i < cnt; i += SPLIT_NT) {
+            const int b = route_fast(rs, norm_key<KT>(__ldg(tin + i), rs));
+            tout[i] = (BT)b;
+            atomicAdd(&hist[b >> s2], 1u);
+        }
+    } else {
+        const BT *tin = bid_in + start;
+        constexpr int BW = 16 / sizeof(BT);        // ids per 16-byte vector
+        const bool vec = (((uintptr_t)tin) & 15) == 0;
+        const int nvec = vec ? cnt / BW : 0;
+        for (int v = t; v < nvec; v += SPLIT_NT) {
+            int b[BW];
+            load_ids<BT, BW>(tin + (long long)v * BW, b);
+#pragma unroll
+            for (int e = 0; e < BW; ++e) atomicAdd(&hist[b[e] & mask2], 1u);
+        }
+        for (int i = nvec * BW + t; i < cnt; i += SPLIT_NT) atomicAdd(&hist[(int)tin[i] & mask2], 1u);
     }
     __syncthreads();
     const long long base_e = (long long)D * tile_base[s];
-    for (int d = threadIdx.x; d < D; d += SPLIT_NT) {
+    for (int d = t; d < D; d += SPLIT_NT) {
         unsigned int c = 0;
 #pragma unroll
         for (int w = 0; w < NW; ++w) c += hall[w * D + d];
@@ -571,23 +619,24 @@ k_split_hist(const typename Key<KT>::T *__restrict__ in, const BT *__restrict__ 
 // Moves one tile's keys (and, at level 1, their bucket ids) to the level's
 // output: first into shared memory grouped by digit (the tile's own counts,
 // scanned, give each digit's stretch; a shared counter hands out slots), then
-// out with every digit's stretch written contiguously at its scanned position.
-template <int KT, typename BT>
+// out with every digit's stretch written contiguously by one warp.
+template <int KT, typename BT, int LEVEL>
 __global__ void __launch_bounds__(SPLIT_NT)
 k_split_scatter(const typename Key<KT>::T *__restrict__ in, const BT *__restrict__ bid_in,
                 typename Key<KT>::T *__restrict__ out, BT *__restrict__ bid_out, const long long *__restrict__ seg_off,
                 int S, const int *__restrict__ tile_base, const int *__restrict__ tile_seg,
-                const int *__restrict__ tile_local, int level, int D, int s2, LearnCtrl *__restrict__ lc,
+                const int *__restrict__ tile_local, int D, int s2, LearnCtrl *__restrict__ lc,
                 const unsigned int *__restrict__ counts, const unsigned long long *__restrict__ pos,
                 int *__restrict__ status_word) {
     griddep_wait();
     typedef typename Key<KT>::T T;
+    constexpr int VW = 16 / sizeof(T);
     extern __shared__ __align__(16) unsigned char smem[];
     T *stage_k = reinterpret_cast<T *>(smem);                                       // [SPLIT_T]
     unsigned long long *gbase = reinterpret_cast<unsigned long long *>(stage_k + SPLIT_T);   // [D]
     unsigned int *tstart = reinterpret_cast<unsigned int *>(gbase + D);             // [D + 1]
     unsigned int *taken = tstart + D + 1;                                           // [D]
-    BT *stage_b = reinterpret_cast<BT *>(taken + D);                                // [SPLIT_T]
+    BT *stage_b = reinterpret_cast<BT *>(taken + D);                                // [SPLIT_T] (level 1)
     __shared__ unsigned int s_warp[32];
     const int tile = blockIdx.x;
     if (tile >= tile_base[S]) return;
@@ -621,42 +670,50 @@ k_split_scatter(const typename Key<KT>::T *__restrict__ in, const BT *__restrict
     if (t == 0) tstart[D] = s_warp[SPLIT_NT / 32 - 1];
     __syncthreads();
     const long long start = seg_off[s] + (long long)tl * SPLIT_T;
-    const long long end = min(start + SPLIT_T, seg_off[s + 1]);
-    const int cnt = (int)(end - start);
+    const int cnt = (int)(min(start + SPLIT_T, seg_off[s + 1]) - start);
     const int mask2 = (1 << s2) - 1;
-    for (int i0 = t; i0 < cnt; i0 += SPLIT_NT * SPLIT_BATCH) {
-        const bool full = i0 + (SPLIT_BATCH - 1) * SPLIT_NT < cnt;
-        T k[SPLIT_BATCH];
-        BT bb[SPLIT_BATCH];
-#pragma unroll
-        for (int j = 0; j < SPLIT_BATCH; ++j) {
-            const int i = i0 + j * SPLIT_NT;
-            if (full || i < cnt) { k[j] = in[start + i]; bb[j] = bid_in[start + i]; }
+    const T *tin = in + start;
+    const BT *bin = bid_in + start;
+    bool bad = false;
+    auto stage = [&](T k, int b) {
+        const int d = LEVEL == 1 ? (b >> s2) : (b & mask2);
+        const unsigned int q = atomicAdd(&taken[d], 1u);         // taken[d] starts at the digit's stretch
+        if (q < (unsigned int)cnt) {
+            stage_k[q] = k;
+            if (LEVEL == 1) stage_b[q] = (BT)b;
+        } else {
+            bad = true;                                          // impossible: the counts came from the same ids
         }
-#pragma unroll
-        for (int j = 0; j < SPLIT_BATCH; ++j) {
-            if (full || i0 + j * SPLIT_NT < cnt) {
-                const int d = level == 1 ? ((int)bb[j] >> s2) : ((int)bb[j] & mask2);
-                const unsigned int q = atomicAdd(&taken[d], 1u);     // taken[d] starts at the digit's stretch
-                if (q < (unsigned int)cnt) {
-                    stage_k[q] = k[j];
-                    if (level == 1) stage_b[q] = bb[j];
-                } else {
-                    // impossible: the counts came from the same ids
-                    atomicExch(&lc->fallback, 1);
-                    atomicExch(status_word, (int)SR_ERR_INTERNAL);
-                }
-            }
+    };
+    const bool vec = (((uintptr_t)tin) & 15) == 0 && (((uintptr_t)bin) & (VW * sizeof(BT) - 1)) == 0;
+    const int nvec = vec ? cnt / VW : 0;
+    for (int v = t; v < nvec; v += SPLIT_NT) {
+        T k[VW];
+        if constexpr (VW == 4) {
+            const uint4 q = __ldg(reinterpret_cast<const uint4 *>(tin) + v);
+            k[0] = (T)q.x; k[1] = (T)q.y; k[2] = (T)q.z; k[3] = (T)q.w;
+        } else {
+            const ulonglong2 q = __ldg(reinterpret_cast<const ulonglong2 *>(tin) + v);
+            k[0] = (T)q.x; k[1] = (T)q.y;
         }
+        int b[VW];
+        load_ids<BT, VW>(bin + (long long)v * VW, b);
+#pragma unroll
+        for (int e = 0; e < VW; ++e) stage(k[e], b[e]);
+    }
+    for (int i = nvec * VW + t; i < cnt; i += SPLIT_NT) stage(__ldg(tin + i), (int)bin[i]);
+    if (bad) {
+        atomicExch(&lc->fallback, 1);
+        atomicExch(status_word, (int)SR_ERR_INTERNAL);
     }
     __syncthreads();
     // one warp per digit stretch: contiguous shared reads, contiguous global writes
     for (int d = wid; d < D; d += SPLIT_NT / 32) {
         const unsigned int q0 = tstart[d], q1 = tstart[d + 1];
-        const unsigned long long g0 = gbase[d];
+        T *o = out + gbase[d];
         for (unsigned int q = q0 + lane; q < q1; q += 32) {
-            out[g0 + (q - q0)] = stage_k[q];
-            if (level == 1) bid_out[g0 + (q - q0)] = stage_b[q];
+            o[q - q0] = stage_k[q];
+            if (LEVEL == 1) bid_out[gbase[d] + (q - q0)] = stage_b[q];
         }
     }
 }
@@ -923,27 +980,28 @@ static sr_status learned_impl(void *d_keys, size_t n, const sr_learned_opts *o, 
             const BT *bin = level == 1 ? ba : bb;
             SR_LAUNCH(SR_KERNEL_MODEL, k_split_tiles, 1, 1024, 0, s, segs, S, tb, tseg, tloc);
             const size_t h_smem = (size_t)(SPLIT_NT / 32) * D * 4;
+            auto hist_kernel = level == 1 ? k_split_hist<KT, BT, 1> : k_split_hist<KT, BT, 2>;
             if (h_smem > 48 * 1024 &&
-                cudaFuncSetAttribute((const void *)k_split_hist<KT, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                cudaFuncSetAttribute((const void *)hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)h_smem) != cudaSuccess) {
                 st = launch_status();
                 break;
             }
-            SR_LAUNCH(SR_KERNEL_MODEL, (k_split_hist<KT, BT>), grid, SPLIT_NT, h_smem, s, in, bin, ba, segs,
-                      S, tb, tseg, tloc, level, D, s2, lc, cnt);
+            SR_LAUNCH(SR_KERNEL_MODEL, hist_kernel, grid, SPLIT_NT, h_smem, s, in, bin, ba, segs, S, tb, tseg, tloc, D,
+                      s2, lc, cnt);
             SR_LAUNCH(SR_KERNEL_MODEL, k_scan_sums, sgrid, 1024, 0, s, cnt, tb, S, D, sums);
             SR_LAUNCH(SR_KERNEL_MODEL, k_scan_top, 1, 1024, 0, s, sums, tb, S, D);
             SR_LAUNCH(SR_KERNEL_MODEL, k_scan_apply, sgrid, 1024, 0, s, cnt, tb, S, D, sums, pos);
-            const size_t sc_smem = (size_t)SPLIT_T * (sizeof(T) + sizeof(BT)) + (size_t)D * 16 + 4;
+            const size_t sc_smem = (size_t)SPLIT_T * (sizeof(T) + (level == 1 ? sizeof(BT) : 0)) + (size_t)D * 16 + 4;
+            auto scatter_kernel = level == 1 ? k_split_scatter<KT, BT, 1> : k_split_scatter<KT, BT, 2>;
             if (sc_smem > 48 * 1024 &&
-                cudaFuncSetAttribute((const void *)k_split_scatter<KT, BT>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc_smem) != cudaSuccess) {
+                cudaFuncSetAttribute((const void *)scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sc_smem) != cudaSuccess) {
                 st = launch_status();
                 break;
             }
-            SR_LAUNCH(SR_KERNEL_MODEL, (k_split_scatter<KT, BT>), grid, SPLIT_NT, sc_smem, s, in, bin, out,
-                      level == 1 ? bb : (BT *)nullptr, segs, S, tb, tseg, tloc, level, D, s2, lc, cnt, pos,
-                      ds->status);
+            SR_LAUNCH(SR_KERNEL_MODEL, scatter_kernel, grid, SPLIT_NT, sc_smem, s, in, bin, out,
+                      level == 1 ? bb : (BT *)nullptr, segs, S, tb, tseg, tloc, D, s2, lc, cnt, pos, ds->status);
             if (level == 1) {
                 SR_LAUNCH(SR_KERNEL_MODEL, k_coarse_off, (unsigned)((D1 + 1 + 255) / 256), 256, 0, s, pos, tb, D1, N,
                           coff);
