@@ -341,9 +341,12 @@ def run_ours(args):
         "timing": "per-launch events in a second pass over the same steps; value comes from the unbracketed pass",
     }
 
-    # end to end through the host-buffer entry point (pinned host memory)
+    # end to end through the host-buffer entry point (pinned host memory): the
+    # step's four arrays are queued on four streams, so one array's copies
+    # overlap another's sort; the step ends when all four are back in host memory
     host = [torch.from_numpy(a).pin_memory() for a in arrays]
     host_src = [h.clone().pin_memory() for h in host]
+    streams = [torch.cuda.Stream() for _ in CLASSES]
     for c in range(len(CLASSES)):
         sr.sort_keys_host(host[c].numpy())
     torch.cuda.synchronize()
@@ -351,13 +354,13 @@ def run_ours(args):
     for step in range(args.steps):
         for c in range(len(CLASSES)):
             host[c].copy_(host_src[c])
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            sr.sort_keys_host(host[c].numpy())
-            e1.record(stream)
-            torch.cuda.synchronize()
-            e2e_ms += e0.elapsed_time(e1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for c in range(len(CLASSES)):
+            sr.sort_keys_host_async(host[c], stream=streams[c])
+        for st_ in streams:
+            st_.synchronize()
+        e2e_ms += (time.perf_counter() - t0) * 1e3
     e2e_ms /= args.steps
     if ws > 1:
         t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
@@ -365,7 +368,9 @@ def run_ours(args):
         e2e_ms = float(t.item())
     e2e = {"value": keys_step * ws / (e2e_ms / 1e3) / 1e9, "unit": "Gkeys/s",
            "h2d_bytes_per_step": 4 * keys_step, "d2h_bytes_per_step": 4 * keys_step,
-           "ms_per_step": e2e_ms}
+           "ms_per_step": e2e_ms,
+           "api": "sr_sort_keys_host_async on four streams (one per array), host clock from the first "
+                  "call to the last stream's completion"}
 
     sweep = None
     if not args.no_sweep:

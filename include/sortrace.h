@@ -179,6 +179,16 @@ sr_status sr_sort_segmented_cfg(void *d_keys, size_t n_keys, const int64_t *d_of
 sr_status sr_sort_keys_host(void *h_keys, size_t n, sr_key_type kt, sr_stream stream);
 
 /*
+ * sr_sort_keys_host_async -- sr_sort_keys_host without the final wait: the
+ * copy in, the sort and the copy out are queued on `stream` and the call
+ * returns at once.  h_keys must be page-locked host memory (cudaHostAlloc /
+ * cudaHostRegister; SR_ERR_INVALID_ARG otherwise) and must not be touched
+ * until the stream completes.  Calls on different streams overlap one
+ * array's copies with another's sort.
+ */
+sr_status sr_sort_keys_host_async(void *h_keys, size_t n, sr_key_type kt, sr_stream stream);
+
+/*
  * sr_sort_keys_noalloc -- sr_sort_keys for callers that must not allocate device
  * memory while they sort (a service that reserves all of its memory up front
  * so it can never hit out-of-memory mid-request, a framework that forbids

@@ -72,6 +72,7 @@ SIGNATURES = {
     "sr_segmented_num_configs": (_i32, [_i32]),
     "sr_segmented_config_info": (_i32, [_i32, _i32, _vp]),
     "sr_sort_keys_host": (_i32, [_vp, _sz, _i32, _vp]),
+    "sr_sort_keys_host_async": (_i32, [_vp, _sz, _i32, _vp]),
     "sr_sort_keys_noalloc": (_i32, [_vp, _sz, _i32, _vp]),
     "sr_sort_keys_learned": (_i32, [_vp, _sz, _i32, _vp, _vp]),
     "sr_detect_runs": (_i32, [_vp, _sz, _i32, _vp, _vp]),
@@ -256,11 +257,8 @@ def sort_keys_learned(x, key_type: int | None = None, stream=None, **opts):
     return x
 
 
-def sort_keys_host(arr, key_type: int | None = None, stream=None):
-    """Sorts a host (CPU) tensor or numpy array in place through the device:
-    copy in, sort, copy out, wait."""
+def _host_args(arr, key_type):
     import numpy as np
-    import torch
     if isinstance(arr, np.ndarray):
         if not arr.flags["C_CONTIGUOUS"]:
             raise ValueError("array must be contiguous")
@@ -273,7 +271,23 @@ def sort_keys_host(arr, key_type: int | None = None, stream=None):
             raise ValueError("host tensor must be a contiguous CPU tensor")
         kt = key_type_of(arr) if key_type is None else key_type
         ptr, n = arr.data_ptr(), arr.numel()
+    return ptr, n, kt
+
+
+def sort_keys_host(arr, key_type: int | None = None, stream=None):
+    """Sorts a host (CPU) tensor or numpy array in place through the device:
+    copy in, sort, copy out, wait."""
+    ptr, n, kt = _host_args(arr, key_type)
     _check(load().sr_sort_keys_host(ptr, n, kt, _stream(stream)), "sr_sort_keys_host")
+    return arr
+
+
+def sort_keys_host_async(arr, key_type: int | None = None, stream=None):
+    """sort_keys_host queued on the stream without waiting; `arr` must be in
+    page-locked memory (e.g. torch's pin_memory()) and left alone until the
+    stream completes."""
+    ptr, n, kt = _host_args(arr, key_type)
+    _check(load().sr_sort_keys_host_async(ptr, n, kt, _stream(stream)), "sr_sort_keys_host_async")
     return arr
 
 

@@ -124,13 +124,11 @@ extern "C" sr_status sr_sort_pairs(void *d_keys, uint32_t *d_vals, size_t n, sr_
     return dispatch_sort<true>(d_keys, d_vals, n, kt, (cudaStream_t)stream, 2);
 }
 
-extern "C" sr_status sr_sort_keys_host(void *h_keys, size_t n, sr_key_type kt, sr_stream stream) {
-    if (!valid_key_type(kt)) return SR_ERR_INVALID_ARG;
-    if (n > 1 && !h_keys) return SR_ERR_INVALID_ARG;
-    if (n < 2) return SR_OK;
+// Copy in, sort, copy out, all on stream s (the device copy is pool scratch,
+// freed in stream order).
+static sr_status host_sort_enqueue(void *h_keys, size_t n, sr_key_type kt, cudaStream_t s) {
     DeviceState *ds = nullptr;
     SR_TRY(device_state(&ds));
-    cudaStream_t s = (cudaStream_t)stream;
     const size_t bytes = n * key_bytes_of(kt);
     void *d = nullptr;
     SR_TRY(scratch_alloc(ds, &d, bytes, s));
@@ -140,8 +138,29 @@ extern "C" sr_status sr_sort_keys_host(void *h_keys, size_t n, sr_key_type kt, s
     if (st == SR_OK && cudaMemcpyAsync(h_keys, d, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
         st = launch_status();
     scratch_free(d, s);
+    return st;
+}
+
+extern "C" sr_status sr_sort_keys_host(void *h_keys, size_t n, sr_key_type kt, sr_stream stream) {
+    if (!valid_key_type(kt)) return SR_ERR_INVALID_ARG;
+    if (n > 1 && !h_keys) return SR_ERR_INVALID_ARG;
+    if (n < 2) return SR_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    sr_status st = host_sort_enqueue(h_keys, n, kt, s);
     if (cudaStreamSynchronize(s) != cudaSuccess && st == SR_OK) st = launch_status();
     return st;
+}
+
+extern "C" sr_status sr_sort_keys_host_async(void *h_keys, size_t n, sr_key_type kt, sr_stream stream) {
+    if (!valid_key_type(kt)) return SR_ERR_INVALID_ARG;
+    if (n > 1 && !h_keys) return SR_ERR_INVALID_ARG;
+    if (n < 2) return SR_OK;
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, h_keys) != cudaSuccess || pa.type != cudaMemoryTypeHost) {
+        cudaGetLastError();
+        return SR_ERR_INVALID_ARG;                 // must be page-locked host memory
+    }
+    return host_sort_enqueue(h_keys, n, kt, (cudaStream_t)stream);
 }
 
 extern "C" sr_status sr_detect_runs(const void *d_keys, size_t n, sr_key_type kt, sr_run_info *out,

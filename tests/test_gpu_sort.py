@@ -226,6 +226,23 @@ def test_host_entry_point(gpu_lib):
     assert b.tobytes() == oracle.sort_keys(a).tobytes()
 
 
+def test_host_async_entry_point_on_several_streams(gpu_lib):
+    """Four host arrays in page-locked memory sorted at once on four streams;
+    pageable memory is refused before anything is queued."""
+    import torch
+    arrays = [si.int32_input(kind, (1 << 20) + 3 * i, seed=20 + i) for i, kind in enumerate(si.INT32_CLASSES)]
+    host = [torch.from_numpy(a.copy()).pin_memory() for a in arrays]
+    streams = [torch.cuda.Stream() for _ in arrays]
+    for h, st in zip(host, streams):
+        gpu_lib.sort_keys_host_async(h, stream=st)
+    for st in streams:
+        st.synchronize()
+    for h, a in zip(host, arrays):
+        assert h.numpy().tobytes() == oracle.sort_keys(a).tobytes()
+    with pytest.raises(gpu_lib.SortError):
+        gpu_lib.sort_keys_host_async(arrays[0].copy())
+
+
 def test_oom_injection(gpu_lib, monkeypatch):
     import torch
     a = _to_dev(si.uniform_i32(100_000, 1))
