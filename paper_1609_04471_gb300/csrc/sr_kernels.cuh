@@ -503,11 +503,14 @@ k_partition(const typename Key<KT>::T *__restrict__ uk, const typename Key<KT>::
     if ((lane & ((1 << lg) - 1)) == 0) splits[b] = a_beg + sp;
 }
 
-// Lanes per boundary for k_partition: about 160k searching lanes in all
-// (a single wave on 152 SMs), between 1 and 32 per boundary.
+// Lanes per boundary for k_partition: about SR_PARTITION_LANES searching
+// lanes in all, between 1 and 32 per boundary.
+#ifndef SR_PARTITION_LANES
+#define SR_PARTITION_LANES 160000
+#endif
 inline int partition_lg(long long nbound) {
     int lg = 5;
-    while (lg > 0 && (nbound << lg) > 160000) --lg;
+    while (lg > 0 && (nbound << lg) > SR_PARTITION_LANES) --lg;
     return lg;
 }
 
