@@ -90,7 +90,7 @@ template <int KB, bool VALS> struct Shape;
 #define SR_K4V_IPT 11
 #endif
 #ifndef SR_K8_IPT
-#define SR_K8_IPT 13
+#define SR_K8_IPT 17
 #endif
 #ifndef SR_K8V_IPT
 #define SR_K8V_IPT 13
@@ -193,7 +193,7 @@ __device__ __forceinline__ void serial_merge(const U *s, int a, int a_end, int b
 // pairs, generated at compile time.
 struct NetPairs {
     int n;
-    unsigned char a[256], b[256];
+    unsigned char a[1024], b[1024];     // enough for N <= 64
 };
 __host__ __device__ constexpr NetPairs batcher_pairs(int N) {
     NetPairs r{};
@@ -213,6 +213,7 @@ __host__ __device__ constexpr NetPairs batcher_pairs(int N) {
 template <typename U, int IPT, bool VALS>
 __device__ __forceinline__ void thread_sort(U (&k)[IPT], uint32_t (&v)[IPT]) {
     if constexpr (!VALS && SR_KEYS_NETWORK) {
+        static_assert(IPT <= 64, "network tables hold up to 64 inputs");
         constexpr NetPairs net = batcher_pairs(IPT);
 #pragma unroll
         for (int c = 0; c < net.n; ++c) {

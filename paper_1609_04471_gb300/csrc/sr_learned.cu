@@ -450,7 +450,6 @@ __global__ void k_sample(const typename Key<KT>::T *__restrict__ keys, long long
 // ones, which are the buckets.  No key needs a global atomic.
 constexpr int SPLIT_T = 8192;
 constexpr int SPLIT_NT = 512;
-constexpr int SPLIT_BATCH = 8;
 constexpr int SCAN_PER_CTA = 8192;
 
 // Tile table of a level (one CTA; at most 1024 segments): tile_base[s] = first
