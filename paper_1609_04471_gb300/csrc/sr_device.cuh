@@ -156,6 +156,27 @@ __device__ __forceinline__ long long group_split(const typename K::T *__restrict
     return lo;
 }
 
+// The smallest m in [lo, hi] with before(m) false, found by a group of
+// 2^lg lanes (before(m) is true below the answer and false from it on; m = hi
+// counts as false): the same (G+1)-ary search as group_split over any
+// predicate.  All lanes of the group call it with the same lo, hi.
+template <typename Pred>
+__device__ __forceinline__ long long group_search(long long lo, long long hi, int lane, int lg, Pred before) {
+    const int G = 1 << lg;
+    const int j = lane & (G - 1);
+    const unsigned mask = lg == 5 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+    while (hi > lo) {
+        const long long step = (hi - lo + G) / (G + 1);
+        const long long m = lo + (long long)(j + 1) * step - 1;
+        const bool b = m < hi && before(m);
+        const int cnt = __popc(__ballot_sync(mask, b));
+        const long long nhi = cnt == G ? hi : lo + (long long)(cnt + 1) * step - 1;
+        lo = lo + (long long)cnt * step;
+        hi = min(hi, nhi);
+    }
+    return lo;
+}
+
 template <typename K>
 __device__ __forceinline__ long long warp_split(const typename K::T *__restrict__ src, long long a_beg,
                                                 long long na, long long b_beg, long long nb,

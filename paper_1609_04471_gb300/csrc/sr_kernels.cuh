@@ -5,6 +5,9 @@
 
 #include "sr_device.cuh"
 
+#ifndef SR_SPLIT_SAMPLES
+#define SR_SPLIT_SAMPLES 1  // merge splits searched over recorded tile samples first
+#endif
 #ifndef SR_FEW_KEYS
 #define SR_FEW_KEYS 1       // the few-distinct-keys path (4-byte keys, keys only)
 #endif
@@ -309,7 +312,8 @@ template <int KT, int NT, int IPT, bool VALS>
 __global__ void __launch_bounds__(NT)
 k_block_sort(const typename Key<KT>::T *in_k, const uint32_t *in_v, typename Key<KT>::T *out_k,
              uint32_t *out_v, long long n, const Ctrl *__restrict__ c,
-             typename Key<KT>::U *__restrict__ tile_lo, typename Key<KT>::U *__restrict__ tile_hi) {
+             typename Key<KT>::U *__restrict__ tile_lo, typename Key<KT>::U *__restrict__ tile_hi,
+             typename Key<KT>::U *__restrict__ samp, int mv) {
     griddep_wait();
     typedef Key<KT> K;
     typedef typename K::U U;
@@ -340,8 +344,20 @@ k_block_sort(const typename Key<KT>::T *in_k, const uint32_t *in_v, typename Key
     }
     const int any_desc = __syncthreads_or(desc);
     const int any_nondesc = __syncthreads_or(nondesc);
+    // first and last key of every merge tile of mv keys in this tile, for the
+    // first merge pass's split search; `rev` reads the tile back to front
+    auto samples = [&](bool rev) {
+        if (!samp) return;
+        const int per = NV / mv;
+        for (int q = t; q < per && q * mv < cnt; q += NT) {
+            const int f = q * mv, l = min(f + mv, cnt) - 1;
+            samp[2 * ((long long)blockIdx.x * per + q)] = rev ? s[cnt - 1 - f] : s[f];
+            samp[2 * ((long long)blockIdx.x * per + q) + 1] = rev ? s[cnt - 1 - l] : s[l];
+        }
+    };
     if (!any_desc) {                       // already ascending
         if (t == 0 && tile_lo) { tile_lo[blockIdx.x] = s[0]; tile_hi[blockIdx.x] = s[cnt - 1]; }
+        samples(false);
         if (out_k != in_k) {
             for (int idx = t; idx < cnt; idx += NT) {
                 out_k[base + idx] = K::unord(s[idx]);
@@ -352,6 +368,7 @@ k_block_sort(const typename Key<KT>::T *in_k, const uint32_t *in_v, typename Key
     }
     if (!any_nondesc) {                    // strictly descending: reverse
         if (t == 0 && tile_lo) { tile_lo[blockIdx.x] = s[cnt - 1]; tile_hi[blockIdx.x] = s[0]; }
+        samples(true);
         for (int idx = t; idx < cnt; idx += NT) {
             out_k[base + idx] = K::unord(s[cnt - 1 - idx]);
             if (VALS) out_v[base + idx] = sv[cnt - 1 - idx];
@@ -374,6 +391,7 @@ k_block_sort(const typename Key<KT>::T *in_k, const uint32_t *in_v, typename Key
     }
     __syncthreads();
     if (t == 0 && tile_lo) { tile_lo[blockIdx.x] = s[0]; tile_hi[blockIdx.x] = s[cnt - 1]; }
+    samples(false);
     for (int idx = t; idx < cnt; idx += NT) {
         out_k[base + idx] = K::unord(s[idx]);
         if (VALS) out_v[base + idx] = sv[idx];
@@ -487,9 +505,10 @@ template <int KT>
 __global__ void __launch_bounds__(256)
 k_partition(const typename Key<KT>::T *__restrict__ uk, const typename Key<KT>::T *__restrict__ sk,
             long long n, long long w, int nv, long long nbound, long long *__restrict__ splits,
-            const Ctrl *__restrict__ c, int p, int lg) {
+            const Ctrl *__restrict__ c, int p, int lg, const typename Key<KT>::U *__restrict__ samp) {
     griddep_wait();
     typedef Key<KT> K;
+    typedef typename K::U U;
     const int lane = threadIdx.x & 31;
     const long long b = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> lg;
     if (b >= nbound) return;                       // uniform across the group
@@ -499,7 +518,29 @@ k_partition(const typename Key<KT>::T *__restrict__ uk, const typename Key<KT>::
     const long long pb = (out / (2 * w)) * (2 * w);
     const long long a_beg = pb, a_end = min(pb + w, n);
     const long long b_beg = a_end, b_end = min(pb + 2 * w, n);
-    const long long sp = group_split<K>(src, a_beg, a_end - a_beg, b_beg, b_end - b_beg, out - pb, lane, lg);
+    const long long na = a_end - a_beg, nb = b_end - b_beg, d = out - pb;
+    long long lo = max(0ll, d - nb), hi = min(d, na);
+    if (samp && out < n && hi > lo) {
+        // Coarse: the merge-path test at the multiples m = j*nv uses only the
+        // first key of A's tile j and the last key of B's tile d/nv - j - 1,
+        // which the previous pass (or the block sort) recorded; d, a_beg and
+        // b_beg are multiples of nv here.
+        const long long jlo = (lo + nv - 1) / nv, jhi = (hi - 1) / nv, dj = d / nv;
+        const long long ta = a_beg / nv, tb = b_beg / nv;
+        const long long jt = group_search(jlo, jhi + 1, lane, lg, [&](long long j) {
+            const U x = samp[2 * (ta + j)];
+            const U y = samp[2 * (tb + dj - j - 1) + 1];
+            return !(y < x);
+        });
+        if (jt > jlo) lo = max(lo, (jt - 1) * nv + 1);
+        if (jt <= jhi) hi = min(hi, jt * nv);
+    }
+    // fine: the keys themselves, inside the stretch the samples left
+    const long long sp = group_search(lo, hi, lane, lg, [&](long long m) {
+        const U x = K::ord(src[a_beg + m]);
+        const U y = K::ord(src[b_beg + d - 1 - m]);
+        return !(y < x);
+    });
     if ((lane & ((1 << lg) - 1)) == 0) splits[b] = a_beg + sp;
 }
 
@@ -531,7 +572,8 @@ __device__ __forceinline__ void merge_tile(const typename Key<KT>::T *__restrict
                                            typename Key<KT>::T *__restrict__ dst_k,
                                            const uint32_t *__restrict__ src_v, uint32_t *__restrict__ dst_v,
                                            long long n, long long out0, int cnt, long long a0, long long a1,
-                                           long long b0, typename Key<KT>::U *s, uint32_t *sv) {
+                                           long long b0, typename Key<KT>::U *s, uint32_t *sv,
+                                           typename Key<KT>::U *samp = nullptr, long long tile = 0) {
     typedef Key<KT> K;
     typedef typename K::U U;
     typedef typename K::T T;
@@ -627,6 +669,10 @@ __device__ __forceinline__ void merge_tile(const typename Key<KT>::T *__restrict
         if (VALS) sv[t * IPT + i] = v[i];
     }
     __syncthreads();
+    if (samp && t == 0) {                          // the output tile's first and last key, for the next pass
+        samp[2 * tile] = s[0];
+        samp[2 * tile + 1] = s[cnt - 1];
+    }
     if (VEC) {
         // keys before the first 4-key group boundary of the output go one by one
         const int head = min(cnt, (int)((4 - (out0 & 3)) & 3));
@@ -698,7 +744,8 @@ __device__ __forceinline__ void merge_tile(const typename Key<KT>::T *__restrict
 template <int KT, int NT, int IPT, bool VALS, bool VEC>
 __global__ void __launch_bounds__(NT)
 k_merge(typename Key<KT>::T *uk, uint32_t *uv, typename Key<KT>::T *sk, uint32_t *svb, long long n,
-        long long w, int lgt, const long long *__restrict__ splits, const Ctrl *__restrict__ c, int p) {
+        long long w, int lgt, const long long *__restrict__ splits, const Ctrl *__restrict__ c, int p,
+        typename Key<KT>::U *__restrict__ samp) {
     griddep_wait();
     typedef Key<KT> K;
     typedef typename K::U U;
@@ -719,7 +766,7 @@ k_merge(typename Key<KT>::T *uk, uint32_t *uv, typename Key<KT>::T *sk, uint32_t
     const long long a1 = (out1 == b_end) ? a_end : splits[blockIdx.x + 1];
     const long long b0 = b_beg + (out0 - pb) - (a0 - a_beg);
     merge_tile<KT, NT, IPT, VALS, VEC>(cur ? sk : uk, cur ? uk : sk, cur ? svb : uv, cur ? uv : svb, n, out0,
-                                       (int)(out1 - out0), a0, a1, b0, s, sv);
+                                       (int)(out1 - out0), a0, a1, b0, s, sv, samp, (long long)blockIdx.x);
 }
 
 template <int KT, bool VALS>

@@ -37,7 +37,8 @@ namespace sr {
 namespace {
 
 // Scratch for the largest n of the widest key type; PlainSort lays it out as
-// [control block | tile extremes for the pass planner | split table | key buffer].
+// [control block | tile extremes for the pass planner | split table |
+// merge-tile samples | key buffer].
 // (the same arithmetic as PlainSort's constructor, at compile time; every call
 // checks its own layout against this size).
 constexpr size_t up256(size_t x) { return (x + 255) / 256 * 256; }
@@ -48,6 +49,7 @@ constexpr long long kMTiles64 = (SR_NOALLOC_MAX_KEYS + kMergeTile64 - 1) / kMerg
 constexpr size_t kScratchBytes = up256(sizeof(Ctrl)) +
                                  up256((size_t)(2 * kTiles64 + 2 * ((kTiles64 + 1) / 2) + 2) * 8) +
                                  up256((size_t)(kMTiles64 + 1) * 8) +
+                                 (SR_SPLIT_SAMPLES ? up256((size_t)(2 * kMTiles64) * 8) : 0) +
                                  up256((size_t)SR_NOALLOC_MAX_KEYS * 8);
 
 // The scratch itself.  In host code this name is only a host-side stand-in

@@ -14,6 +14,10 @@
 //   k_plan        which merge passes have any run pair out of order.
 //   per pass p    k_partition (merge-path splits of every output tile) and
 //                 k_merge (policy e1); passes with every pair in order skip.
+//                 The block sort and every merge record the first and last
+//                 key of each merge tile they write; the next pass's split
+//                 search runs over those samples first and reads keys only
+//                 within one tile.
 //   k_copy_back   if skipped passes left the result in scratch, copy it home.
 #pragma once
 
@@ -36,7 +40,7 @@ template <int KT, bool VALS> struct PlainSort {
     long long n = 0, tiles = 0, mtiles = 0;
     int passes = 0;
     // byte offsets inside the scratch area
-    size_t off_ctrl = 0, off_plan = 0, off_split = 0, off_keys = 0, off_vals = 0, bytes = 0;
+    size_t off_ctrl = 0, off_plan = 0, off_split = 0, off_samp = 0, off_keys = 0, off_vals = 0, bytes = 0;
 
     explicit PlainSort(size_t n_) {
         n = (long long)n_;
@@ -47,7 +51,8 @@ template <int KT, bool VALS> struct PlainSort {
         off_plan = align_up(sizeof(Ctrl), 256);
         const size_t plan_bytes = align_up((size_t)(2 * tiles + 2 * ((tiles + 1) / 2) + 2) * sizeof(U), 256);
         off_split = off_plan + plan_bytes;
-        off_keys = off_split + align_up((size_t)(mtiles + 1) * 8, 256);
+        off_samp = off_split + align_up((size_t)(mtiles + 1) * 8, 256);
+        off_keys = off_samp + (SR_SPLIT_SAMPLES && passes > 0 ? align_up((size_t)(2 * mtiles) * sizeof(U), 256) : 0);
         const size_t kb = passes > 0 ? align_up((size_t)n * sizeof(T), 256) : 0;
         off_vals = off_keys + kb;
         const size_t vb = (VALS && passes > 0) ? align_up((size_t)n * 4, 256) : 0;
@@ -67,6 +72,7 @@ template <int KT, bool VALS> struct PlainSort {
         U *plo2 = phi + tiles;
         U *phi2 = plo2 + (tiles + 1) / 2 + 1;
         long long *splits = (long long *)(scratch + off_split);
+        U *samp = SR_SPLIT_SAMPLES && passes > 0 ? (U *)(scratch + off_samp) : nullptr;
         T *sk = (T *)(scratch + off_keys);
         uint32_t *sv = (uint32_t *)(scratch + off_vals);
         const int P = passes;
@@ -90,7 +96,7 @@ template <int KT, bool VALS> struct PlainSort {
             const size_t bs_smem = (size_t)TS * (sizeof(U) + (VALS ? 4 : 0));
             if ((st = allow_smem(k_block_sort<KT, SNT, IPT, VALS>, bs_smem)) != SR_OK) break;
             SR_LAUNCH(SR_KERNEL_BLOCK_SORT, (k_block_sort<KT, SNT, IPT, VALS>), (unsigned)tiles, SNT,
-                      bs_smem, s, uk, uv, cur0 ? sk : uk, cur0 ? sv : uv, n, ctrl, plo, phi);
+                      bs_smem, s, uk, uv, cur0 ? sk : uk, cur0 ? sv : uv, n, ctrl, plo, phi, samp, (int)NV);
             if (P == 0) break;
             if ((tiles + PLAN_CHUNK - 1) / PLAN_CHUNK > PLAN_CHUNK) { st = SR_ERR_UNSUPPORTED; break; }
             SR_LAUNCH(SR_KERNEL_PARTITION, (k_plan<KT>), (unsigned)((tiles + PLAN_CHUNK - 1) / PLAN_CHUNK),
@@ -104,13 +110,13 @@ template <int KT, bool VALS> struct PlainSort {
                 const long long nb = mtiles + 1;
                 const int lg = partition_lg(nb);
                 SR_LAUNCH(SR_KERNEL_PARTITION, (k_partition<KT>), (unsigned)(((nb << lg) + 255) / 256), 256, 0,
-                          s, uk, sk, n, w, NV, nb, splits, ctrl, p, lg);
+                          s, uk, sk, n, w, NV, nb, splits, ctrl, p, lg, samp);
                 if (vec) {
                     SR_LAUNCH(SR_KERNEL_MERGE, (k_merge<KT, NT, IPT, VALS, true>), (unsigned)mtiles, NT,
-                              m_smem, s, uk, uv, sk, sv, n, w, lgt, splits, ctrl, p);
+                              m_smem, s, uk, uv, sk, sv, n, w, lgt, splits, ctrl, p, samp);
                 } else {
                     SR_LAUNCH(SR_KERNEL_MERGE, (k_merge<KT, NT, IPT, VALS, false>), (unsigned)mtiles, NT,
-                              m_smem, s, uk, uv, sk, sv, n, w, lgt, splits, ctrl, p);
+                              m_smem, s, uk, uv, sk, sv, n, w, lgt, splits, ctrl, p, samp);
                 }
             }
             if (st != SR_OK) break;
