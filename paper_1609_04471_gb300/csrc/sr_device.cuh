@@ -186,6 +186,28 @@ __device__ __forceinline__ long long warp_split(const typename K::T *__restrict_
 
 // IPT outputs of the stable merge of s[a..a_end) and s[b..b_end) into
 // registers; ix[i] is the shared-memory index each output came from.
+// serial_merge for buffers with readable slack: one shared load per step (the
+// next key of whichever side was taken), with no bounds test on the load.
+// Reads reach index max(a_end, b_end) + IPT + 1 at most (a thread whose
+// outputs run past the end keeps taking from an exhausted side), so s must be
+// readable that far; keys read past a range's end are never selected.
+template <typename U, int IPT>
+__device__ __forceinline__ void serial_merge_slack(const U *s, int a, int a_end, int b, int b_end,
+                                                   U (&k)[IPT], int (&ix)[IPT]) {
+    U ak = s[a];
+    U bk = s[b];
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+        const bool take_a = (b >= b_end) || ((a < a_end) && !(bk < ak));
+        k[i] = take_a ? ak : bk;
+        ix[i] = take_a ? a : b;
+        const int nx = (take_a ? a : b) + 1;
+        const U nk = s[nx];
+        if (take_a) { a = nx; ak = nk; }
+        else        { b = nx; bk = nk; }
+    }
+}
+
 template <typename U, int IPT>
 __device__ __forceinline__ void serial_merge(const U *s, int a, int a_end, int b, int b_end,
                                              U (&k)[IPT], int (&ix)[IPT]) {

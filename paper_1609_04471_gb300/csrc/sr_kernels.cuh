@@ -8,6 +8,9 @@
 #ifndef SR_SPLIT_SAMPLES
 #define SR_SPLIT_SAMPLES 1  // merge splits searched over recorded tile samples first
 #endif
+#ifndef SR_MERGE_1LD
+#define SR_MERGE_1LD 1      // global merge tiles: one unguarded shared load per merge step (padded buffer)
+#endif
 #ifndef SR_FEW_KEYS
 #define SR_FEW_KEYS 1       // the few-distinct-keys path (4-byte keys, keys only)
 #endif
@@ -558,8 +561,9 @@ inline int partition_lg(long long nbound) {
 // Merges one output tile: outputs [out0, out0 + cnt) of the stable merge of
 // the sorted ranges A = src[a0 .. a1) and B = src[b0 .. b0 + cnt - (a1 - a0)),
 // written to dst at out0.  All threads of the CTA call it; s / sv are shared
-// buffers of NT*IPT + 16 keys / values.  `n` bounds the buffers (loads stay
-// below it).
+// buffers of NT*IPT + 16 keys / values, and with SR_MERGE_1LD the key buffer
+// must stay readable IPT + 8 keys further (the memory after it: the value
+// buffer, or padding).  `n` bounds the global buffers (loads stay below it).
 //
 // VEC (every buffer 16-byte aligned): the ranges are staged as windows of
 // 4-key groups starting on a group boundary, so every group moves with 128-bit
@@ -656,7 +660,10 @@ __device__ __forceinline__ void merge_tile(const typename Key<KT>::T *__restrict
     const int sp = merge_path(s + sa, acnt, s + sb, bcnt, diag);
     U k[IPT];
     int ix[IPT];
-    serial_merge<U, IPT>(s, sa + sp, sa + acnt, sb + diag - sp, sb + bcnt, k, ix);
+    if (SR_MERGE_1LD)
+        serial_merge_slack<U, IPT>(s, sa + sp, sa + acnt, sb + diag - sp, sb + bcnt, k, ix);
+    else
+        serial_merge<U, IPT>(s, sa + sp, sa + acnt, sb + diag - sp, sb + bcnt, k, ix);
     uint32_t v[IPT];
     if (VALS) {
 #pragma unroll
