@@ -558,12 +558,20 @@ inline int partition_lg(long long nbound) {
     return lg;
 }
 
+// Dynamic shared memory that merge_tile needs: NT*IPT + 16 staged keys (and
+// as many values), plus the key slack the one-load merge step reads into.
+template <typename U, int NT, int IPT, bool VALS>
+constexpr size_t merge_tile_smem() {
+    return (size_t)(NT * IPT + 16) * (sizeof(U) + (VALS ? 4 : 0)) + (SR_MERGE_1LD ? (size_t)(IPT + 8) * sizeof(U) : 0);
+}
+
 // Merges one output tile: outputs [out0, out0 + cnt) of the stable merge of
 // the sorted ranges A = src[a0 .. a1) and B = src[b0 .. b0 + cnt - (a1 - a0)),
 // written to dst at out0.  All threads of the CTA call it; s / sv are shared
 // buffers of NT*IPT + 16 keys / values, and with SR_MERGE_1LD the key buffer
 // must stay readable IPT + 8 keys further (the memory after it: the value
-// buffer, or padding).  `n` bounds the global buffers (loads stay below it).
+// buffer, or padding) -- merge_tile_smem gives the dynamic shared memory for
+// s followed by sv.  `n` bounds the global buffers (loads stay below it).
 //
 // VEC (every buffer 16-byte aligned): the ranges are staged as windows of
 // 4-key groups starting on a group boundary, so every group moves with 128-bit

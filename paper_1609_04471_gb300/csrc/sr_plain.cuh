@@ -101,10 +101,7 @@ template <int KT, bool VALS> struct PlainSort {
             if ((tiles + PLAN_CHUNK - 1) / PLAN_CHUNK > PLAN_CHUNK) { st = SR_ERR_UNSUPPORTED; break; }
             SR_LAUNCH(SR_KERNEL_PARTITION, (k_plan<KT>), (unsigned)((tiles + PLAN_CHUNK - 1) / PLAN_CHUNK),
                       1024, 0, s, plo, phi, plo2, phi2, n, tiles, P, cur0, ctrl);
-            // staged keys (+16 of window slack) and values; the single-load
-            // serial merge may read IPT + 8 keys past the staged keys
-            const size_t m_smem = (size_t)(NV + 16) * (sizeof(U) + (VALS ? 4 : 0)) +
-                                  (SR_MERGE_1LD ? (size_t)(IPT + 8) * sizeof(U) : 0);
+            const size_t m_smem = merge_tile_smem<U, NT, IPT, VALS>();
             if ((st = allow_smem(k_merge<KT, NT, IPT, VALS, true>, m_smem)) != SR_OK) break;
             if ((st = allow_smem(k_merge<KT, NT, IPT, VALS, false>, m_smem)) != SR_OK) break;
             for (int p = 0; p < P; ++p) {

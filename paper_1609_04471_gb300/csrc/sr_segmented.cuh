@@ -653,7 +653,9 @@ sr_status segmented_run_t(const typename Key<KT>::T *in, typename Key<KT>::T *ou
         }
         SR_LAUNCH(SR_KERNEL_SEGMENTED, (k_seg_sort<KT, CFG>), sort_grid, SNT, sort_smem, s, in, out, alt, d_off,
                   bucket_mode ? 0ll : nchunks, chunk_first, medium, big, tile_base, ctrl);
-        const size_t m_smem = (size_t)(NV + 16) * sizeof(U);
+        const size_t m_smem = merge_tile_smem<U, MNT, MIPT, false>();
+        if ((st = allow_smem(k_seg_merge<KT, MNT, MIPT, true>, m_smem)) != SR_OK) break;
+        if ((st = allow_smem(k_seg_merge<KT, MNT, MIPT, false>, m_smem)) != SR_OK) break;
         const int merge_grid = sm_count() * 8;
         for (int p = 0; p < passes_upper; ++p) {
             if (vec) {
