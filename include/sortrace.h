@@ -273,7 +273,10 @@ typedef struct {
     int32_t passes_skipped;     /* passes found already in order (no bytes moved) */
     int32_t input_class;        /* 0 unsorted, 1 sorted, 2 strictly descending,
                                    3 at most 64 distinct keys (4-byte keys, keys only:
-                                   counted per distinct key and written as runs) */
+                                   counted per distinct key and written as runs),
+                                   4 few displaced keys (keys only: the keys left in
+                                   order merged with the displaced ones, sorted on
+                                   the side) */
     int32_t fallback;           /* learned: 1 if the bucket check failed */
     uint64_t runs;              /* Run(A) of the input, from the scan */
     uint64_t bytes_moved;       /* DRAM bytes the executed passes read + wrote */
@@ -311,7 +314,8 @@ enum {
     SR_KERNEL_COPY = 5,       /* copy-back / gather */
     SR_KERNEL_SEGMENTED = 6,  /* segmented / bucket sorts */
     SR_KERNEL_MODEL = 7,      /* learned router: train, predict, histogram, scatter */
-    SR_KERNEL_KINDS = 8
+    SR_KERNEL_DISPLACED = 8,  /* few displaced keys: bounds, split, bucket sorts, merge */
+    SR_KERNEL_KINDS = 9
 };
 
 typedef struct {

@@ -87,7 +87,7 @@ SIGNATURES = {
     "sr_profile_end": (_i32, [_vp, _i32]),
 }
 
-KERNEL_KINDS = ("detect", "reverse", "block_sort", "partition", "merge", "copy", "segmented", "model")
+KERNEL_KINDS = ("detect", "reverse", "block_sort", "partition", "merge", "copy", "segmented", "model", "displaced")
 
 
 class SegmentedConfig(ctypes.Structure):

@@ -313,7 +313,7 @@ __device__ __forceinline__ void block_sort(U (&k)[IPT], uint32_t (&v)[IPT], U *s
 
 // ------------------------------------------------------- per-call control
 
-enum { MODE_SORT = 0, MODE_SORTED = 1, MODE_REVERSE = 2, MODE_FEW = 3 };
+enum { MODE_SORT = 0, MODE_SORTED = 1, MODE_REVERSE = 2, MODE_FEW = 3, MODE_REM = 4 };
 enum { MAX_PASSES = 48 };
 // Few distinct keys: at most FEW_MAX distinct order images (4-byte keys).
 enum { FEW_MAX = 64, FEW_SLOTS = 128 };
@@ -343,12 +343,19 @@ struct Ctrl {
     unsigned long long few_slot[FEW_SLOTS];
     unsigned int few_sorted[FEW_MAX];            // the distinct images, ascending
     unsigned long long few_count[FEW_MAX];       // keys equal to each
+    // Few displaced keys (keys only): the path was tried (rem_active), a
+    // bucket overflowed (rem_over), or it wrote the output (rem_gate).
+    int rem_active;
+    int rem_over;
+    int rem_gate;
+    unsigned long long rem_dcount;               // keys that went through the buckets
 };
 
 __device__ __forceinline__ int call_mode(const Ctrl *c, long long n) {
     if (c->descents == 0) return MODE_SORTED;
     if (c->nondescents == 0 && n > 1) return MODE_REVERSE;
     if (c->few_active) return MODE_FEW;
+    if (c->rem_gate) return MODE_REM;
     return MODE_SORT;
 }
 

@@ -11,6 +11,9 @@
 #ifndef SR_MERGE_1LD
 #define SR_MERGE_1LD 1      // global merge tiles: one unguarded shared load per merge step (padded buffer)
 #endif
+#ifndef SR_REM_KEYS
+#define SR_REM_KEYS 1       // the few-displaced-keys path (keys only)
+#endif
 #ifndef SR_FEW_KEYS
 #define SR_FEW_KEYS 1       // the few-distinct-keys path (4-byte keys, keys only)
 #endif
@@ -27,10 +30,36 @@ namespace sr {
 // the next vector's first, read again through the read-only path.
 // `gate` (optional): when it points at 0 the scan counts nothing, so the call
 // sees a "sorted" input and every later kernel of the sequence returns at once.
+// The median of the keys at positions p-4 .. p+4 (positions past n read the
+// last key), as an order image.
+template <int KT>
+__device__ __forceinline__ typename Key<KT>::U median9_image(const typename Key<KT>::T *__restrict__ keys,
+                                                             long long n, long long p) {
+    typedef Key<KT> K;
+    typedef typename K::U U;
+    U x[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) x[i] = K::ord(keys[min(p - 4 + i, n - 1)]);
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+#pragma unroll
+        for (int i = r & 1; i + 1 < 9; i += 2) {
+            const U a = x[i], b = x[i + 1];
+            x[i] = a < b ? a : b;
+            x[i + 1] = a < b ? b : a;
+        }
+    }
+    return x[4];
+}
+
+// `med` (optional): the scan also records, for every multiple b*mt of mt
+// below n (mt divides NT*IPT), the median of the 9 keys around it in med[b]
+// (med[0] = 0), for the few-displaced-keys path's value bounds.
 template <int KT, int NT, int IPT>
 __global__ void __launch_bounds__(NT) k_detect(const typename Key<KT>::T *__restrict__ keys,
                                                long long n, Ctrl *__restrict__ c,
-                                               const int *__restrict__ gate) {
+                                               const int *__restrict__ gate,
+                                               typename Key<KT>::U *__restrict__ med, int mt) {
     griddep_wait();
     if (gate && *gate == 0) return;
     typedef Key<KT> K;
@@ -92,6 +121,11 @@ __global__ void __launch_bounds__(NT) k_detect(const typename Key<KT>::T *__rest
         if (red[1]) atomicAdd(&c->nondescents, (unsigned long long)red[1]);
         if (!red[2]) atomicAdd(&c->tiles_ascending, 1ull);
         if (!red[3]) atomicAdd(&c->tiles_descending, 1ull);
+    }
+    // after the scan: the keys around this tile's multiples of mt are cached
+    if (med && t < NT * IPT / mt) {
+        const long long b = (long long)blockIdx.x * (NT * IPT / mt) + t;
+        if (b * mt < n) med[b] = b == 0 ? U(0) : median9_image<KT>(keys, n, b * mt);
     }
 }
 

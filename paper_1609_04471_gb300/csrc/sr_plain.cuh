@@ -8,6 +8,10 @@
 //                 counts each; if all were in the set, k_few_write writes the
 //                 runs and nothing else runs.
 //   k_reverse     strictly descending input: one reversal, nothing else runs.
+//   k_rem_*       few displaced keys (keys only, when the plan asks for it;
+//                 sr_rem.cuh): the keys left in order go straight to their
+//                 block, the displaced ones through small per-tile buckets,
+//                 and nothing else runs.
 //   k_block_sort  tiles of SORT_NT*IPT keys sorted in shared memory (ascending
 //                 tiles kept, strictly descending tiles reversed); records each
 //                 tile's smallest and largest key.
@@ -23,6 +27,7 @@
 
 #include "sr_device.cuh"
 #include "sr_kernels.cuh"
+#include "sr_rem.cuh"
 #include "sr_runtime.cuh"
 
 namespace sr {
@@ -39,10 +44,20 @@ template <int KT, bool VALS> struct PlainSort {
 
     long long n = 0, tiles = 0, mtiles = 0;
     int passes = 0;
+    bool rem = false;                  // the few-displaced-keys path is queued
+    long long rem_dmax = 0;            // most descents for which it is tried
+    long long rtiles = 0;              // its tiles of RT keys
+    enum { RT = REM_TNT * IPT, RMIPT = IPT + (REM_CAP + REM_TNT - 1) / REM_TNT };
+    static_assert((SNT * IPT) % RT == 0, "the scan's tile holds whole tiles of the displaced-keys path");
+    static_assert(REM_TNT * RMIPT >= RT + REM_CAP, "a tile's block fits one merge tile");
     // byte offsets inside the scratch area
     size_t off_ctrl = 0, off_plan = 0, off_split = 0, off_samp = 0, off_keys = 0, off_vals = 0, bytes = 0;
+    size_t off_rem_buck = 0, off_rem_bound = 0, off_rem_scount = 0, off_rem_bcount = 0, off_rem_blk = 0;
 
-    explicit PlainSort(size_t n_) {
+    // rem_: queue the few-displaced-keys path (keys only, at least
+    // REM_MIN_TILES sort tiles).  Its tiles are RT = REM_TNT x IPT keys.
+    enum { REM_MIN_TILES = 16 };
+    explicit PlainSort(size_t n_, bool rem_ = false) {
         n = (long long)n_;
         tiles = (n + TS - 1) / TS;
         mtiles = (n + NV - 1) / NV;
@@ -57,6 +72,18 @@ template <int KT, bool VALS> struct PlainSort {
         off_vals = off_keys + kb;
         const size_t vb = (VALS && passes > 0) ? align_up((size_t)n * 4, 256) : 0;
         bytes = off_vals + vb;
+        rem = rem_ && !VALS && tiles >= REM_MIN_TILES && passes > 0;
+        if (rem) {
+            rem_dmax = n / 32;
+            rtiles = (n + RT - 1) / RT;
+            // the buckets follow the key buffer directly: one index space for the merge
+            off_rem_buck = off_keys + kb;
+            off_rem_bound = off_rem_buck + align_up((size_t)rtiles * REM_CAP * sizeof(T), 256);
+            off_rem_scount = off_rem_bound + align_up((size_t)(rtiles + 1) * sizeof(U), 256);
+            off_rem_bcount = off_rem_scount + align_up((size_t)rtiles * 4, 256);
+            off_rem_blk = off_rem_bcount + align_up((size_t)rtiles * 4, 256);
+            bytes = off_rem_blk + align_up((size_t)(rtiles + 1) * 8, 256);
+        }
     }
 
     // Launches the whole sequence on stream s.  The block sort writes to the
@@ -81,8 +108,9 @@ template <int KT, bool VALS> struct PlainSort {
         sr_status st = SR_OK;
         do {
             if (cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s) != cudaSuccess) { st = launch_status(); break; }
+            U *rem_bound = rem ? (U *)(scratch + off_rem_bound) : nullptr;   // the scan records its medians
             SR_LAUNCH(SR_KERNEL_DETECT, (k_detect<KT, SNT, IPT>), (unsigned)tiles, SNT, 0, s,
-                      uk, n, ctrl, gate);
+                      uk, n, ctrl, gate, rem_bound, (int)RT);
             constexpr bool FEW = sizeof(T) == 4 && !VALS && SR_FEW_KEYS;   // few distinct keys: written as runs
             if constexpr (FEW)
                 SR_LAUNCH(SR_KERNEL_DETECT, k_few_sample<KT>, FEW_SAMPLE / FEW_NT, FEW_NT, 0, s, uk, n, ctrl, gate);
@@ -92,6 +120,35 @@ template <int KT, bool VALS> struct PlainSort {
                 SR_LAUNCH(SR_KERNEL_COPY, k_few_count<KT>, grid_for(n, 256, 152 * 8), 256, 0, s, uk, n, ctrl);
                 SR_LAUNCH(SR_KERNEL_COPY, k_few_write<KT>, grid_for(n / 4 + 1, 256, 152 * 8), 256, 0, s, uk, n,
                           ctrl);
+            }
+            if constexpr (!VALS) if (rem) {
+                U *bound = rem_bound;
+                unsigned int *scount = (unsigned int *)(scratch + off_rem_scount);
+                unsigned int *bcount = (unsigned int *)(scratch + off_rem_bcount);
+                long long *blk = (long long *)(scratch + off_rem_blk);
+                T *buck = (T *)(scratch + off_rem_buck);
+                const long long dofs = (long long)((off_rem_buck - off_keys) / sizeof(T));
+                SR_LAUNCH(SR_KERNEL_DISPLACED, k_rem_bounds<KT>, 1, REM_NT, 0, s, n, rtiles, rem_dmax, ctrl, bound,
+                          bcount);
+                // grids of SR_REM_GRID CTAs per SM that loop over the tiles:
+                // when the path is not taken, every CTA returns at once
+                const unsigned rgrid = (unsigned)grid_for(rtiles, 1, 152 * SR_REM_GRID);
+                const size_t sp_smem = (size_t)RT * (sizeof(U) + 1);
+                SR_LAUNCH(SR_KERNEL_DISPLACED, (k_rem_split<KT, REM_TNT, IPT>), rgrid, REM_TNT, sp_smem, s, uk, n,
+                          rtiles, ctrl, bound, sk, scount, buck, bcount);
+                SR_LAUNCH(SR_KERNEL_DISPLACED, k_rem_bsort<KT>, rgrid + 1, REM_BSORT_NT, 0, s, buck, rtiles, ctrl,
+                          scount, bcount, blk);
+                const size_t rm_smem = merge_tile_smem<U, REM_TNT, RMIPT, false>();
+                if ((st = allow_smem(k_rem_merge<KT, REM_TNT, RMIPT, true>, rm_smem)) != SR_OK) break;
+                if ((st = allow_smem(k_rem_merge<KT, REM_TNT, RMIPT, false>, rm_smem)) != SR_OK) break;
+                const long long n_src = dofs + rtiles * (long long)REM_CAP;
+                if (vec) {
+                    SR_LAUNCH(SR_KERNEL_DISPLACED, (k_rem_merge<KT, REM_TNT, RMIPT, true>), rgrid, REM_TNT, rm_smem,
+                              s, uk, sk, n_src, dofs, (int)RT, rtiles, ctrl, scount, bcount, blk);
+                } else {
+                    SR_LAUNCH(SR_KERNEL_DISPLACED, (k_rem_merge<KT, REM_TNT, RMIPT, false>), rgrid, REM_TNT, rm_smem,
+                              s, uk, sk, n_src, dofs, (int)RT, rtiles, ctrl, scount, bcount, blk);
+                }
             }
             const size_t bs_smem = (size_t)TS * (sizeof(U) + (VALS ? 4 : 0));
             if ((st = allow_smem(k_block_sort<KT, SNT, IPT, VALS>, bs_smem)) != SR_OK) break;

@@ -232,7 +232,8 @@ extern "C" sr_status sr_get_stats(sr_stats *out) {
     const unsigned long long n = out->n;
     const unsigned long long elem = (unsigned long long)(r.key_bytes + r.val_bytes);
     out->runs = n ? c.descents + 1 : 0;
-    out->input_class = c.descents == 0 ? 1 : (c.nondescents == 0 && n > 1 ? 2 : (c.few_active ? 3 : 0));
+    out->input_class = c.descents == 0 ? 1
+                       : (c.nondescents == 0 && n > 1 ? 2 : (c.few_active ? 3 : (c.rem_gate ? 4 : 0)));
     unsigned long long bytes = n * (unsigned long long)r.key_bytes;     // the scan reads the keys
     int skipped = 0, merged = 0;
     if (out->input_class == 0) {
@@ -246,6 +247,10 @@ extern "C" sr_status sr_get_stats(sr_stats *out) {
         bytes += 2 * n * elem;                                          // one reversal
     } else if (out->input_class == 3) {
         bytes += 2 * n * elem;                                          // counted, then written as runs
+    } else if (out->input_class == 4) {
+        bytes += 2 * n * elem;                                          // split: in-order keys and buckets
+        bytes += 2 * c.rem_dcount * elem;                               // bucket sorts
+        bytes += 2 * n * elem;                                          // per-tile merges into place
     }
     out->passes_skipped = skipped;
     out->bytes_moved = bytes;

@@ -21,7 +21,7 @@ template <int KT, bool VALS>
 static sr_status sort_impl(void *d_keys, uint32_t *d_vals, size_t n, cudaStream_t s, int call) {
     typedef PlainSort<KT, VALS> PS;
     typedef typename PS::T T;
-    const PS plan(n);
+    const PS plan(n, !VALS && SR_REM_KEYS);
     CallRecord &rec = call_record();
     rec = CallRecord();
     rec.host.call = call;
@@ -86,7 +86,7 @@ static sr_status detect_impl(const void *d_keys, size_t n, sr_run_info *out, cud
     do {
         if (cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s) != cudaSuccess) { st = launch_status(); break; }
         SR_LAUNCH(SR_KERNEL_DETECT, (k_detect<KT, SNT, IPT>), (unsigned)tiles, SNT, 0, s,
-                  (const T *)d_keys, N, ctrl, (const int *)nullptr);
+                  (const T *)d_keys, N, ctrl, (const int *)nullptr, (typename K::U *)nullptr, 1);
         if (cudaMemcpyAsync(&h, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) {
             st = launch_status();

@@ -350,3 +350,70 @@ def test_full_size_2_28_pairs(gpu_lib):
     assert int(torch.bincount(idx, minlength=1 << 28).max()) == 1
     same = xk[1:] == xk[:-1]
     assert bool((xv[1:][same] > xv[:-1][same]).all())
+
+
+def _exchanged(rng, sorted_keys, frac, adjacent=False):
+    """A k-exchange list (Section 2): sorted keys, then floor(frac * n)
+    exchanges of a uniform position with a uniform partner (or with the key
+    two places on, for clustered displacements)."""
+    a = sorted_keys.copy()
+    n = a.size
+    for _ in range(int(frac * n)):
+        i = int(rng.integers(0, n - 2))
+        j = i + 2 if adjacent else int(rng.integers(0, n))
+        a[i], a[j] = a[j], a[i]
+    return a
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.float32, np.uint64, np.int64])
+def test_few_displaced_keys(gpu_lib, dtype):
+    """Keys only, a few keys away from their place (k-exchange lists, the Rem
+    measure of Section 2): the keys left in order go straight to their block
+    and the displaced ones through per-tile buckets (input_class 4).  Output
+    bit-exact against the oracle on uniform and clustered exchanges and on a
+    ragged size; bytes moved follow the path's model."""
+    rng = np.random.default_rng(62)
+    kb = np.dtype(dtype).itemsize
+    for n, frac, adjacent in (((1 << 20) + 17, 0.01, False), (700_001, 0.005, True), (1 << 22, 0.01, False)):
+        base = np.sort(_random(rng, n, dtype))
+        if dtype == np.float32:
+            base = base[~np.isnan(base)]
+        a = _exchanged(rng, base, frac, adjacent)
+        got = _gpu_sort(gpu_lib, a)
+        assert got.tobytes() == oracle.sort_keys(a).tobytes(), (dtype, n, frac, adjacent)
+        st = gpu_lib.stats()
+        assert st["input_class"] == 4, (dtype, n, st["input_class"])
+        m = a.size
+        assert 5 * kb * m <= st["bytes_moved"] <= 5 * kb * m + 2 * kb * (m // 16)
+
+
+def test_few_displaced_keys_fallbacks(gpu_lib):
+    """The path gives way to the ordinary sort (input_class 0), with the same
+    output, when a bucket would overflow (exchanges among few distinct values
+    crowd one bucket), when there are fewer descents than sort tiles, and for
+    pairs (payload order); an unaligned key pointer still takes it."""
+    import torch
+    rng = np.random.default_rng(63)
+    # few distinct values (more than 64): equal keys pile into a few buckets
+    a = _exchanged(rng, np.sort(rng.integers(-50, 50, 400_000).astype(np.int32)), 0.005)
+    assert _gpu_sort(gpu_lib, a).tobytes() == oracle.sort_keys(a).tobytes()
+    assert gpu_lib.stats()["input_class"] == 0
+    # fewer descents than tiles
+    a = _exchanged(rng, np.sort(_random(rng, 1 << 20, np.int32)), 10 / (1 << 20))
+    assert _gpu_sort(gpu_lib, a).tobytes() == oracle.sort_keys(a).tobytes()
+    assert gpu_lib.stats()["input_class"] == 0
+    # pairs
+    k = _exchanged(rng, np.sort(_random(rng, 300_000, np.int32)), 0.01)
+    v = np.arange(k.size, dtype=np.uint32)
+    gk, gv = _gpu_pairs(gpu_lib, k, v)
+    ok, ov = oracle.sort_pairs(k, v)
+    assert gk.tobytes() == ok.tobytes() and gv.tobytes() == ov.tobytes()
+    assert gpu_lib.stats()["input_class"] == 0
+    # a key pointer 4 bytes past a 16-byte boundary
+    a = _exchanged(rng, np.sort(_random(rng, 500_000, np.int32)), 0.01)
+    buf = torch.zeros(a.size + 1, dtype=torch.int32, device="cuda")
+    buf[1:] = torch.from_numpy(a.view(np.int32)).cuda()
+    gpu_lib.sort_keys(buf[1:], key_type=0)
+    assert gpu_lib.stats()["input_class"] == 4
+    assert buf[1:].cpu().numpy().tobytes() == oracle.sort_keys(a).tobytes()
+    assert int(buf[0]) == 0
