@@ -538,19 +538,18 @@ k_plan(const typename Key<KT>::U *__restrict__ lo, const typename Key<KT>::U *__
 // 2^lg lanes per boundary (the host picks lg: wide groups take fewer
 // dependent rounds, narrow ones fewer scattered loads when there are many
 // boundaries).
+// The merge-path split of output tile b (outputs from b*nv) of a merge pass
+// over runs of w keys of src: the index in src where the tile's share of run
+// A starts.  A group of 2^lg lanes computes it together (all lanes of the
+// group get it).  samp (optional): the first and last key of every merge
+// tile of src, as recorded when src was written; with it the search first
+// narrows the split to one tile's stretch and then reads keys only there.
 template <int KT>
-__global__ void __launch_bounds__(256)
-k_partition(const typename Key<KT>::T *__restrict__ uk, const typename Key<KT>::T *__restrict__ sk,
-            long long n, long long w, int nv, long long nbound, long long *__restrict__ splits,
-            const Ctrl *__restrict__ c, int p, int lg, const typename Key<KT>::U *__restrict__ samp) {
-    griddep_wait();
+__device__ __forceinline__ long long merge_split(const typename Key<KT>::T *__restrict__ src, long long n,
+                                                 long long w, int nv, long long b, int lane, int lg,
+                                                 const typename Key<KT>::U *__restrict__ samp) {
     typedef Key<KT> K;
     typedef typename K::U U;
-    const int lane = threadIdx.x & 31;
-    const long long b = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> lg;
-    if (b >= nbound) return;                       // uniform across the group
-    if (c->unordered[p] == 0) return;             // also 0 for every pass unless the input needs sorting
-    const typename K::T *src = c->src_buf[p] ? sk : uk;
     const long long out = min(b * (long long)nv, n);
     const long long pb = (out / (2 * w)) * (2 * w);
     const long long a_beg = pb, a_end = min(pb + w, n);
@@ -559,9 +558,8 @@ k_partition(const typename Key<KT>::T *__restrict__ uk, const typename Key<KT>::
     long long lo = max(0ll, d - nb), hi = min(d, na);
     if (samp && out < n && hi > lo) {
         // Coarse: the merge-path test at the multiples m = j*nv uses only the
-        // first key of A's tile j and the last key of B's tile d/nv - j - 1,
-        // which the previous pass (or the block sort) recorded; d, a_beg and
-        // b_beg are multiples of nv here.
+        // first key of A's tile j and the last key of B's tile d/nv - j - 1;
+        // d, a_beg and b_beg are multiples of nv here.
         const long long jlo = (lo + nv - 1) / nv, jhi = (hi - 1) / nv, dj = d / nv;
         const long long ta = a_beg / nv, tb = b_beg / nv;
         const long long jt = group_search(jlo, jhi + 1, lane, lg, [&](long long j) {
@@ -578,7 +576,26 @@ k_partition(const typename Key<KT>::T *__restrict__ uk, const typename Key<KT>::
         const U y = K::ord(src[b_beg + d - 1 - m]);
         return !(y < x);
     });
-    if ((lane & ((1 << lg) - 1)) == 0) splits[b] = a_beg + sp;
+    return a_beg + sp;
+}
+
+// Splits of every output tile boundary of pass p, a group of 2^lg lanes per
+// boundary.  The tile samples of the buffer a pass reads are at samp +
+// smt * (that buffer: 0 the caller's, 1 the scratch copy).
+template <int KT>
+__global__ void __launch_bounds__(256)
+k_partition(const typename Key<KT>::T *__restrict__ uk, const typename Key<KT>::T *__restrict__ sk,
+            long long n, long long w, int nv, long long nbound, long long *__restrict__ splits,
+            const Ctrl *__restrict__ c, int p, int lg, const typename Key<KT>::U *__restrict__ samp,
+            long long smt) {
+    griddep_wait();
+    const int lane = threadIdx.x & 31;
+    const long long b = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> lg;
+    if (b >= nbound) return;                       // uniform across the group
+    if (c->unordered[p] == 0) return;             // also 0 for every pass unless the input needs sorting
+    const int cur = c->src_buf[p];
+    const long long sp = merge_split<KT>(cur ? sk : uk, n, w, nv, b, lane, lg, samp ? samp + cur * smt : nullptr);
+    if ((lane & ((1 << lg) - 1)) == 0) splits[b] = sp;
 }
 
 // Lanes per boundary for k_partition: about SR_PARTITION_LANES searching
@@ -794,7 +811,7 @@ template <int KT, int NT, int IPT, bool VALS, bool VEC>
 __global__ void __launch_bounds__(NT)
 k_merge(typename Key<KT>::T *uk, uint32_t *uv, typename Key<KT>::T *sk, uint32_t *svb, long long n,
         long long w, int lgt, const long long *__restrict__ splits, const Ctrl *__restrict__ c, int p,
-        typename Key<KT>::U *__restrict__ samp) {
+        typename Key<KT>::U *__restrict__ samp, long long smt) {
     griddep_wait();
     typedef Key<KT> K;
     typedef typename K::U U;
@@ -814,8 +831,10 @@ k_merge(typename Key<KT>::T *uk, uint32_t *uv, typename Key<KT>::T *sk, uint32_t
     const long long a0 = splits[blockIdx.x];
     const long long a1 = (out1 == b_end) ? a_end : splits[blockIdx.x + 1];
     const long long b0 = b_beg + (out0 - pb) - (a0 - a_beg);
+    // the output's tile samples go with the buffer it lands in
     merge_tile<KT, NT, IPT, VALS, VEC>(cur ? sk : uk, cur ? uk : sk, cur ? svb : uv, cur ? uv : svb, n, out0,
-                                       (int)(out1 - out0), a0, a1, b0, s, sv, samp, (long long)blockIdx.x);
+                                       (int)(out1 - out0), a0, a1, b0, s, sv, samp ? samp + (1 - cur) * smt : nullptr,
+                                       (long long)blockIdx.x);
 }
 
 template <int KT, bool VALS>

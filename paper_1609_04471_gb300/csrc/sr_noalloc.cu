@@ -49,7 +49,7 @@ constexpr long long kMTiles64 = (SR_NOALLOC_MAX_KEYS + kMergeTile64 - 1) / kMerg
 constexpr size_t kScratchBytes = up256(sizeof(Ctrl)) +
                                  up256((size_t)(2 * kTiles64 + 2 * ((kTiles64 + 1) / 2) + 2) * 8) +
                                  up256((size_t)(kMTiles64 + 1) * 8) +
-                                 (SR_SPLIT_SAMPLES ? up256((size_t)(2 * kMTiles64) * 8) : 0) +
+                                 (SR_SPLIT_SAMPLES ? up256((size_t)(4 * kMTiles64) * 8) : 0) +
                                  up256((size_t)SR_NOALLOC_MAX_KEYS * 8);
 
 // The scratch itself.  In host code this name is only a host-side stand-in

@@ -67,7 +67,8 @@ template <int KT, bool VALS> struct PlainSort {
         const size_t plan_bytes = align_up((size_t)(2 * tiles + 2 * ((tiles + 1) / 2) + 2) * sizeof(U), 256);
         off_split = off_plan + plan_bytes;
         off_samp = off_split + align_up((size_t)(mtiles + 1) * 8, 256);
-        off_keys = off_samp + (SR_SPLIT_SAMPLES && passes > 0 ? align_up((size_t)(2 * mtiles) * sizeof(U), 256) : 0);
+        // tile samples: one set per buffer (the caller's, the scratch copy)
+        off_keys = off_samp + (SR_SPLIT_SAMPLES && passes > 0 ? align_up((size_t)(4 * mtiles) * sizeof(U), 256) : 0);
         const size_t kb = passes > 0 ? align_up((size_t)n * sizeof(T), 256) : 0;
         off_vals = off_keys + kb;
         const size_t vb = (VALS && passes > 0) ? align_up((size_t)n * 4, 256) : 0;
@@ -153,7 +154,8 @@ template <int KT, bool VALS> struct PlainSort {
             const size_t bs_smem = (size_t)TS * (sizeof(U) + (VALS ? 4 : 0));
             if ((st = allow_smem(k_block_sort<KT, SNT, IPT, VALS>, bs_smem)) != SR_OK) break;
             SR_LAUNCH(SR_KERNEL_BLOCK_SORT, (k_block_sort<KT, SNT, IPT, VALS>), (unsigned)tiles, SNT,
-                      bs_smem, s, uk, uv, cur0 ? sk : uk, cur0 ? sv : uv, n, ctrl, plo, phi, samp, (int)NV);
+                      bs_smem, s, uk, uv, cur0 ? sk : uk, cur0 ? sv : uv, n, ctrl, plo, phi,
+                      samp ? samp + cur0 * 2 * mtiles : nullptr, (int)NV);
             if (P == 0) break;
             if ((tiles + PLAN_CHUNK - 1) / PLAN_CHUNK > PLAN_CHUNK) { st = SR_ERR_UNSUPPORTED; break; }
             SR_LAUNCH(SR_KERNEL_PARTITION, (k_plan<KT>), (unsigned)((tiles + PLAN_CHUNK - 1) / PLAN_CHUNK),
@@ -167,13 +169,13 @@ template <int KT, bool VALS> struct PlainSort {
                 const long long nb = mtiles + 1;
                 const int lg = partition_lg(nb);
                 SR_LAUNCH(SR_KERNEL_PARTITION, (k_partition<KT>), (unsigned)(((nb << lg) + 255) / 256), 256, 0,
-                          s, uk, sk, n, w, NV, nb, splits, ctrl, p, lg, samp);
+                          s, uk, sk, n, w, NV, nb, splits, ctrl, p, lg, samp, 2 * mtiles);
                 if (vec) {
                     SR_LAUNCH(SR_KERNEL_MERGE, (k_merge<KT, NT, IPT, VALS, true>), (unsigned)mtiles, NT,
-                              m_smem, s, uk, uv, sk, sv, n, w, lgt, splits, ctrl, p, samp);
+                              m_smem, s, uk, uv, sk, sv, n, w, lgt, splits, ctrl, p, samp, 2 * mtiles);
                 } else {
                     SR_LAUNCH(SR_KERNEL_MERGE, (k_merge<KT, NT, IPT, VALS, false>), (unsigned)mtiles, NT,
-                              m_smem, s, uk, uv, sk, sv, n, w, lgt, splits, ctrl, p, samp);
+                              m_smem, s, uk, uv, sk, sv, n, w, lgt, splits, ctrl, p, samp, 2 * mtiles);
                 }
             }
             if (st != SR_OK) break;
