@@ -59,6 +59,9 @@ def _args():
                     help="with --profile-form batched: this launch configuration instead of tuning")
     ap.add_argument("--profile-pairs", action="store_true",
                     help="with --profile-case: a stable uint64-key + uint32-payload sort instead")
+    ap.add_argument("--profile-class", default="uniform",
+                    choices=["uniform", "reversed", "nearly_sorted", "few_unique"],
+                    help="with --profile-case (key sort): the int32 input class")
     return ap.parse_args()
 
 
@@ -474,14 +477,15 @@ def run_profile_case(args):
             x = src.clone()
             sr.sort_segmented_cfg(x, toff, best)
     else:
-        src = torch.from_numpy(si.uniform_i32(n, SEED)).cuda()
+        src = torch.from_numpy(si.int32_input(args.profile_class, n, SEED)).cuda()
         for _ in range(2):
             x = src.clone()
             sr.sort_keys(x)
     torch.cuda.synchronize()
     st = sr.stats()
     print(json.dumps({"profile_case": args.profile_case, "pairs": bool(args.profile_pairs),
-                      "form": args.profile_form, "bytes_moved": st["bytes_moved"],
+                      "form": args.profile_form, "class": args.profile_class, "input_class": st["input_class"],
+                      "bytes_moved": st["bytes_moved"],
                       "passes_planned": st["passes_planned"], "passes_skipped": st["passes_skipped"], "ok": True}))
 
 
