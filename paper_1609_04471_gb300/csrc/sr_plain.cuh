@@ -94,17 +94,19 @@ template <int KT, bool VALS> struct PlainSort {
     // sequence does nothing.
     sr_status launch(T *uk, uint32_t *uv, unsigned char *scratch, cudaStream_t s,
                      const int *gate = nullptr) const {
+        sr_status st = launch_prefix(uk, uv, scratch, s, gate);
+        if (st == SR_OK) st = launch_sort(uk, uv, scratch, s);
+        return st;
+    }
+
+    // The scan and the whole-input paths (sorted, strictly descending, few
+    // distinct keys, few displaced keys): after them the call's mode is
+    // final, and launch_sort's kernels all return at once unless it is
+    // MODE_SORT.
+    sr_status launch_prefix(T *uk, uint32_t *uv, unsigned char *scratch, cudaStream_t s,
+                            const int *gate = nullptr) const {
         Ctrl *ctrl = (Ctrl *)(scratch + off_ctrl);
-        U *plo = (U *)(scratch + off_plan);
-        U *phi = plo + tiles;
-        U *plo2 = phi + tiles;
-        U *phi2 = plo2 + (tiles + 1) / 2 + 1;
-        long long *splits = (long long *)(scratch + off_split);
-        U *samp = SR_SPLIT_SAMPLES && passes > 0 ? (U *)(scratch + off_samp) : nullptr;
         T *sk = (T *)(scratch + off_keys);
-        uint32_t *sv = (uint32_t *)(scratch + off_vals);
-        const int P = passes;
-        const int cur0 = P & 1;
         const bool vec = ((uintptr_t)uk % 16) == 0 && (!VALS || ((uintptr_t)uv % 16) == 0);
         sr_status st = SR_OK;
         do {
@@ -151,6 +153,27 @@ template <int KT, bool VALS> struct PlainSort {
                               s, uk, sk, n_src, dofs, (int)RT, rtiles, ctrl, scount, bcount, blk);
                 }
             }
+        } while (0);
+        (void)sk; (void)vec;
+        return st;
+    }
+
+    // The block sort, the pass planner, the merge passes and the copy-back.
+    sr_status launch_sort(T *uk, uint32_t *uv, unsigned char *scratch, cudaStream_t s) const {
+        Ctrl *ctrl = (Ctrl *)(scratch + off_ctrl);
+        U *plo = (U *)(scratch + off_plan);
+        U *phi = plo + tiles;
+        U *plo2 = phi + tiles;
+        U *phi2 = plo2 + (tiles + 1) / 2 + 1;
+        long long *splits = (long long *)(scratch + off_split);
+        U *samp = SR_SPLIT_SAMPLES && passes > 0 ? (U *)(scratch + off_samp) : nullptr;
+        T *sk = (T *)(scratch + off_keys);
+        uint32_t *sv = (uint32_t *)(scratch + off_vals);
+        const int P = passes;
+        const int cur0 = P & 1;
+        const bool vec = ((uintptr_t)uk % 16) == 0 && (!VALS || ((uintptr_t)uv % 16) == 0);
+        sr_status st = SR_OK;
+        do {
             const size_t bs_smem = (size_t)TS * (sizeof(U) + (VALS ? 4 : 0));
             if ((st = allow_smem(k_block_sort<KT, SNT, IPT, VALS>, bs_smem)) != SR_OK) break;
             SR_LAUNCH(SR_KERNEL_BLOCK_SORT, (k_block_sort<KT, SNT, IPT, VALS>), (unsigned)tiles, SNT,

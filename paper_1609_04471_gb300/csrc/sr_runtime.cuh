@@ -67,6 +67,11 @@ sr_status segmented_stats(const void *aux, sr_stats *out);
 sr_status learned_stats(const void *aux, sr_stats *out);
 CallRecord &call_record();
 
+// Whether per-launch profiling is on for this thread (sr_profile_begin), and
+// an adjustment of the launch count (graph replays count their kernels).
+bool profiling_on();
+void count_launches(long long k);
+
 // Kernel instrumentation: every launch site calls launch_begin / launch_end
 // around its <<<>>> (see SR_LAUNCH).
 void launch_begin(int kind, cudaStream_t s);

@@ -417,3 +417,57 @@ def test_few_displaced_keys_fallbacks(gpu_lib):
     assert gpu_lib.stats()["input_class"] == 4
     assert buf[1:].cpu().numpy().tobytes() == oracle.sort_keys(a).tobytes()
     assert int(buf[0]) == 0
+
+
+@pytest.mark.parametrize("kind", list(si.INT32_CLASSES))
+def test_repeated_calls(gpu_lib, kind):
+    """The same buffer sorted again and again: from the second call on, the
+    call replays a CUDA graph whose merge section runs only when the input
+    needs it.  Every result bit-exact against the oracle, statistics of the
+    call's own input, launches counted."""
+    import torch
+    a = si.int32_input(kind, (1 << 20) + 5, seed=11)
+    want = oracle.sort_keys(a).tobytes()
+    src = torch.from_numpy(a).cuda()
+    x = torch.empty_like(src)
+    classes = set()
+    for _ in range(4):
+        x.copy_(src)
+        l0 = gpu_lib.launch_count()
+        gpu_lib.sort_keys(x, key_type=0)
+        assert gpu_lib.launch_count() > l0
+        assert x.cpu().numpy().tobytes() == want
+        classes.add(gpu_lib.stats()["input_class"])
+    assert len(classes) == 1
+    # stable pairs on a repeated buffer as well
+    k = si.int32_input(kind, 300_007, seed=12)
+    v = np.arange(k.size, dtype=np.uint32)
+    ok, ov = oracle.sort_pairs(k, v)
+    tk, tv = torch.from_numpy(k).cuda(), torch.from_numpy(v.view(np.int32)).cuda()
+    xk, xv = torch.empty_like(tk), torch.empty_like(tv)
+    for _ in range(3):
+        xk.copy_(tk)
+        xv.copy_(tv)
+        gpu_lib.sort_pairs(xk, xv, key_type=0)
+        assert xk.cpu().numpy().tobytes() == ok.tobytes()
+        assert xv.cpu().numpy().view(np.uint32).tobytes() == ov.tobytes()
+
+
+def test_sort_keys_in_captured_graph(gpu_lib):
+    """sr_sort_keys captured in the caller's CUDA graph (ordinary launches,
+    scratch from graph allocation nodes) and replayed on new inputs."""
+    import torch
+    arrays = [si.int32_input(kind, 500_003, seed=13) for kind in si.INT32_CLASSES]
+    x = torch.from_numpy(arrays[0]).cuda()
+    gpu_lib.sort_keys(x.clone(), key_type=0)        # device state exists before the capture
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        gpu_lib.sort_keys(x, key_type=0, stream=s)
+    for a in arrays:
+        x.copy_(torch.from_numpy(a).cuda())
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        assert x.cpu().numpy().tobytes() == oracle.sort_keys(a).tobytes()
