@@ -73,18 +73,26 @@ typedef void *sr_stream;     /* a cudaStream_t */
  * reversed in one pass: the adaptivity the paper credits for its mergesort
  * and quicksort wins (Section 4, the remark that with techniques (e) and (f)
  * quicksort takes O(n) on sorted and reversely sorted lists; Section 3,
- * technique (a)).  Cites: Section 1 (the race's operation), Section 5 (qsort
- * interface), Section 2 (sortedness).
+ * technique (a)).  Inputs with few keys out of place (k-exchange lists,
+ * Section 2) take the few-displaced-keys path: the keys left in order stay in
+ * order and only the others are sorted on the side.  Cites: Section 1 (the
+ * race's operation), Section 5 (qsort interface), Section 2 (sortedness).
+ * Asynchronous on `stream`.  A call repeated with the same arguments (key type,
+ * n, buffer) on any stream replays a CUDA graph the library builds on the
+ * second such call; the graph and its scratch stay with the library (at most
+ * 16 argument sets per process, least recently used dropped).  Calls inside a
+ * stream capture launch their kernels into the capture instead.
  */
 sr_status sr_sort_keys(void *d_keys, size_t n, sr_key_type kt, sr_stream stream);
 
 /*
  * sr_sort_pairs -- stable sort of (d_keys[i], d_vals[i]) by key, in place.
  *   d_keys  n keys of type kt;  d_vals  n uint32 payloads moved with their keys.
- * Equal keys keep their input order: the mergesort's stability (Section 6:
- * "mergesort is stable"; Section 3, technique (a), the stable treatment of
- * equal items in reversed runs).  With payload = original index the output
- * is unique.
+ * Equal keys keep their input order: the mergesort's stability (Section 6,
+ * where stability is what decides for mergesort; Section 3, technique (a),
+ * the stable treatment of equal items in reversed runs).  With payload =
+ * original index the output is unique.  Repeated calls replay a graph as for
+ * sr_sort_keys.
  */
 sr_status sr_sort_pairs(void *d_keys, uint32_t *d_vals, size_t n, sr_key_type kt,
                         sr_stream stream);
