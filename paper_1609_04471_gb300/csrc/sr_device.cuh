@@ -101,10 +101,13 @@ template <int KB, bool VALS> struct Shape;
 #ifndef SR_MERGE_NT
 #define SR_MERGE_NT 256
 #endif
-template <> struct Shape<4, false> { enum { NT = SR_MERGE_NT, IPT = SR_K4_IPT, SORT_NT = SR_SORT_NT }; };
-template <> struct Shape<4, true>  { enum { NT = SR_MERGE_NT, IPT = SR_K4V_IPT, SORT_NT = SR_SORT_NT }; };
-template <> struct Shape<8, false> { enum { NT = SR_MERGE_NT, IPT = SR_K8_IPT, SORT_NT = SR_SORT_NT }; };
-template <> struct Shape<8, true>  { enum { NT = SR_MERGE_NT, IPT = SR_K8V_IPT, SORT_NT = SR_SORT_NT }; };
+// MERGE_MINB: resident merge CTAs per SM the register allocator is held to
+// (4-byte keys: 40 registers, six CTAs -- measured 9.14 -> 9.00 ms at 2^28;
+// the others keep the occupancy they reach unconstrained).
+template <> struct Shape<4, false> { enum { NT = SR_MERGE_NT, IPT = SR_K4_IPT, SORT_NT = SR_SORT_NT, MERGE_MINB = 6 }; };
+template <> struct Shape<4, true>  { enum { NT = SR_MERGE_NT, IPT = SR_K4V_IPT, SORT_NT = SR_SORT_NT, MERGE_MINB = 8 }; };
+template <> struct Shape<8, false> { enum { NT = SR_MERGE_NT, IPT = SR_K8_IPT, SORT_NT = SR_SORT_NT, MERGE_MINB = 4 }; };
+template <> struct Shape<8, true>  { enum { NT = SR_MERGE_NT, IPT = SR_K8V_IPT, SORT_NT = SR_SORT_NT, MERGE_MINB = 4 }; };
 
 // ------------------------------------------------------------- merge path
 

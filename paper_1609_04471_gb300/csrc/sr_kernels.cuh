@@ -808,7 +808,7 @@ __device__ __forceinline__ void merge_tile(const typename Key<KT>::T *__restrict
 // ranges come from the split table and are merged by merge_tile.  A run pair
 // (2w keys) spans 2^lgt whole tiles.
 template <int KT, int NT, int IPT, bool VALS, bool VEC>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, Shape<sizeof(typename Key<KT>::T), VALS>::MERGE_MINB)
 k_merge(typename Key<KT>::T *uk, uint32_t *uv, typename Key<KT>::T *sk, uint32_t *svb, long long n,
         long long w, int lgt, const long long *__restrict__ splits, const Ctrl *__restrict__ c, int p,
         typename Key<KT>::U *__restrict__ samp, long long smt) {

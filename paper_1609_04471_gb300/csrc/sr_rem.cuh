@@ -399,8 +399,16 @@ k_rem_bsort(typename Key<KT>::T *__restrict__ buck, long long tiles, Ctrl *__res
 // src indexes the scratch buffer that holds the candidate slots (tile b at
 // b*ts) followed, at index dofs, by the buckets (bucket b at dofs +
 // b*REM_CAP); n_src bounds it.
+#ifndef SR_REM_MERGE_MINB
+#define SR_REM_MERGE_MINB 4     // 64 registers: four CTAs per SM
+#endif
+#if SR_REM_MERGE_MINB
+#define SR_REM_MERGE_BOUNDS __launch_bounds__(NT, SR_REM_MERGE_MINB)
+#else
+#define SR_REM_MERGE_BOUNDS __launch_bounds__(NT)
+#endif
 template <int KT, int NT, int MIPT, bool VEC>
-__global__ void __launch_bounds__(NT)
+__global__ void SR_REM_MERGE_BOUNDS
 k_rem_merge(typename Key<KT>::T *__restrict__ out, const typename Key<KT>::T *__restrict__ src, long long n_src,
             long long dofs, int ts, long long tiles, const Ctrl *__restrict__ c,
             const unsigned int *__restrict__ s_count, const unsigned int *__restrict__ b_count,
