@@ -103,28 +103,34 @@ template <int KT, bool VALS> struct PlainSort {
     // distinct keys, few displaced keys): after them the call's mode is
     // final, and launch_sort's kernels all return at once unless it is
     // MODE_SORT.
+    // Parts of the prefix, for a caller that routes between them on the device.
+    enum { PART_SCAN = 1, PART_REVERSE = 2, PART_FEW = 4, PART_REM = 8, PART_ALL = 15 };
     sr_status launch_prefix(T *uk, uint32_t *uv, unsigned char *scratch, cudaStream_t s,
-                            const int *gate = nullptr) const {
+                            const int *gate = nullptr, int parts = PART_ALL) const {
         Ctrl *ctrl = (Ctrl *)(scratch + off_ctrl);
         T *sk = (T *)(scratch + off_keys);
         const bool vec = ((uintptr_t)uk % 16) == 0 && (!VALS || ((uintptr_t)uv % 16) == 0);
         sr_status st = SR_OK;
         do {
-            if (cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s) != cudaSuccess) { st = launch_status(); break; }
             U *rem_bound = rem ? (U *)(scratch + off_rem_bound) : nullptr;   // the scan records its medians
-            SR_LAUNCH(SR_KERNEL_DETECT, (k_detect<KT, SNT, IPT>), (unsigned)tiles, SNT, 0, s,
-                      uk, n, ctrl, gate, rem_bound, (int)RT);
             constexpr bool FEW = sizeof(T) == 4 && !VALS && SR_FEW_KEYS;   // few distinct keys: written as runs
-            if constexpr (FEW)
-                SR_LAUNCH(SR_KERNEL_DETECT, k_few_sample<KT>, FEW_SAMPLE / FEW_NT, FEW_NT, 0, s, uk, n, ctrl, gate);
-            SR_LAUNCH(SR_KERNEL_REVERSE, (k_reverse<KT, VALS>), grid_for(n / 2, 256, 152 * 16), 256, 0, s,
-                      uk, uv, n, ctrl);
-            if constexpr (FEW) {
+            if (parts & PART_SCAN) {
+                if (cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s) != cudaSuccess) { st = launch_status(); break; }
+                SR_LAUNCH(SR_KERNEL_DETECT, (k_detect<KT, SNT, IPT>), (unsigned)tiles, SNT, 0, s,
+                          uk, n, ctrl, gate, rem_bound, (int)RT);
+                if constexpr (FEW)
+                    SR_LAUNCH(SR_KERNEL_DETECT, k_few_sample<KT>, FEW_SAMPLE / FEW_NT, FEW_NT, 0, s, uk, n, ctrl,
+                              gate);
+            }
+            if (parts & PART_REVERSE)
+                SR_LAUNCH(SR_KERNEL_REVERSE, (k_reverse<KT, VALS>), grid_for(n / 2, 256, 152 * 16), 256, 0, s,
+                          uk, uv, n, ctrl);
+            if constexpr (FEW) if (parts & PART_FEW) {
                 SR_LAUNCH(SR_KERNEL_COPY, k_few_count<KT>, grid_for(n, 256, 152 * 8), 256, 0, s, uk, n, ctrl);
                 SR_LAUNCH(SR_KERNEL_COPY, k_few_write<KT>, grid_for(n / 4 + 1, 256, 152 * 8), 256, 0, s, uk, n,
                           ctrl);
             }
-            if constexpr (!VALS) if (rem) {
+            if constexpr (!VALS) if (rem && (parts & PART_REM)) {
                 U *bound = rem_bound;
                 unsigned int *scount = (unsigned int *)(scratch + off_rem_scount);
                 unsigned int *bcount = (unsigned int *)(scratch + off_rem_bcount);

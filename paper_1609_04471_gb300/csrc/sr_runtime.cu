@@ -161,9 +161,10 @@ extern "C" const char *sr_status_string(sr_status s) {
 namespace sr {
 bool profiling_on() { return g_prof_on; }
 void count_launches(long long k) { g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
+unsigned long long host_launch_count() { return g_launches.load(); }
 }  // namespace sr
 
-extern "C" uint64_t sr_launch_count(void) { return g_launches.load(); }
+extern "C" uint64_t sr_launch_count(void) { return g_launches.load() + sr::graph_kernel_count(); }
 
 extern "C" sr_status sr_profile_begin(void) {
     for (auto &t : g_prof) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }

@@ -71,6 +71,10 @@ CallRecord &call_record();
 // an adjustment of the launch count (graph replays count their kernels).
 bool profiling_on();
 void count_launches(long long k);
+unsigned long long host_launch_count();     // the launches counted on the host
+// Kernels that graph replays ran beyond those counted on the host (read on
+// the device after it finishes its queued work; 0 if no graph ran).
+unsigned long long graph_kernel_count();
 
 // Kernel instrumentation: every launch site calls launch_begin / launch_end
 // around its <<<>>> (see SR_LAUNCH).

@@ -20,19 +20,50 @@ namespace sr {
 // ------------------------------------------------- repeated calls as graphs
 //
 // A call repeated with the same arguments (key type, payloads, n, buffers)
-// replays a CUDA graph of its launch sequence: the scan and the whole-input
-// paths, a one-thread kernel that reads the call's mode, and a conditional
-// node whose body -- the block sort, planner, merge passes and copy-back --
-// runs only when the mode is MODE_SORT.  Inputs that a whole-input path
-// finishes (sorted, strictly descending, few distinct or few displaced keys)
-// then skip the ~2 launches per merge pass whose kernels would return at once.
-// The graph owns its scratch.  Not used inside a stream capture, while
-// profiling, or with SORTRACE_GRAPHS=0; the first call with new arguments
-// takes the ordinary launches.
+// replays a CUDA graph of its launch sequence.  After the scan, a one-thread
+// kernel reads the call's state and picks one branch of a switch node:
+//   0 sorted input: nothing more;
+//   1 strictly descending: the reversal;
+//   2 a few-distinct-keys candidate: count and write (then the few-displaced-
+//     keys path and the sort section behind an IF node, for a candidate the
+//     count rejects);
+//   3 few displaced keys: that path, then the sort section behind an IF node
+//     (for a bucket overflow);
+//   4 the sort section.
+// Inputs a whole-input path finishes so skip every launch of the other
+// paths and the ~2 launches per merge pass.  The graph owns its scratch.  Not
+// used inside a stream capture, while profiling, or with SORTRACE_GRAPHS=0;
+// the first call with new arguments takes the ordinary launches.  The
+// deciding kernels add the kernels of the branch they pick to a device
+// counter that sr_launch_count reads.
 
-__global__ void k_sort_cond(cudaGraphConditionalHandle h, const Ctrl *__restrict__ c, long long n) {
+__device__ unsigned long long g_branch_kernels;
+
+struct BranchKernels {
+    unsigned int reverse, few_rem, rem, sort;
+};
+
+__global__ void k_route(cudaGraphConditionalHandle h, const Ctrl *__restrict__ c, long long n, long long rtiles,
+                        long long dmax, int rem, BranchKernels k) {
     griddep_wait();
-    cudaGraphSetConditional(h, call_mode(c, n) == MODE_SORT ? 1u : 0u);
+    unsigned int v, cnt;
+    if (c->descents == 0) { v = 0; cnt = 0; }
+    else if (c->nondescents == 0 && n > 1) { v = 1; cnt = k.reverse; }
+    else if (c->few_cand) { v = 2; cnt = k.few_rem; }
+    else if (rem && 2 * c->descents >= (unsigned long long)rtiles && c->descents <= (unsigned long long)dmax) {
+        v = 3;
+        cnt = k.rem;
+    } else { v = 4; cnt = k.sort; }
+    cudaGraphSetConditional(h, v);
+    if (cnt) atomicAdd(&g_branch_kernels, (unsigned long long)cnt);
+}
+
+__global__ void k_sort_cond(cudaGraphConditionalHandle h, const Ctrl *__restrict__ c, long long n,
+                            unsigned int sort_kernels) {
+    griddep_wait();
+    const bool go = call_mode(c, n) == MODE_SORT;
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+    if (go) atomicAdd(&g_branch_kernels, (unsigned long long)sort_kernels);
 }
 
 namespace {
@@ -46,15 +77,17 @@ struct GraphEntry {
     unsigned long long used = 0;     // recency tick
     void *scratch = nullptr;         // owned by the graph
     cudaGraphExec_t exec = nullptr;
-    long long kernels = 0;           // kernel nodes of the graph (the launch count per replay)
+    long long kernels = 0;           // kernels every replay runs (the rest is counted on the device)
     cudaStream_t last = nullptr;     // stream of the last replay
 };
 constexpr int kGraphSlots = 16;
 constexpr size_t kGraphMinKeys = 1u << 16;
+constexpr int kMaxDev = 64;
 std::mutex g_gmu;
 GraphEntry g_graph[kGraphSlots];
 unsigned long long g_tick = 0;
-cudaStream_t g_cap_stream[2][64];    // per device: the two capture streams
+cudaStream_t g_cap_stream[3][kMaxDev];   // per device: capture streams (top, branch, nested)
+bool g_graph_used[kMaxDev];
 
 bool graphs_enabled() {
     static const bool on = [] {
@@ -63,65 +96,158 @@ bool graphs_enabled() {
     }();
     return on;
 }
+
+// Adds a conditional node of `type` with `size` bodies after the current
+// capture dependencies of s, and makes it the capture's only dependency.
+sr_status add_conditional(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                          unsigned size, cudaGraph_t *bodies) {
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *edata = nullptr;
+    size_t ndeps = 0;
+    if (cudaStreamGetCaptureInfo(s, &cst, nullptr, &g, &deps, &edata, &ndeps) != cudaSuccess) return launch_status();
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = type;
+    cp.conditional.size = size;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, g, deps, edata, ndeps, &cp) != cudaSuccess) return launch_status();
+    for (unsigned i = 0; i < size; ++i) bodies[i] = cp.conditional.phGraph_out[i];
+    if (cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess)
+        return launch_status();
+    return SR_OK;
+}
+
+// A handle for a conditional node in the graph that s is capturing into.
+sr_status new_handle(cudaStream_t s, cudaGraphConditionalHandle *h) {
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamGetCaptureInfo(s, &cst, nullptr, &g) != cudaSuccess) return launch_status();
+    if (cudaGraphConditionalHandleCreate(h, g, 0, 0) != cudaSuccess) return launch_status();
+    return SR_OK;
+}
 }  // namespace
 
-// Builds the conditional graph of `plan` over `scratch` (capture on private
-// streams; nothing runs).
+// Captures `fn(stream)` into `body` on stream `cb`; *kernels = the kernels it
+// launched.
+template <typename F>
+static sr_status capture_into(cudaGraph_t body, cudaStream_t cb, F fn, unsigned int *kernels) {
+    const unsigned long long l0 = host_launch_count();
+    if (cudaStreamBeginCaptureToGraph(cb, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+        return launch_status();
+    sr_status st = fn(cb);
+    cudaGraph_t out = nullptr;
+    if (cudaStreamEndCapture(cb, &out) != cudaSuccess && st == SR_OK) st = launch_status();
+    *kernels = (unsigned int)(host_launch_count() - l0);
+    return st;
+}
+
+// The kernels fn would launch (captured into a scratch graph and dropped).
+template <typename F>
+static sr_status count_kernels(cudaStream_t cb, F fn, unsigned int *kernels) {
+    cudaGraph_t g = nullptr;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return launch_status();
+    const sr_status st = capture_into(g, cb, fn, kernels);
+    cudaGraphDestroy(g);
+    return st;
+}
+
+// Builds the routed graph of `plan` over `scratch` (capture on private
+// streams; nothing runs).  *kernels: the kernels every replay runs (the scan
+// and the router; the rest is counted on the device).
 template <typename PS>
 static sr_status build_graph(const PS &plan, typename PS::T *uk, uint32_t *uv, unsigned char *scratch, int dev,
                              cudaGraphExec_t *exec, long long *kernels) {
-    cudaStream_t *cs = &g_cap_stream[0][dev], *cb = &g_cap_stream[1][dev];
-    if (!*cs && cudaStreamCreateWithFlags(cs, cudaStreamNonBlocking) != cudaSuccess) return launch_status();
-    if (!*cb && cudaStreamCreateWithFlags(cb, cudaStreamNonBlocking) != cudaSuccess) return launch_status();
-    const unsigned long long l0 = sr_launch_count();
-    cudaGraph_t g = nullptr;
-    sr_status st = SR_OK;
-    if (cudaStreamBeginCapture(*cs, cudaStreamCaptureModeRelaxed) != cudaSuccess) return launch_status();
+    cudaStream_t cs[3];
+    for (int i = 0; i < 3; ++i) {
+        if (!g_cap_stream[i][dev] &&
+            cudaStreamCreateWithFlags(&g_cap_stream[i][dev], cudaStreamNonBlocking) != cudaSuccess)
+            return launch_status();
+        cs[i] = g_cap_stream[i][dev];
+    }
+    const Ctrl *ctrl = (const Ctrl *)(scratch + plan.off_ctrl);
+    const long long n = plan.n;
+    const unsigned long long l_start = host_launch_count();
+    auto part = [&](int parts) { return [&, parts](cudaStream_t x) {
+        return plan.launch_prefix(uk, uv, scratch, x, nullptr, parts); }; };
+    auto sort = [&](cudaStream_t x) { return plan.launch_sort(uk, uv, scratch, x); };
+    // kernels per part, for the device-side count
+    unsigned int k_scan = 0, k_rev = 0, k_few = 0, k_rem = 0, k_sort = 0;
+    sr_status st = count_kernels(cs[1], part(PS::PART_SCAN), &k_scan);
+    if (st == SR_OK) st = count_kernels(cs[1], part(PS::PART_REVERSE), &k_rev);
+    if (st == SR_OK) st = count_kernels(cs[1], part(PS::PART_FEW), &k_few);
+    if (st == SR_OK) st = count_kernels(cs[1], part(PS::PART_REM), &k_rem);
+    if (st == SR_OK) st = count_kernels(cs[1], sort, &k_sort);
+    // a branch body: `parts` of the prefix, then the sort section behind an
+    // IF node that a one-thread kernel sets from the call's mode
+    auto guarded = [&](int parts) { return [&, parts](cudaStream_t x) -> sr_status {
+        sr_status s2 = plan.launch_prefix(uk, uv, scratch, x, nullptr, parts);
+        cudaGraphConditionalHandle hi;
+        if (s2 == SR_OK) s2 = new_handle(x, &hi);
+        if (s2 != SR_OK) return s2;
+        do {
+            sr_status &st = s2;     // SR_LAUNCH reports into `st`
+            SR_LAUNCH(SR_KERNEL_PARTITION, k_sort_cond, 1, 32, 0, x, hi, ctrl, n, k_sort);
+        } while (0);
+        cudaGraph_t ifb[1];
+        if (s2 == SR_OK) s2 = add_conditional(x, hi, cudaGraphCondTypeIf, 1, ifb);
+        unsigned int k = 0;
+        if (s2 == SR_OK) s2 = capture_into(ifb[0], cs[2], sort, &k);
+        return s2;
+    }; };
+    if (st != SR_OK) return st;
+    if (cudaStreamBeginCapture(cs[0], cudaStreamCaptureModeRelaxed) != cudaSuccess) return launch_status();
     do {
-        cudaStreamCaptureStatus cst;
-        if (cudaStreamGetCaptureInfo(*cs, &cst, nullptr, &g) != cudaSuccess) { st = launch_status(); break; }
-        cudaGraphConditionalHandle h;
-        if (cudaGraphConditionalHandleCreate(&h, g, 0, 0) != cudaSuccess) { st = launch_status(); break; }
-        if ((st = plan.launch_prefix(uk, uv, scratch, *cs)) != SR_OK) break;
-        SR_LAUNCH(SR_KERNEL_PARTITION, k_sort_cond, 1, 32, 0, *cs, h, (const Ctrl *)(scratch + plan.off_ctrl),
-                  (long long)plan.n);
-        const cudaGraphNode_t *deps = nullptr;
-        const cudaGraphEdgeData *edata = nullptr;
-        size_t ndeps = 0;
-        if (cudaStreamGetCaptureInfo(*cs, &cst, nullptr, &g, &deps, &edata, &ndeps) != cudaSuccess) {
+        if ((st = plan.launch_prefix(uk, uv, scratch, cs[0], nullptr, PS::PART_SCAN)) != SR_OK) break;
+        cudaGraphConditionalHandle hs;
+        if ((st = new_handle(cs[0], &hs)) != SR_OK) break;
+        const BranchKernels bk = {k_rev, k_few + k_rem + 1, k_rem + 1, k_sort};
+        SR_LAUNCH(SR_KERNEL_PARTITION, k_route, 1, 32, 0, cs[0], hs, ctrl, n, plan.rtiles, plan.rem_dmax,
+                  plan.rem ? 1 : 0, bk);
+        cudaGraph_t br[5];
+        if ((st = add_conditional(cs[0], hs, cudaGraphCondTypeSwitch, 5, br)) != SR_OK) break;
+        cudaGraphNode_t empty;
+        if (cudaGraphAddEmptyNode(&empty, br[0], nullptr, 0) != cudaSuccess) { st = launch_status(); break; }
+        unsigned int k = 0;
+        if ((st = capture_into(br[1], cs[1], part(PS::PART_REVERSE), &k)) != SR_OK) break;
+        if ((st = capture_into(br[2], cs[1], guarded(PS::PART_FEW | PS::PART_REM), &k)) != SR_OK) break;
+        if (plan.rem) {
+            if ((st = capture_into(br[3], cs[1], guarded(PS::PART_REM), &k)) != SR_OK) break;
+        } else if (cudaGraphAddEmptyNode(&empty, br[3], nullptr, 0) != cudaSuccess) {
             st = launch_status();
             break;
         }
-        cudaGraphNodeParams cp = {};
-        cp.type = cudaGraphNodeTypeConditional;
-        cp.conditional.handle = h;
-        cp.conditional.type = cudaGraphCondTypeIf;
-        cp.conditional.size = 1;
-        cudaGraphNode_t cnode;
-        if (cudaGraphAddNode(&cnode, g, deps, edata, ndeps, &cp) != cudaSuccess) { st = launch_status(); break; }
-        if (cudaStreamBeginCaptureToGraph(*cb, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                          cudaStreamCaptureModeRelaxed) != cudaSuccess) {
-            st = launch_status();
-            break;
-        }
-        st = plan.launch_sort(uk, uv, scratch, *cb);
-        cudaGraph_t body = nullptr;
-        if (cudaStreamEndCapture(*cb, &body) != cudaSuccess && st == SR_OK) st = launch_status();
-        if (st != SR_OK) break;
-        if (cudaStreamUpdateCaptureDependencies(*cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies) !=
-            cudaSuccess) {
-            st = launch_status();
-            break;
-        }
+        if ((st = capture_into(br[4], cs[1], sort, &k)) != SR_OK) break;
     } while (0);
     cudaGraph_t done = nullptr;
-    if (cudaStreamEndCapture(*cs, &done) != cudaSuccess && st == SR_OK) st = launch_status();
+    if (cudaStreamEndCapture(cs[0], &done) != cudaSuccess && st == SR_OK) st = launch_status();
     if (st == SR_OK && cudaGraphInstantiate(exec, done, 0) != cudaSuccess) st = launch_status();
     if (done) cudaGraphDestroy(done);
     cudaGetLastError();
-    *kernels = (long long)(sr_launch_count() - l0);
-    count_launches(-*kernels);                   // captured, not launched
+    count_launches(-(long long)(host_launch_count() - l_start));   // captured, not launched
+    *kernels = (long long)k_scan + 1;                                // the scan kernels and the router
     return st;
+}
+
+unsigned long long graph_kernel_count() {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+        cudaGetLastError();
+        return 0;
+    }
+    {
+        std::lock_guard<std::mutex> lock(g_gmu);
+        if (!g_graph_used[dev]) return 0;
+    }
+    unsigned long long v = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpyFromSymbol(&v, g_branch_kernels, sizeof(v)) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return v;
 }
 
 // Replays (or builds, on the second identical call) the graph of this call.
@@ -180,6 +306,7 @@ static sr_status graph_call(const PlainSort<KT, VALS> &plan, int kt, void *d_key
     }
     if (cudaGraphLaunch(e->exec, s) != cudaSuccess) return launch_status();
     e->last = s;
+    g_graph_used[ds->device] = true;
     count_launches(e->kernels);
     if (cudaMemcpyAsync(ds->last_ctrl, (unsigned char *)e->scratch + plan.off_ctrl, sizeof(Ctrl),
                         cudaMemcpyDeviceToDevice, s) != cudaSuccess)
