@@ -307,7 +307,9 @@ const char *sr_status_string(sr_status s);
 /* ---------------------------------------------------------------------------
  * Instrumentation.  Every kernel the library launches belongs to one of these
  * kinds.  sr_launch_count() is the number of kernels the library has launched
- * in this process.  Between sr_profile_begin() and sr_profile_end() the calls
+ * in this process (graph replays included: once a replay has run on the
+ * current device, the call waits for that device's queued work to read the
+ * kernels the replays' branches ran).  Between sr_profile_begin() and sr_profile_end() the calls
  * made by this host thread bracket each launch with CUDA events on the
  * launch's own stream; sr_profile_end() waits for them and returns, per kind,
  * the launch count and the summed device time (ms).  Profiling cannot be
