@@ -46,6 +46,7 @@ struct BranchKernels {
 __global__ void k_route(cudaGraphConditionalHandle h, const Ctrl *__restrict__ c, long long n, long long rtiles,
                         long long dmax, int rem, BranchKernels k) {
     griddep_wait();
+    if (threadIdx.x != 0) return;                 // one setter of the condition
     unsigned int v, cnt;
     if (c->descents == 0) { v = 0; cnt = 0; }
     else if (c->nondescents == 0 && n > 1) { v = 1; cnt = k.reverse; }
@@ -61,6 +62,7 @@ __global__ void k_route(cudaGraphConditionalHandle h, const Ctrl *__restrict__ c
 __global__ void k_sort_cond(cudaGraphConditionalHandle h, const Ctrl *__restrict__ c, long long n,
                             unsigned int sort_kernels) {
     griddep_wait();
+    if (threadIdx.x != 0) return;                 // one setter of the condition
     const bool go = call_mode(c, n) == MODE_SORT;
     cudaGraphSetConditional(h, go ? 1u : 0u);
     if (go) atomicAdd(&g_branch_kernels, (unsigned long long)sort_kernels);
