@@ -197,6 +197,19 @@ sr_status sr_sort_keys_host(void *h_keys, size_t n, sr_key_type kt, sr_stream st
 sr_status sr_sort_keys_host_async(void *h_keys, size_t n, sr_key_type kt, sr_stream stream);
 
 /*
+ * sr_sort_keys_host_many -- sorts `count` host arrays h_keys[i][0..n[i]) of key
+ * type kt in place, as a pipeline: array i+1 is copied in while earlier ones
+ * are sorted and copied out (the library's streams: one for the copies in, in
+ * array order, and two lanes of sort + copy out that take the arrays in turn).  Queued after the caller's earlier work on `stream`; the caller's
+ * later work on `stream` waits for all of it; the call returns at once.
+ * Every array with n[i] > 1 must be page-locked host memory (else
+ * SR_ERR_INVALID_ARG before anything is queued) and left alone until the
+ * stream completes.  Same result per array as sr_sort_keys.
+ */
+sr_status sr_sort_keys_host_many(void *const *h_keys, const size_t *n, int count, sr_key_type kt,
+                                 sr_stream stream);
+
+/*
  * sr_sort_keys_noalloc -- sr_sort_keys for callers that must not allocate device
  * memory while they sort (a service that reserves all of its memory up front
  * so it can never hit out-of-memory mid-request, a framework that forbids

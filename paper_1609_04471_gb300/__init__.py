@@ -73,6 +73,7 @@ SIGNATURES = {
     "sr_segmented_config_info": (_i32, [_i32, _i32, _vp]),
     "sr_sort_keys_host": (_i32, [_vp, _sz, _i32, _vp]),
     "sr_sort_keys_host_async": (_i32, [_vp, _sz, _i32, _vp]),
+    "sr_sort_keys_host_many": (_i32, [_vp, _vp, _i32, _i32, _vp]),
     "sr_sort_keys_noalloc": (_i32, [_vp, _sz, _i32, _vp]),
     "sr_sort_keys_learned": (_i32, [_vp, _sz, _i32, _vp, _vp]),
     "sr_detect_runs": (_i32, [_vp, _sz, _i32, _vp, _vp]),
@@ -289,6 +290,21 @@ def sort_keys_host_async(arr, key_type: int | None = None, stream=None):
     ptr, n, kt = _host_args(arr, key_type)
     _check(load().sr_sort_keys_host_async(ptr, n, kt, _stream(stream)), "sr_sort_keys_host_async")
     return arr
+
+
+def sort_keys_host_many(arrs, key_type: int | None = None, stream=None):
+    """Sorts several page-locked host arrays in place as a pipeline (copy in,
+    sort, copy out overlap across arrays), queued on the stream without
+    waiting; the arrays must be left alone until the stream completes."""
+    args = [_host_args(a, key_type) for a in arrs]
+    kts = {kt for _, _, kt in args}
+    if len(kts) > 1:
+        raise ValueError("all arrays must have one key type")
+    ptrs = (ctypes.c_void_p * len(args))(*[p for p, _, _ in args])
+    ns = (ctypes.c_size_t * len(args))(*[n for _, n, _ in args])
+    kt = kts.pop() if kts else (key_type if key_type is not None else KEY_I32)
+    _check(load().sr_sort_keys_host_many(ptrs, ns, len(args), kt, _stream(stream)), "sr_sort_keys_host_many")
+    return arrs
 
 
 def detect_runs(x, key_type: int | None = None, stream=None) -> dict:

@@ -473,6 +473,78 @@ extern "C" sr_status sr_sort_keys_host_async(void *h_keys, size_t n, sr_key_type
     return host_sort_enqueue(h_keys, n, kt, (cudaStream_t)stream);
 }
 
+// Per-device streams for sr_sort_keys_host_many: one for the copies in, and
+// two lanes of (sort, copy out) that take the arrays in turn, so a short sort
+// and its copy out need not wait behind a long one.
+static cudaStream_t g_pipe[5][64];
+
+extern "C" sr_status sr_sort_keys_host_many(void *const *h_keys, const size_t *n, int count, sr_key_type kt,
+                                            sr_stream stream) {
+    if (!valid_key_type(kt) || count < 0 || (count > 0 && (!h_keys || !n))) return SR_ERR_INVALID_ARG;
+    for (int i = 0; i < count; ++i) {
+        if (n[i] < 2) continue;
+        cudaPointerAttributes pa;
+        if (!h_keys[i] || cudaPointerGetAttributes(&pa, h_keys[i]) != cudaSuccess ||
+            pa.type != cudaMemoryTypeHost) {
+            cudaGetLastError();
+            return SR_ERR_INVALID_ARG;             // every array page-locked
+        }
+    }
+    DeviceState *ds = nullptr;
+    SR_TRY(device_state(&ds));
+    const int dev = ds->device;
+    if (dev < 0 || dev >= 64) return SR_ERR_UNSUPPORTED;
+    for (int k = 0; k < 5; ++k)
+        if (!g_pipe[k][dev] && cudaStreamCreateWithFlags(&g_pipe[k][dev], cudaStreamNonBlocking) != cudaSuccess)
+            return launch_status();
+    cudaStream_t cin = g_pipe[0][dev];
+    cudaStream_t comp[2] = {g_pipe[1][dev], g_pipe[2][dev]}, cout[2] = {g_pipe[3][dev], g_pipe[4][dev]};
+    const cudaStream_t s = (cudaStream_t)stream;
+    auto link = [&](cudaStream_t from, cudaStream_t to) -> sr_status {   // `to` waits for `from`'s work so far
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return launch_status();
+        const bool ok = cudaEventRecord(e, from) == cudaSuccess && cudaStreamWaitEvent(to, e, 0) == cudaSuccess;
+        cudaEventDestroy(e);
+        return ok ? SR_OK : launch_status();
+    };
+    // the pipeline starts after the caller's earlier work on `stream`
+    SR_TRY(link(s, cin));
+    for (int k = 0; k < 2; ++k) {
+        SR_TRY(link(s, comp[k]));
+        SR_TRY(link(s, cout[k]));
+    }
+    const size_t kb = key_bytes_of(kt);
+    sr_status st = SR_OK;
+    int lane = 0;
+    for (int i = 0; i < count && st == SR_OK; ++i) {
+        if (n[i] < 2) continue;
+        const size_t bytes = n[i] * kb;
+        cudaStream_t cs = comp[lane], co = cout[lane];
+        lane ^= 1;
+        void *d = nullptr;
+        if ((st = scratch_alloc(ds, &d, bytes, cin)) != SR_OK) break;
+        if (cudaMemcpyAsync(d, h_keys[i], bytes, cudaMemcpyHostToDevice, cin) != cudaSuccess) {
+            st = launch_status();
+            break;
+        }
+        if ((st = link(cin, cs)) != SR_OK) break;              // array i is on the device
+        if ((st = dispatch_sort<false>(d, nullptr, n[i], kt, cs, 1, false)) != SR_OK) break;
+        if ((st = link(cs, co)) != SR_OK) break;               // array i is sorted
+        if (cudaMemcpyAsync(h_keys[i], d, bytes, cudaMemcpyDeviceToHost, co) != cudaSuccess) {
+            st = launch_status();
+            break;
+        }
+        scratch_free(d, co);
+    }
+    // the caller's later work on `stream` waits for all of it
+    if (st == SR_OK) st = link(cin, s);
+    for (int k = 0; k < 2 && st == SR_OK; ++k) {
+        st = link(comp[k], s);
+        if (st == SR_OK) st = link(cout[k], s);
+    }
+    return st;
+}
+
 extern "C" sr_status sr_detect_runs(const void *d_keys, size_t n, sr_key_type kt, sr_run_info *out,
                                     sr_stream stream) {
     if (!valid_key_type(kt) || !out) return SR_ERR_INVALID_ARG;

@@ -243,6 +243,32 @@ def test_host_async_entry_point_on_several_streams(gpu_lib):
         gpu_lib.sort_keys_host_async(arrays[0].copy())
 
 
+def test_host_many_pipeline(gpu_lib):
+    """Several page-locked host arrays (every int32 class, ragged sizes, an
+    empty and a one-key array) sorted as one pipeline; 8-byte keys too;
+    pageable memory is refused before anything is queued."""
+    import torch
+    sizes = [(1 << 20) + 7, 0, 300_001, 1, (1 << 18) - 1, 2_000_003]
+    kinds = list(si.INT32_CLASSES)
+    arrays = [si.int32_input(kinds[i % len(kinds)], n, seed=30 + i) for i, n in enumerate(sizes)]
+    host = [torch.from_numpy(a.copy()).pin_memory() for a in arrays]
+    s = torch.cuda.Stream()
+    gpu_lib.sort_keys_host_many(host, stream=s)
+    s.synchronize()
+    for h, a in zip(host, arrays):
+        assert h.numpy().tobytes() == oracle.sort_keys(a).tobytes()
+    rng = np.random.default_rng(64)
+    arrays = [_random(rng, n, np.uint64) for n in (700_001, 5, 100_000)]
+    host = [torch.from_numpy(a.view(np.int64).copy()).pin_memory() for a in arrays]
+    gpu_lib.sort_keys_host_many(host, key_type=3, stream=s)
+    s.synchronize()
+    for h, a in zip(host, arrays):
+        assert h.numpy().view(np.uint64).tobytes() == oracle.sort_keys(a).tobytes()
+    with pytest.raises(gpu_lib.SortError):
+        gpu_lib.sort_keys_host_many([torch.zeros(10, dtype=torch.int64).pin_memory(), arrays[0].copy()],
+                                    key_type=3)
+
+
 def test_oom_injection(gpu_lib, monkeypatch):
     import torch
     a = _to_dev(si.uniform_i32(100_000, 1))
