@@ -21,6 +21,7 @@ struct Timed {
     cudaEvent_t a, b;
 };
 thread_local bool g_prof_on = false;
+thread_local unsigned long long g_thread_launches = 0;   // this thread's launches (captures count with it)
 thread_local std::vector<Timed> g_prof;
 thread_local cudaEvent_t g_prof_pending = nullptr;
 }  // namespace
@@ -41,6 +42,7 @@ void launch_begin(int kind, cudaStream_t s) {
 sr_status launch_end(int kind, cudaStream_t s) {
     sr_status st = launch_status();
     g_launches.fetch_add(1, std::memory_order_relaxed);
+    ++g_thread_launches;
     if (g_prof_on && g_prof_pending) {
         cudaEvent_t b = nullptr;
         if (cudaEventCreate(&b) == cudaSuccess && cudaEventRecord(b, s) == cudaSuccess) {
@@ -162,6 +164,7 @@ namespace sr {
 bool profiling_on() { return g_prof_on; }
 void count_launches(long long k) { g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
 unsigned long long host_launch_count() { return g_launches.load(); }
+unsigned long long thread_launch_count() { return g_thread_launches; }
 }  // namespace sr
 
 extern "C" uint64_t sr_launch_count(void) { return g_launches.load() + sr::graph_kernel_count(); }

@@ -72,6 +72,7 @@ CallRecord &call_record();
 bool profiling_on();
 void count_launches(long long k);
 unsigned long long host_launch_count();     // the launches counted on the host
+unsigned long long thread_launch_count();   // ... by this host thread
 // Kernels that graph replays ran beyond those counted on the host (read on
 // the device after it finishes its queued work; 0 if no graph ran).
 unsigned long long graph_kernel_count();

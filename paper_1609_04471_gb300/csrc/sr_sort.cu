@@ -80,7 +80,7 @@ struct GraphEntry {
     void *scratch = nullptr;         // owned by the graph
     cudaGraphExec_t exec = nullptr;
     long long kernels = 0;           // kernels every replay runs (the rest is counted on the device)
-    cudaStream_t last = nullptr;     // stream of the last replay
+    cudaEvent_t done = nullptr;      // recorded after every replay
 };
 constexpr int kGraphSlots = 16;
 constexpr size_t kGraphMinKeys = 1u << 16;
@@ -136,13 +136,13 @@ sr_status new_handle(cudaStream_t s, cudaGraphConditionalHandle *h) {
 // launched.
 template <typename F>
 static sr_status capture_into(cudaGraph_t body, cudaStream_t cb, F fn, unsigned int *kernels) {
-    const unsigned long long l0 = host_launch_count();
+    const unsigned long long l0 = thread_launch_count();
     if (cudaStreamBeginCaptureToGraph(cb, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess)
         return launch_status();
     sr_status st = fn(cb);
     cudaGraph_t out = nullptr;
     if (cudaStreamEndCapture(cb, &out) != cudaSuccess && st == SR_OK) st = launch_status();
-    *kernels = (unsigned int)(host_launch_count() - l0);
+    *kernels = (unsigned int)(thread_launch_count() - l0);
     return st;
 }
 
@@ -171,7 +171,7 @@ static sr_status build_graph(const PS &plan, typename PS::T *uk, uint32_t *uv, u
     }
     const Ctrl *ctrl = (const Ctrl *)(scratch + plan.off_ctrl);
     const long long n = plan.n;
-    const unsigned long long l_start = host_launch_count();
+    const unsigned long long l_start = thread_launch_count();
     auto part = [&](int parts) { return [&, parts](cudaStream_t x) {
         return plan.launch_prefix(uk, uv, scratch, x, nullptr, parts); }; };
     auto sort = [&](cudaStream_t x) { return plan.launch_sort(uk, uv, scratch, x); };
@@ -228,7 +228,7 @@ static sr_status build_graph(const PS &plan, typename PS::T *uk, uint32_t *uv, u
     if (st == SR_OK && cudaGraphInstantiate(exec, done, 0) != cudaSuccess) st = launch_status();
     if (done) cudaGraphDestroy(done);
     cudaGetLastError();
-    count_launches(-(long long)(host_launch_count() - l_start));   // captured, not launched
+    count_launches(-(long long)(thread_launch_count() - l_start));  // captured, not launched
     *kernels = (long long)k_scan + 1;                                // the scan kernels and the router
     return st;
 }
@@ -266,22 +266,27 @@ static sr_status graph_call(const PlainSort<KT, VALS> &plan, int kt, void *d_key
         return SR_OK;
     }
     std::lock_guard<std::mutex> lock(g_gmu);
-    GraphEntry *e = nullptr, *victim = &g_graph[0];
+    GraphEntry *e = nullptr, *victim = nullptr;
     for (auto &x : g_graph) {
         if (x.hits && x.dev == ds->device && x.kt == kt && x.vals == VALS && x.n == (size_t)plan.n &&
             x.keys == d_keys && x.pay == d_vals) {
             e = &x;
             break;
         }
-        if (!x.hits || x.used < victim->used) victim = &x;
+        // the slot to reuse: an empty one, else the least recent of this device
+        if (!x.hits) {
+            if (!victim || victim->hits) victim = &x;
+        } else if (x.dev == ds->device && (!victim || (victim->hits && x.used < victim->used))) {
+            victim = &x;
+        }
     }
     ++g_tick;
+    if (!e && !victim) return SR_OK;             // every slot holds another device's graph
     if (!e) {                                    // first sight: remember, launch ordinarily
-        if (victim->exec) {
-            if (victim->last) cudaStreamSynchronize(victim->last);
-            cudaGraphExecDestroy(victim->exec);
-        }
-        if (victim->scratch) scratch_free(victim->scratch, victim->last ? victim->last : s);
+        if (victim->done) cudaEventSynchronize(victim->done);     // its last replay has finished
+        if (victim->exec) cudaGraphExecDestroy(victim->exec);
+        if (victim->scratch) scratch_free(victim->scratch, s);
+        if (victim->done) cudaEventDestroy(victim->done);
         *victim = GraphEntry();
         victim->dev = ds->device; victim->kt = kt; victim->vals = VALS; victim->n = (size_t)plan.n;
         victim->keys = d_keys; victim->pay = d_vals; victim->hits = 1; victim->used = g_tick;
@@ -306,8 +311,10 @@ static sr_status graph_call(const PlainSort<KT, VALS> &plan, int kt, void *d_key
         e->scratch = scratch;
         e->kernels = kernels;
     }
-    if (cudaGraphLaunch(e->exec, s) != cudaSuccess) return launch_status();
-    e->last = s;
+    if (!e->done && cudaEventCreateWithFlags(&e->done, cudaEventDisableTiming) != cudaSuccess)
+        return launch_status();
+    if (cudaGraphLaunch(e->exec, s) != cudaSuccess || cudaEventRecord(e->done, s) != cudaSuccess)
+        return launch_status();
     g_graph_used[ds->device] = true;
     count_launches(e->kernels);
     if (cudaMemcpyAsync(ds->last_ctrl, (unsigned char *)e->scratch + plan.off_ctrl, sizeof(Ctrl),

@@ -504,3 +504,19 @@ def test_sort_keys_in_captured_graph(gpu_lib):
         g.replay()
         torch.cuda.synchronize()
         assert x.cpu().numpy().tobytes() == oracle.sort_keys(a).tobytes()
+
+
+def test_graph_cache_eviction(gpu_lib):
+    """More repeated-call argument sets than the library keeps graphs for: the
+    least recently used are dropped and rebuilt; every result exact."""
+    import torch
+    rng = np.random.default_rng(65)
+    arrays = [_random(rng, 70_000 + 13 * i, np.int32) for i in range(20)]
+    bufs = [torch.from_numpy(a).cuda() for a in arrays]
+    wants = [oracle.sort_keys(a).tobytes() for a in arrays]
+    for sweep in range(2):
+        for a, b, w in zip(arrays, bufs, wants):
+            for _ in range(3):                  # first sight, graph build, replay
+                b.copy_(torch.from_numpy(a).cuda())
+                gpu_lib.sort_keys(b, key_type=0)
+                assert b.cpu().numpy().tobytes() == w, sweep
