@@ -59,6 +59,8 @@ def _args():
                     help="with --profile-form batched: this launch configuration instead of tuning")
     ap.add_argument("--profile-pairs", action="store_true",
                     help="with --profile-case: a stable uint64-key + uint32-payload sort instead")
+    ap.add_argument("--classes", action="store_true",
+                    help="time the paper's parametrised input classes (Section 2) at 2^24 int32 and exit")
     ap.add_argument("--profile-class", default="uniform",
                     choices=["uniform", "reversed", "nearly_sorted", "few_unique"],
                     help="with --profile-case (key sort): the int32 input class")
@@ -487,6 +489,57 @@ def run_profile_case(args):
                       "passes_planned": st["passes_planned"], "passes_skipped": st["passes_skipped"], "ok": True}))
 
 
+def run_classes(args):
+    """The paper's input classes with a parameter k (Section 2) at 2^24 int32
+    keys: per class the sort time (median of 5 after 3 warm-ups, L2 flushed,
+    input restored untimed), the path the call took and the passes it skipped.
+    Every output is compared with numpy's sort of the same keys."""
+    import numpy as np
+    import torch
+    import paper_1609_04471_gb300 as sr
+    import sortrace_inputs as si
+    torch.cuda.set_device(0)
+    sr.load()
+    n = 1 << 24
+    classes = {
+        "random": lambda: si.uniform_i32(n, SEED),
+        "k-limited, k=12": lambda: si.k_limited(n, 12, SEED),
+        "k-equal teeth, k=8": lambda: si.k_equal_teeth(n, 8),
+        "k-even teeth, k=8": lambda: si.k_even_teeth(n, 8),
+        "k-sharp teeth, k=8": lambda: si.k_sharp_teeth(n, 8),
+        "k-shuffled teeth, k=8": lambda: si.k_shuffled_teeth(n, 8, SEED),
+        "k-distance, k=256": lambda: si.k_distance(n, 256, SEED),
+        "k-exchange, k=n/100": lambda: si.k_exchange(n, n // 100, SEED),
+    }
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    out = {}
+    for name, gen in classes.items():
+        a = gen()
+        src = torch.from_numpy(a).cuda()
+        x = torch.empty_like(src)
+        ts = []
+        for r in range(8):
+            x.copy_(src)
+            flush.fill_(r & 0xFF)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            sr.sort_keys(x)
+            e1.record()
+            torch.cuda.synchronize()
+            if r >= 3:
+                ts.append(e0.elapsed_time(e1))
+        ok = bool(np.array_equal(x.cpu().numpy(), np.sort(a)))
+        st = sr.stats()
+        ms = float(np.median(ts))
+        out[name] = {"ms": round(ms, 4), "gkeys_s": round(n / (ms / 1e3) / 1e9, 2), "ok": ok,
+                     "input_class": st["input_class"], "runs": st["runs"],
+                     "passes_planned": st["passes_planned"], "passes_skipped": st["passes_skipped"],
+                     "bytes_moved": st["bytes_moved"]}
+    print(json.dumps({"classes": out, "n": n, "key": "int32", "data": "synthetic (Section 2 generators)"}))
+
+
 def _timed(torch, stream, fn, restore, reps):
     """Best device time (ms) of fn() over reps runs, each after restore()
     (the restore is not timed) and an L2 flush."""
@@ -620,6 +673,9 @@ def _forms(sr, torch, dev, stream, peak):
 
 def main():
     args = _args()
+    if args.classes:
+        run_classes(args)
+        return
     if args.profile_case:
         run_profile_case(args)
     elif args.impl == "reference":

@@ -78,6 +78,7 @@ _STREAMS = {
     "few_pick": 6, "u64": 7, "zipf_table": 8, "zipf_u": 9, "shuffle": 10,
     "lognormal_c": 11, "lognormal_u1": 12, "lognormal_u2": 13, "seg_len_u1": 14,
     "seg_len_u2": 15, "seg_type": 16, "teeth": 17, "kdist": 18, "kexch": 19,
+    "klimited": 20, "kshuffle": 21,
 }
 
 
@@ -340,6 +341,26 @@ def k_sharp_teeth(n: int, k: int) -> np.ndarray:
     a = np.arange(1, n + 1, dtype=np.int32).reshape(k, L)
     a[0::2] = a[0::2, ::-1]
     return a.reshape(-1).copy()
+
+
+def k_limited(n: int, k: int, seed: int = 1) -> np.ndarray:
+    """n values drawn uniformly from 2^k distinct ones, 0 .. 2^k - 1 (Section 2;
+    the blow-up map is monotone and omitted)."""
+    return (u64_stream(seed, "klimited", n) >> np.uint64(64 - k)).astype(np.int32) if k > 0 else \
+        np.zeros(n, np.int32)
+
+
+def k_shuffled_teeth(n: int, k: int, seed: int = 1) -> np.ndarray:
+    """k-sharp teeth whose k sections are interleaved into one sequence at
+    random, each section keeping its own order (Section 2)."""
+    L = n // k
+    sections = k_sharp_teeth(L * k, k).reshape(k, L)
+    labels = np.repeat(np.arange(k), L)
+    order = np.argsort(u64_stream(seed, "kshuffle", L * k), kind="stable")
+    labels = labels[order]
+    out = np.empty(L * k, np.int32)
+    out[np.argsort(labels, kind="stable")] = sections.reshape(-1)   # section j's positions, in order
+    return out
 
 
 def k_distance(n: int, k: int, seed: int = 1) -> np.ndarray:

@@ -100,3 +100,35 @@ def test_nearly_sorted_is_k_exchange():
     s = np.sort(a)
     assert np.count_nonzero(a != s) <= 2 * m
     assert oracle.mono(a) <= 2 * m + 1
+
+
+@pytest.mark.parametrize("k", [0, 1, 4, 12])
+def test_k_limited(k):
+    """At most 2^k distinct values, all in [0, 2^k) (Section 2); k = 0 gives
+    one value."""
+    a = si.k_limited(20_000, k, seed=3)
+    u = np.unique(a)
+    assert u.size <= (1 << k) and u.min() >= 0 and u.max() < (1 << k)
+    if k == 12:
+        assert u.size > 3000            # 20,000 draws cover most of 4,096 values
+
+
+@pytest.mark.parametrize("k", [1, 2, 8])
+def test_k_shuffled_teeth(k):
+    """A permutation of 1..n in which the values of each k-sharp-teeth section
+    appear in that section's order (Section 2); one section is the reversed
+    list, and the interleaving is not the unshuffled teeth for k > 1."""
+    n = 4096
+    a = si.k_shuffled_teeth(n, k, seed=5)
+    assert np.array_equal(np.sort(a), np.arange(1, n + 1, dtype=np.int32))
+    sharp = si.k_sharp_teeth(n, k)
+    L = n // k
+    pos = np.empty(n + 1, np.int64)
+    pos[a] = np.arange(n)
+    for j in range(k):
+        sec = sharp[j * L:(j + 1) * L]
+        assert np.all(np.diff(pos[sec]) > 0)
+    if k == 1:
+        assert np.array_equal(a, sharp)
+    else:
+        assert not np.array_equal(a, sharp)
