@@ -148,6 +148,23 @@ class Clocks:
                 "samples": len(rows)}
 
 
+def _max_over_ranks(x: float, device) -> float:
+    """The maximum of x over the ranks of the default process group (x itself
+    when there is none or it has one rank): the job's time is its slowest rank's."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_value(keys_per_rank: int, ranks: int, ms: float) -> float:
+    """Whole-job throughput in Gkeys/s: every rank's keys over the job's time."""
+    return keys_per_rank * ranks / (ms / 1e3) / 1e9
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -302,13 +319,9 @@ def run_ours(args):
         for c, (e0, e1) in enumerate(evs):
             per_class_ms[c] += e0.elapsed_time(e1)
     per_class_ms = [m / args.steps for m in per_class_ms]
-    ms_step = sum(per_class_ms)
-    if ws > 1:
-        t = torch.tensor([ms_step], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = _max_over_ranks(sum(per_class_ms), dev)
     keys_step = N_KEYS * len(CLASSES)
-    value = keys_step * ws / (ms_step / 1e3) / 1e9
+    value = _job_value(keys_step, ws, ms_step)
 
     # live roofline of each kernel kind over the timed region
     kinds = {}
@@ -367,12 +380,8 @@ def run_ours(args):
         for st_ in streams:
             st_.synchronize()
         e2e_ms += (time.perf_counter() - t0) * 1e3
-    e2e_ms /= args.steps
-    if ws > 1:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e = {"value": keys_step * ws / (e2e_ms / 1e3) / 1e9, "unit": "Gkeys/s",
+    e2e_ms = _max_over_ranks(e2e_ms / args.steps, dev)
+    e2e = {"value": _job_value(keys_step, ws, e2e_ms), "unit": "Gkeys/s",
            "h2d_bytes_per_step": 4 * keys_step, "d2h_bytes_per_step": 4 * keys_step,
            "ms_per_step": e2e_ms,
            "api": "sr_sort_keys_host_async on four streams (one per array), host clock from the first "
