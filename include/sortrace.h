@@ -254,7 +254,7 @@ enum {
  * sample of the input, scattering them, sorting each bucket, and checking
  * that every bucket's largest key is <= the next bucket's smallest; if the
  * check fails the plain sort runs instead (the fallback is in stats.fallback).
- * The call reads the check's verdict back, so it waits for `stream` once.
+ * The call reads the check's outcome back, so it waits for `stream` once.
  * The paper has no learned component; this is the partition-then-sort form of
  * its quicksort (Section 4: split by pivots, then sort the parts), with the
  * pivots read off a learned CDF.

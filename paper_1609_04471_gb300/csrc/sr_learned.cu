@@ -1019,7 +1019,7 @@ static sr_status learned_impl(void *d_keys, size_t n, const sr_learned_opts *o, 
             break;
         }
         rec.aux_kind = 4;
-        // the check's verdict decides whether the plain sort runs: read it back
+        // the check's outcome decides whether the plain sort runs: read it back
         // (launching the plain sort gated on the device would still cost every
         // one of its kernels a full grid of empty CTAs)
         int fallback = 0;
