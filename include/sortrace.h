@@ -86,6 +86,13 @@ typedef void *sr_stream;     /* a cudaStream_t */
 sr_status sr_sort_keys(void *d_keys, size_t n, sr_key_type kt, sr_stream stream);
 
 /*
+ * sr_release_cached -- drops the graphs (and their scratch) that the library
+ * keeps for repeated sr_sort_keys / sr_sort_pairs calls on the current device,
+ * after waiting for their last replays.  Later calls build them again.
+ */
+sr_status sr_release_cached(void);
+
+/*
  * sr_sort_pairs -- stable sort of (d_keys[i], d_vals[i]) by key, in place.
  *   d_keys  n keys of type kt;  d_vals  n uint32 payloads moved with their keys.
  * Equal keys keep their input order: the mergesort's stability (Section 6,

@@ -74,6 +74,7 @@ SIGNATURES = {
     "sr_sort_keys_host": (_i32, [_vp, _sz, _i32, _vp]),
     "sr_sort_keys_host_async": (_i32, [_vp, _sz, _i32, _vp]),
     "sr_sort_keys_host_many": (_i32, [_vp, _vp, _i32, _i32, _vp]),
+    "sr_release_cached": (_i32, []),
     "sr_sort_keys_noalloc": (_i32, [_vp, _sz, _i32, _vp]),
     "sr_sort_keys_learned": (_i32, [_vp, _sz, _i32, _vp, _vp]),
     "sr_detect_runs": (_i32, [_vp, _sz, _i32, _vp, _vp]),
@@ -305,6 +306,12 @@ def sort_keys_host_many(arrs, key_type: int | None = None, stream=None):
     kt = kts.pop() if kts else (key_type if key_type is not None else KEY_I32)
     _check(load().sr_sort_keys_host_many(ptrs, ns, len(args), kt, _stream(stream)), "sr_sort_keys_host_many")
     return arrs
+
+
+def release_cached():
+    """Drops the graphs kept for repeated sort calls on the current device
+    (and their scratch); later calls build them again."""
+    _check(load().sr_release_cached(), "sr_release_cached")
 
 
 def detect_runs(x, key_type: int | None = None, stream=None) -> dict:

@@ -233,6 +233,23 @@ static sr_status build_graph(const PS &plan, typename PS::T *uk, uint32_t *uv, u
     return st;
 }
 
+// Drops every cached graph of the current device and returns its scratch.
+static sr_status graph_cache_clear() {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return launch_status();
+    std::lock_guard<std::mutex> lock(g_gmu);
+    sr_status st = SR_OK;
+    for (auto &x : g_graph) {
+        if (!x.hits || x.dev != dev) continue;
+        if (x.done && cudaEventSynchronize(x.done) != cudaSuccess) st = launch_status();
+        if (x.exec) cudaGraphExecDestroy(x.exec);
+        scratch_free(x.scratch, nullptr);           // idle now: its last replay has finished
+        if (x.done) cudaEventDestroy(x.done);
+        x = GraphEntry();
+    }
+    return st;
+}
+
 unsigned long long graph_kernel_count() {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
@@ -543,14 +560,17 @@ extern "C" sr_status sr_sort_keys_host_many(void *const *h_keys, const size_t *n
         }
         scratch_free(d, co);
     }
-    // the caller's later work on `stream` waits for all of it
-    if (st == SR_OK) st = link(cin, s);
-    for (int k = 0; k < 2 && st == SR_OK; ++k) {
-        st = link(comp[k], s);
-        if (st == SR_OK) st = link(cout[k], s);
+    // the caller's later work on `stream` waits for all of it (also after an
+    // error: the arrays queued before it are still in flight)
+    sr_status st2 = link(cin, s);
+    for (int k = 0; k < 2; ++k) {
+        if (st2 == SR_OK) st2 = link(comp[k], s);
+        if (st2 == SR_OK) st2 = link(cout[k], s);
     }
-    return st;
+    return st != SR_OK ? st : st2;
 }
+
+extern "C" sr_status sr_release_cached(void) { return graph_cache_clear(); }
 
 extern "C" sr_status sr_detect_runs(const void *d_keys, size_t n, sr_key_type kt, sr_run_info *out,
                                     sr_stream stream) {

@@ -520,3 +520,19 @@ def test_graph_cache_eviction(gpu_lib):
                 b.copy_(torch.from_numpy(a).cuda())
                 gpu_lib.sort_keys(b, key_type=0)
                 assert b.cpu().numpy().tobytes() == w, sweep
+
+
+def test_release_cached(gpu_lib):
+    """The graphs kept for repeated calls can be dropped; the next calls
+    rebuild them and give the same results."""
+    import torch
+    a = si.int32_input("nearly_sorted", 300_001, seed=14)
+    want = oracle.sort_keys(a).tobytes()
+    src = torch.from_numpy(a).cuda()
+    x = torch.empty_like(src)
+    for r in range(6):
+        x.copy_(src)
+        gpu_lib.sort_keys(x, key_type=0)
+        assert x.cpu().numpy().tobytes() == want
+        if r == 2:
+            gpu_lib.release_cached()
