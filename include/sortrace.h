@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define SR_ABI_VERSION 1
+#define SR_ABI_VERSION 2
 
 typedef enum {
     SR_KEY_I32 = 0,
@@ -312,6 +312,8 @@ typedef struct {
     uint64_t big_segments;      /* segmented: segments longer than one tile */
     float model_loss;           /* learned: training loss after the last step */
     float bucket_imbalance;     /* learned: B * sum(c_b^2) / n^2 over bucket sizes c_b; 1 = even */
+    uint64_t displaced;         /* input class 4: keys sorted on the side (at least Rem(A),
+                                   Section 2: the kept ones are in order); 0 otherwise */
 } sr_stats;
 
 /* sr_get_stats -- waits for the last call's stream and fills *out. */

@@ -68,7 +68,7 @@ def _load():
             lib.sro_sort_keys.argtypes = [vp, sz, i32, i32]
             lib.sro_sort_pairs.argtypes = [vp, vp, sz, i32, i32]
             lib.sro_sort_segmented.argtypes = [vp, vp, sz, i32, i32]
-            for f in (lib.sro_runs, lib.sro_mono, lib.sro_inversions):
+            for f in (lib.sro_runs, lib.sro_mono, lib.sro_inversions, lib.sro_rem):
                 f.argtypes = [vp, sz, i32]
                 f.restype = u64
             lib.sro_cmp_count.restype = u64
@@ -139,6 +139,12 @@ def inversions(a: np.ndarray) -> int:
     """Inv(A) by its O(n^2) definition."""
     a = np.ascontiguousarray(a)
     return int(_load().sro_inversions(_ptr(a), a.size, _kt(a)))
+
+
+def rem(a: np.ndarray) -> int:
+    """Rem(A): fewest items whose removal leaves a sorted list."""
+    a = np.ascontiguousarray(a)
+    return int(_load().sro_rem(_ptr(a), a.size, _kt(a)))
 
 
 def comparisons() -> int:

@@ -19,9 +19,10 @@
  *   sro_runs         Run(A): descents + 1 (Section 2).
  *   sro_mono         Mono(A): fewest monotone pieces (Section 2), greedy.
  *   sro_inversions   Inv(A) by the O(n^2) definition (Section 2).
+ *   sro_rem          Rem(A): fewest items whose removal leaves a sorted list
+ *                    (the measure Section 2 relates to k-exchange lists).
  *
- * Readings of places where the paper is garbled or silent (each is also listed
- * in the design notes):
+ * Readings of places where the paper is garbled or silent:
  *   R3  Appendix A as printed does not compile and its braces bind the final
  *       "else next++" to the wrong test.  Read: on a descent, a current run
  *       shorter than minrun is extended (reverse the following non-increasing
@@ -536,6 +537,33 @@ uint64_t sro_inversions(const void *base, size_t n, int kt) {
         for (size_t j = i + 1; j < n; j++)
             if (cmp(AT(base, i, es), AT(base, j, es)) > 0) inv++;
     return inv;
+}
+
+/* Rem(A): the fewest items whose removal leaves a non-decreasing list, i.e. n
+ * minus the length of a longest non-decreasing subsequence, found by patience
+ * sorting: tail[l] is the index of the smallest possible last item of a
+ * non-decreasing subsequence of length l + 1 seen so far; each item replaces
+ * the first tail greater than it (or extends the longest).  UINT64_MAX if the
+ * work array cannot be allocated. */
+uint64_t sro_rem(const void *base, size_t n, int kt) {
+    sro_cmp cmp = cmp_for(kt);
+    size_t es = key_size(kt);
+    if (n == 0) return 0;
+    size_t *tail = (size_t *)malloc(n * sizeof(size_t));
+    if (!tail) return UINT64_MAX;
+    size_t len = 0;
+    for (size_t i = 0; i < n; i++) {
+        size_t lo = 0, hi = len;
+        while (lo < hi) {
+            const size_t mid = lo + (hi - lo) / 2;
+            if (cmp(AT(base, tail[mid], es), AT(base, i, es)) > 0) hi = mid;
+            else lo = mid + 1;
+        }
+        tail[lo] = i;
+        if (lo == len) len++;
+    }
+    free(tail);
+    return (uint64_t)(n - len);
 }
 
 /* --------------------------------------------------------- entry points */

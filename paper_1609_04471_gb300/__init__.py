@@ -50,7 +50,8 @@ class Stats(ctypes.Structure):
                 ("input_class", ctypes.c_int32), ("fallback", ctypes.c_int32),
                 ("runs", ctypes.c_uint64), ("bytes_moved", ctypes.c_uint64),
                 ("max_bucket", ctypes.c_uint64), ("big_segments", ctypes.c_uint64),
-                ("model_loss", ctypes.c_float), ("bucket_imbalance", ctypes.c_float)]
+                ("model_loss", ctypes.c_float), ("bucket_imbalance", ctypes.c_float),
+                ("displaced", ctypes.c_uint64)]
 
 
 class LearnedOpts(ctypes.Structure):

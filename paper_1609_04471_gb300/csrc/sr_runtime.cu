@@ -257,6 +257,7 @@ extern "C" sr_status sr_get_stats(sr_stats *out) {
     } else if (out->input_class == 3) {
         bytes += 2 * n * elem;                                          // counted, then written as runs
     } else if (out->input_class == 4) {
+        out->displaced = c.rem_dcount;
         bytes += 2 * n * elem;                                          // split: in-order keys and buckets
         bytes += 2 * c.rem_dcount * elem;                               // bucket sorts
         bytes += 2 * n * elem;                                          // per-tile merges into place

@@ -132,3 +132,45 @@ def test_k_shuffled_teeth(k):
         assert np.array_equal(a, sharp)
     else:
         assert not np.array_equal(a, sharp)
+
+
+def _rem_brute(a):
+    """The fewest removals that leave a sorted list, over every subset kept."""
+    n = len(a)
+    best = n
+    for mask in range(1 << n):
+        kept = [a[i] for i in range(n) if mask >> i & 1]
+        if all(kept[i] <= kept[i + 1] for i in range(len(kept) - 1)):
+            best = min(best, n - len(kept))
+    return best
+
+
+def test_rem_brute_force():
+    """Rem(A) against its definition on every small input drawn (ties included)."""
+    rng = np.random.default_rng(80)
+    for _ in range(300):
+        n = int(rng.integers(0, 10))
+        a = rng.integers(-3, 4, n).astype(np.int32)
+        assert oracle.rem(a) == _rem_brute(a.tolist())
+
+
+def test_rem_closed_forms():
+    n = 1000
+    assert oracle.rem(np.arange(n, dtype=np.int32)) == 0
+    assert oracle.rem(np.zeros(n, np.int32)) == 0
+    assert oracle.rem(np.arange(n, 0, -1).astype(np.int32)) == n - 1
+    # one exchange: two items out of place, one if they were neighbours
+    assert oracle.rem(np.array([1, 4, 3, 2, 5], np.int32)) == 2
+    assert oracle.rem(np.array([1, 3, 2, 4, 5], np.int32)) == 1
+    # float32 totalOrder: -0.0 before +0.0
+    f = np.array([0x00000000, 0x80000000], np.uint32).view(np.float32)
+    assert oracle.rem(f) == 1
+
+
+@pytest.mark.parametrize("k", [1, 5, 40])
+def test_rem_of_k_exchange_lists(k):
+    """A k-exchange list leaves a sorted list once the at most 2k items out of
+    place are removed (Section 2)."""
+    a = si.k_exchange(5000, k, seed=k)
+    r = oracle.rem(a)
+    assert 0 < r <= 2 * k
