@@ -63,6 +63,11 @@ def test_argument_errors_need_no_device(lib):
     assert lib.sr_sort_pairs(None, None, 1, 0, None) == 0
     assert lib.sr_detect_runs(None, 4, 0, None, None) == 1
     assert lib.sr_get_stats(None) == 1
+    # several host arrays: a bad key type, a negative count, missing arrays
+    n = (ctypes.c_size_t * 1)(10)
+    assert lib.sr_sort_keys_host_many(None, n, 1, 9, None) == 1
+    assert lib.sr_sort_keys_host_many(None, None, -1, 0, None) == 1
+    assert lib.sr_sort_keys_host_many(None, n, 1, 0, None) == 1
 
 
 def test_segmented_configs_described_without_gpu():
