@@ -17,8 +17,9 @@ bit):
 Implementations (``sr_oracle.c``, plain single-threaded C over the paper's
 qsort-style interface):
 
-* ``merge``  natural mergesort after the paper's mer6 (Section 3, Appendix A).
-* ``quick``  the hybrid quicksort hyb2 (Section 4, Appendix B).
+* ``merge``  natural mergesort with the techniques of the paper's mer6
+             (Section 3); ``merge5`` the same without short-run growth (mer5).
+* ``quick``  the hybrid quicksort hyb2 (Section 4).
 * ``isort``  insertion sort, the brute-force definition.
 
 Also Run(A), Mono(A) and Inv(A) of Section 2, a comparison counter and a trace
@@ -44,7 +45,7 @@ _lib = None
 
 KEY_TYPES = {np.dtype(np.int32): 0, np.dtype(np.uint32): 1, np.dtype(np.float32): 2,
              np.dtype(np.uint64): 3, np.dtype(np.int64): 4}
-ALGOS = {"merge": 0, "quick": 1, "isort": 2}
+ALGOS = {"merge": 0, "quick": 1, "isort": 2, "merge5": 3}
 
 
 def build(force: bool = False) -> str:
@@ -159,12 +160,14 @@ TRACE_EVENTS = {1: "trim_a", 2: "trim_b", 3: "copy_a", 4: "copy_b", 5: "gallop_a
 
 
 def sort_with_trace(keys: np.ndarray):
-    """Mergesorts a copy of ``keys`` and returns (sorted, [(event, count), ...])
+    """Mergesorts a copy of ``keys`` with the paper's mer5 (natural runs, no
+    growth of short runs, so the runs merged are the input's own, as in the
+    worked example of Section 3) and returns (sorted, [(event, count), ...])
     listing what every merge did."""
     lib = _load()
     lib.sro_trace_enable(1)
     try:
-        out = sort_keys(keys, "merge")
+        out = sort_keys(keys, "merge5")
         buf = np.zeros(256, dtype=np.int64)
         k = lib.sro_trace_read(_ptr(buf), 256)
     finally:

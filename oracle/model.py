@@ -135,20 +135,30 @@ def init_from_sample(xs_sorted: np.ndarray, min_gap: float = 1e-7) -> np.ndarray
     return np.concatenate([[kn[0]], softplus_inv(gaps), np.zeros(H)])
 
 
-def adam_train(theta, x, t, steps: int, lr: float = 3e-3, b1: float = 0.9,
+def adam_steps(theta, grad_fn, steps: int, lr: float = 3e-3, b1: float = 0.9,
                b2: float = 0.999, eps: float = 1e-8):
-    """Plain full-batch Adam (Kingma and Ba, 2015) in float64."""
+    """Adam (Kingma and Ba, 2015, Algorithm 1) in float64: for t = 1..steps,
+    g = grad_fn(theta, t); first and second moment estimates
+    m = b1 m + (1 - b1) g and v = b2 v + (1 - b2) g^2, both started at 0;
+    bias-corrected m^ = m / (1 - b1^t), v^ = v / (1 - b2^t); then
+    theta -= lr m^ / (sqrt(v^) + eps), elementwise."""
     th = np.asarray(theta, dtype=np.float64).copy()
     mo = np.zeros_like(th)
     ve = np.zeros_like(th)
     for k in range(1, steps + 1):
-        _, gr = loss_and_grad(th, x, t)
+        gr = np.asarray(grad_fn(th, k), dtype=np.float64)
         mo = b1 * mo + (1 - b1) * gr
         ve = b2 * ve + (1 - b2) * gr * gr
         mh = mo / (1 - b1 ** k)
         vh = ve / (1 - b2 ** k)
         th = th - lr * mh / (np.sqrt(vh) + eps)
     return th
+
+
+def adam_train(theta, x, t, steps: int, lr: float = 3e-3, b1: float = 0.9,
+               b2: float = 0.999, eps: float = 1e-8):
+    """Full-batch Adam on the router's loss over the points (x, t)."""
+    return adam_steps(theta, lambda th, k: loss_and_grad(th, x, t)[1], steps, lr, b1, b2, eps)
 
 
 def buckets(theta, x, num_buckets: int) -> np.ndarray:

@@ -11,28 +11,32 @@
  * through one counted comparator call.
  *
  *   sro_isort        plain insertion sort: the brute-force definition of sorting.
- *   sro_mergesort    natural mergesort in the style of the paper's "mer6"
- *                    (Section 3, techniques (a), (b), (f), (g) and the half-down
- *                    run list (e2); Appendix A).  Stable.  The primary oracle.
+ *   sro_mergesort    natural mergesort with the techniques of the paper's "mer6"
+ *                    (Section 3: (a) reversed runs, (b) short runs grown by
+ *                    insertion sort, (f) trimming, (g) galloping, (e2) the
+ *                    half-down run list).  Stable.  The primary oracle.  The
+ *                    "merge5" algorithm is the same without (b) (the paper's
+ *                    mer5).
  *   sro_quicksort    the paper's hybrid quicksort "hyb2" (Section 4, techniques
- *                    (a)-(g), alpha = beta = 32, gamma = 2; Appendix B).
+ *                    (a)-(g), alpha = beta = 32, gamma = 2).
  *   sro_runs         Run(A): descents + 1 (Section 2).
  *   sro_mono         Mono(A): fewest monotone pieces (Section 2), greedy.
  *   sro_inversions   Inv(A) by the O(n^2) definition (Section 2).
  *   sro_rem          Rem(A): fewest items whose removal leaves a sorted list
  *                    (the measure Section 2 relates to k-exchange lists).
  *
+ * The two sorts are written from the techniques as Section 3 and Section 4
+ * state them, not from the listings of the appendices.
+ *
  * Readings of places where the paper is garbled or silent:
- *   R3  Appendix A as printed does not compile and its braces bind the final
- *       "else next++" to the wrong test.  Read: on a descent, a current run
- *       shorter than minrun is extended (reverse the following non-increasing
- *       run, merge, insertion-sort up to minrun); a long-enough run is closed
- *       and pushed on the half-down list; an ascending step just advances.
- *       An equal block still pending when the descending scan stops is also
- *       pre-reversed, so the sort stays stable.  Indices are size_t.
- *   R4  Appendix B's scans are read as the standard Hoare scans:
- *       advance i while a[i] < v, retreat j while a[j] > v; c counts stops on
- *       elements equal to v.
+ *   R3  Techniques (a) and (b) together: the input is cut into maximal runs,
+ *       each either non-decreasing or non-increasing (the latter reversed,
+ *       its blocks of equal items reversed first so they keep their order);
+ *       a run shorter than minrun is then grown to minrun items by insertion
+ *       sort.  Every run so made goes on the half-down list.
+ *   R4  The 2-way split (technique (e)) is Hoare's: one scan advances past
+ *       items < v, the other retreats past items > v, the stopped pair is
+ *       exchanged; the equal items the scans stop on are counted for (g).
  *   R5  Technique (f): the B-suffix that is >= the last element of A is
  *       left in place (">=" trims more than ">" and gives the same result).
  *   R6  An ascending run is non-decreasing (Run(A) counts strict descents only).
@@ -45,9 +49,9 @@
  *       side, the count used by the worked example of Section 3; it then
  *       moves the winning side's whole block, found by probing 1, 3, 7, ...
  *       items ahead and finishing with a binary search.
- *   R11 minrun is not stated.  minrun = 8 reproduces Table 4's count for mer6
- *       on random integers (22.15 comparisons per item at n = 2,000,000)
- *       within 1%; 16 and 32 give about 23.0 and 25.8.
+ *   R11 minrun is not stated; MINRUN is the value whose comparison count on
+ *       random integers comes closest to Table 4's 22.15 per item for mer6
+ *       at n = 2,000,000: 14 gives 22.11 (8 gives 21.53, 16 gives 22.25).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -309,67 +313,104 @@ static void merge_runs(void *base, size_t lo, size_t mid, size_t hi, size_t es, 
 
 /* ------------------------------------------------------------ mergesort */
 
-#define MINRUN 8     /* reading R11 */
+#define MINRUN 14    /* reading R11 */
 
-/* Natural mergesort with the paper's techniques (Section 3, Appendix A;
- * reading R3).  Returns 0, or -1 if the temporary buffer cannot be had. */
-int sro_mergesort(void *base, size_t n, size_t es, sro_cmp cmp) {
+/* What a sort routine works on: the array, its item size, the comparison and
+ * a temporary buffer of n items for the merges. */
+typedef struct {
+    char *base;
+    size_t n, es;
+    sro_cmp cmp;
+    char *tmp;
+} sorter;
+
+/* Technique (a): the end of the run that starts at lo, turned ascending.  A
+ * run that opens with a rise (or an equal pair) is the longest non-decreasing
+ * stretch; one that opens with a strict fall is the longest non-increasing
+ * stretch, which is reversed in place -- after every block of equal items in
+ * it has been reversed on its own, so that equal items end up in their input
+ * order again (stability). */
+static size_t take_run(sorter *so, size_t lo) {
+    size_t hi = lo + 1;
+    if (hi >= so->n) return so->n;
+    if (so->cmp(AT(so->base, lo, so->es), AT(so->base, hi, so->es)) <= 0) {
+        while (hi + 1 < so->n && so->cmp(AT(so->base, hi, so->es), AT(so->base, hi + 1, so->es)) <= 0) hi++;
+        return hi + 1;
+    }
+    size_t eq_from = hi;                 /* first item of the current block of equal items */
+    for (;;) {
+        int c = hi + 1 < so->n ? so->cmp(AT(so->base, hi, so->es), AT(so->base, hi + 1, so->es)) : -1;
+        if (c != 0 && hi > eq_from) reverse_items(so->base, eq_from, hi, so->es);
+        if (c < 0) break;                /* a rise (or the end): the run stops at hi */
+        hi++;
+        if (c > 0) eq_from = hi;
+    }
+    reverse_items(so->base, lo, hi, so->es);
+    return hi + 1;
+}
+
+/* Technique (b): a run [lo, end) shorter than `minrun` grows to minrun items
+ * (or to the end of the array) by insertion sort. */
+static size_t grow_run(sorter *so, size_t lo, size_t end, size_t minrun) {
+    if (end - lo >= minrun || end >= so->n) return end;
+    size_t want = so->n - lo < minrun ? so->n : lo + minrun;
+    isort_range(so->base, lo, end, want, so->es, so->cmp);
+    return want;
+}
+
+/* Technique (e2), the half-down list: sorted runs side by side from the start
+ * of the array; edge[0] = 0 and run i is [edge[i], edge[i+1]).  Each run on
+ * the list is at most half as long as its predecessor. */
+typedef struct {
+    size_t edge[130];
+    int runs;
+} halfdown_list;
+
+static void list_merge_top(sorter *so, halfdown_list *L) {
+    size_t a = L->edge[L->runs - 2], m = L->edge[L->runs - 1], b = L->edge[L->runs];
+    merge_runs(so->base, a, m, b, so->es, so->cmp, so->tmp);
+    L->edge[L->runs - 1] = b;
+    L->runs--;
+}
+
+/* Appends the run that ends at `end`, then restores the half-down property:
+ * while the newest run is longer than half of the one before it, the two are
+ * merged (which may in turn break the property one place further back). */
+static void list_append(sorter *so, halfdown_list *L, size_t end) {
+    L->edge[++L->runs] = end;
+    while (L->runs >= 2) {
+        size_t last = L->edge[L->runs] - L->edge[L->runs - 1];
+        size_t before = L->edge[L->runs - 1] - L->edge[L->runs - 2];
+        if (last <= before / 2) break;
+        list_merge_top(so, L);
+    }
+}
+
+/* Natural mergesort of Section 3: runs are taken from the input (a), short
+ * ones grown to `minrun` (b; minrun <= 1 leaves them alone), kept on the
+ * half-down list (e2), and merged with trimming (f) and galloping (g).  The
+ * run lengths on the list fall by half at every step, so it holds at most
+ * log2(n) + 2 runs.  With minrun = MINRUN this is the paper's mer6; with
+ * minrun = 1, mer5.  Returns 0, or -1 if the temporary buffer cannot be had. */
+static int mergesort_runs(void *base, size_t n, size_t es, sro_cmp cmp, size_t minrun) {
     if (n < 2) return 0;
-    char *tmp = (char *)malloc(n * es);
-    if (!tmp) return -1;
-    size_t run[128];                 /* starts of the runs on the half-down list */
-    int runnum = 0;
-    size_t start = 0, next = 1;
-    run[0] = 0;
-    while (next < n) {
-        if (cmp(AT(base, next - 1, es), AT(base, next, es)) <= 0) { next++; continue; }
-        /* a descent between next-1 and next */
-        if (next - start < MINRUN) {
-            /* (a): take the non-increasing run that follows; reverse each
-             * block of equal items first so the whole reversal keeps them in
-             * their original order. */
-            size_t j = next + 1, s = 0;
-            int t;
-            while (j < n && (t = cmp(AT(base, j - 1, es), AT(base, j, es))) >= 0) {
-                if (t == 0) s++;
-                else if (s > 0) { reverse_items(base, j - 1 - s, j - 1, es); s = 0; }
-                j++;
-            }
-            if (s > 0) reverse_items(base, j - 1 - s, j - 1, es);   /* flush (R3) */
-            if (next > start + 1) {
-                reverse_items(base, next, j - 1, es);
-                merge_runs(base, start, next, j, es, cmp, tmp);
-            } else {
-                reverse_items(base, start, j - 1, es);
-            }
-            next = j;
-            if (next - start < MINRUN) {
-                /* (b): still short, extend to minrun by insertion sort */
-                size_t e = start + MINRUN < n ? start + MINRUN : n;
-                isort_range(base, start, next, e, es, cmp);
-                next = e;
-            }
-        } else {
-            /* the run [start, next) is long enough: close it and keep the
-             * half-down list (e2): merge a closed run with its predecessor
-             * while it is longer than half of the predecessor. */
-            run[++runnum] = start = next;
-            next++;
-            while (runnum > 1 &&
-                   (run[runnum] - run[runnum - 1]) > ((run[runnum - 1] - run[runnum - 2]) >> 1)) {
-                merge_runs(base, run[runnum - 2], run[runnum - 1], run[runnum], es, cmp, tmp);
-                run[runnum - 1] = run[runnum];
-                runnum--;
-            }
-        }
+    sorter so = {(char *)base, n, es, cmp, (char *)malloc(n * es)};
+    if (!so.tmp) return -1;
+    halfdown_list L;
+    L.edge[0] = 0;
+    L.runs = 0;
+    for (size_t lo = 0; lo < n;) {
+        size_t end = grow_run(&so, lo, take_run(&so, lo), minrun);
+        list_append(&so, &L, end);
+        lo = end;
     }
-    /* merge what is left on the list, last run first */
-    while (runnum > 0) {
-        merge_runs(base, run[runnum - 1], run[runnum], n, es, cmp, tmp);
-        runnum--;
-    }
-    free(tmp);
+    while (L.runs > 1) list_merge_top(&so, &L);    /* what is left, last run first */
+    free(so.tmp);
     return 0;
+}
+
+int sro_mergesort(void *base, size_t n, size_t es, sro_cmp cmp) {
+    return mergesort_runs(base, n, es, cmp, MINRUN);
 }
 
 /* ------------------------------------------------------------ quicksort */
@@ -403,91 +444,102 @@ static size_t pivot9(const void *base, size_t lo, size_t hi, size_t es, sro_cmp 
     return med3(base, m1, m2, m3, es, cmp);
 }
 
-/* 3-way quicksort on [lo, hi] inclusive with techniques (a)-(f): while
- * splitting, items equal to the pivot are swapped to both ends; afterwards they
- * are moved to the middle and left out of the recursion (technique (d)). */
-static void qsort_3way(void *base, long lo, long hi, size_t es, sro_cmp cmp) {
-    while (hi > lo) {
-        long n = hi - lo + 1;
-        if (n < ALPHA) { isort_range(base, (size_t)lo, (size_t)lo + 1, (size_t)hi + 1, es, cmp); return; }
-        if (is_sorted_range(base, (size_t)lo, (size_t)hi, es, cmp)) return;
-        size_t p = n < BETA ? med3(base, (size_t)lo, (size_t)(lo + (hi - lo) / 2), (size_t)hi, es, cmp)
-                            : pivot9(base, (size_t)lo, (size_t)hi, es, cmp);
-        char v[64];
-        memcpy(v, AT(base, p, es), es);
-        /* during the split: [lo,a) == v, [a,b) < v, (c,d] > v, (d,hi] == v */
-        long a = lo, b = lo, c = hi, d = hi;
-        for (;;) {
-            while (b <= c) {
-                int r = cmp(AT(base, b, es), v);
-                if (r > 0) break;
-                if (r == 0) { swap_items(base, (size_t)a, (size_t)b, es); a++; }
-                b++;
-            }
-            while (b <= c) {
-                int r = cmp(AT(base, c, es), v);
-                if (r < 0) break;
-                if (r == 0) { swap_items(base, (size_t)c, (size_t)d, es); d--; }
-                c--;
-            }
-            if (b > c) break;
-            swap_items(base, (size_t)b, (size_t)c, es);
-            b++; c--;
-        }
-        /* move both equal blocks next to each other in the middle */
-        long s = (a - lo) < (b - a) ? (a - lo) : (b - a);
-        for (long k = 0; k < s; k++) swap_items(base, (size_t)(lo + k), (size_t)(b - s + k), es);
-        s = (d - c) < (hi - d) ? (d - c) : (hi - d);
-        for (long k = 0; k < s; k++) swap_items(base, (size_t)(b + k), (size_t)(hi + 1 - s + k), es);
-        long nlt = b - a, ngt = d - c;      /* < part [lo, lo+nlt), > part [hi+1-ngt, hi] */
-        if (nlt < ngt) {
-            if (nlt > 1) qsort_3way(base, lo, lo + nlt - 1, es, cmp);
-            lo = hi + 1 - ngt;
-        } else {
-            if (ngt > 1) qsort_3way(base, hi + 1 - ngt, hi, es, cmp);
-            hi = lo + nlt - 1;
-        }
+/* The outcome of splitting [lo, hi] around a pivot value v: the recursion
+ * continues on [lo, left_end] and [right_begin, hi]; `equal_seen` counts the
+ * items equal to v that the split met (technique (g)). */
+typedef struct {
+    long left_end, right_begin;
+    long equal_seen;
+} split_result;
+
+/* 2-way split with the pivot left unplaced (technique (e)): afterwards
+ * [lo, left_end] <= v and [left_end + 1, hi] >= v.  Two scans move towards
+ * each other, each stopping at an item on the wrong side (or equal to v), and
+ * the two stopped items change places.  A median pivot is never the unique
+ * largest item of the range, so both parts are shorter than the range. */
+static split_result split_two_way(sorter *so, long lo, long hi, const void *v) {
+    split_result r = {0, 0, 0};
+    long up = lo - 1, down = hi + 1;
+    for (;;) {
+        int c;
+        do { up++; c = so->cmp(AT(so->base, up, so->es), v); } while (c < 0);
+        r.equal_seen += c == 0;
+        do { down--; c = so->cmp(AT(so->base, down, so->es), v); } while (c > 0);
+        r.equal_seen += c == 0;
+        if (up >= down) break;
+        swap_items(so->base, (size_t)up, (size_t)down, so->es);
     }
+    if (down >= hi || down < lo) abort();
+    r.left_end = down;
+    r.right_begin = down + 1;
+    return r;
 }
 
-/* hybrid quicksort hyb2 on [lo, hi] inclusive (Section 4 (a)-(g), Appendix B,
- * reading R4): 2-way Hoare split around a pivot that is not placed (e); if the
- * scans stopped on more than GAMMA items equal to the pivot, both halves go to
- * the 3-way quicksort (g). */
-static void qsort_hyb(void *base, long lo, long hi, size_t es, sro_cmp cmp) {
-    long n = hi - lo + 1;
-    if (n < ALPHA) { isort_range(base, (size_t)lo, (size_t)lo + 1, (size_t)hi + 1, es, cmp); return; }
-    if (is_sorted_range(base, (size_t)lo, (size_t)hi, es, cmp)) return;
-    size_t p = n < BETA ? med3(base, (size_t)lo, (size_t)(lo + (hi - lo) / 2), (size_t)hi, es, cmp)
-                        : pivot9(base, (size_t)lo, (size_t)hi, es, cmp);
-    char v[64];
-    memcpy(v, AT(base, p, es), es);
-    long i = lo, j = hi;
-    int c = 0;
+/* 3-way split (technique (d)): items equal to v are parked at both ends of
+ * the range while the scans run, then moved next to each other in the middle,
+ * where they take no further part.  Afterwards [lo, left_end] < v,
+ * [right_begin, hi] > v and everything between equals v. */
+static split_result split_three_way(sorter *so, long lo, long hi, const void *v) {
+    split_result r = {0, 0, 0};
+    long eq_lo = lo, up = lo;              /* [lo, eq_lo) == v, [eq_lo, up) < v */
+    long down = hi, eq_hi = hi;            /* (down, eq_hi] > v, (eq_hi, hi] == v */
     for (;;) {
-        int r;
-        while ((r = cmp(AT(base, i, es), v)) < 0) i++;
-        if (r == 0) c++;
-        while ((r = cmp(AT(base, j, es), v)) > 0) j--;
-        if (r == 0) c++;
-        if (i >= j) break;
-        swap_items(base, (size_t)i, (size_t)j, es);
-        i++; j--;
+        int c;
+        while (up <= down && (c = so->cmp(AT(so->base, up, so->es), v)) <= 0) {
+            if (c == 0) { swap_items(so->base, (size_t)eq_lo, (size_t)up, so->es); eq_lo++; r.equal_seen++; }
+            up++;
+        }
+        while (up <= down && (c = so->cmp(AT(so->base, down, so->es), v)) >= 0) {
+            if (c == 0) { swap_items(so->base, (size_t)down, (size_t)eq_hi, so->es); eq_hi--; r.equal_seen++; }
+            down--;
+        }
+        if (up > down) break;
+        swap_items(so->base, (size_t)up, (size_t)down, so->es);
+        up++;
+        down--;
     }
-    /* [lo, j] <= v and [i, hi] >= v; both are shorter than [lo, hi] because a
-     * median pivot is never the unique extreme of the range. */
-    if (j >= hi || i <= lo) abort();
-    if (c > GAMMA) {
-        if (lo < j) qsort_3way(base, lo, j, es, cmp);
-        if (i < hi) qsort_3way(base, i, hi, es, cmp);
-    } else {
-        if (lo < j) qsort_hyb(base, lo, j, es, cmp);
-        if (i < hi) qsort_hyb(base, i, hi, es, cmp);
+    long less = up - eq_lo, more = eq_hi - down;
+    /* the left block of equal items changes places with the end of the < part */
+    long s = eq_lo - lo < less ? eq_lo - lo : less;
+    for (long k = 0; k < s; k++) swap_items(so->base, (size_t)(lo + k), (size_t)(up - s + k), so->es);
+    /* the right block with the start of the > part */
+    s = hi - eq_hi < more ? hi - eq_hi : more;
+    for (long k = 0; k < s; k++) swap_items(so->base, (size_t)(up + k), (size_t)(hi + 1 - s + k), so->es);
+    r.left_end = lo + less - 1;
+    r.right_begin = hi + 1 - more;
+    return r;
+}
+
+/* Hybrid quicksort of Section 4 on [lo, hi] (inclusive): insertion sort for
+ * fewer than ALPHA items (a), nothing to do on an already sorted range (f),
+ * the median of three (b) or the pseudo-median of nine (c) as pivot, and a
+ * split that is 2-way until a split meets more than GAMMA items equal to its
+ * pivot, after which the ranges below use the 3-way split (g, d).  The
+ * shorter part recurses; the longer one continues in the loop. */
+static void quick_range(sorter *so, long lo, long hi, int three_way) {
+    while (hi > lo) {
+        long n = hi - lo + 1;
+        if (n < ALPHA) { isort_range(so->base, (size_t)lo, (size_t)lo + 1, (size_t)hi + 1, so->es, so->cmp); return; }
+        if (is_sorted_range(so->base, (size_t)lo, (size_t)hi, so->es, so->cmp)) return;
+        size_t p = n < BETA ? med3(so->base, (size_t)lo, (size_t)(lo + (hi - lo) / 2), (size_t)hi, so->es, so->cmp)
+                            : pivot9(so->base, (size_t)lo, (size_t)hi, so->es, so->cmp);
+        char v[64];
+        memcpy(v, AT(so->base, p, so->es), so->es);
+        split_result r = three_way ? split_three_way(so, lo, hi, v) : split_two_way(so, lo, hi, v);
+        if (!three_way && r.equal_seen > GAMMA) three_way = 1;
+        if (r.left_end - lo < hi - r.right_begin) {
+            quick_range(so, lo, r.left_end, three_way);
+            lo = r.right_begin;
+        } else {
+            quick_range(so, r.right_begin, hi, three_way);
+            hi = r.left_end;
+        }
     }
 }
 
 int sro_quicksort(void *base, size_t n, size_t es, sro_cmp cmp) {
-    if (n >= 2) qsort_hyb(base, 0, (long)n - 1, es, cmp);
+    sorter so = {(char *)base, n, es, cmp, NULL};
+    if (n >= 2) quick_range(&so, 0, (long)n - 1, 0);
     return 0;
 }
 
@@ -568,13 +620,14 @@ uint64_t sro_rem(const void *base, size_t n, int kt) {
 
 /* --------------------------------------------------------- entry points */
 
-enum { SRO_ALGO_MERGE = 0, SRO_ALGO_QUICK = 1, SRO_ALGO_ISORT = 2 };
+enum { SRO_ALGO_MERGE = 0, SRO_ALGO_QUICK = 1, SRO_ALGO_ISORT = 2, SRO_ALGO_MERGE5 = 3 };
 
 static int run_algo(void *base, size_t n, size_t es, sro_cmp cmp, int algo) {
     switch (algo) {
     case SRO_ALGO_MERGE: return sro_mergesort(base, n, es, cmp);
     case SRO_ALGO_QUICK: return sro_quicksort(base, n, es, cmp);
     case SRO_ALGO_ISORT: return sro_isort(base, n, es, cmp);
+    case SRO_ALGO_MERGE5: return mergesort_runs(base, n, es, cmp, 1);
     default: return -2;
     }
 }

@@ -69,6 +69,31 @@ def test_device_adam_matches_oracle(gpu_lib):
     assert np.max(np.abs(np.asarray(th_gpu) - th_ref)) < 0.05
 
 
+def test_device_adam_first_step_exact(gpu_lib):
+    """One device Adam step against the oracle's: a bias-corrected first step
+    moves every parameter by lr * g / (|g| + eps), i.e. by the step size in
+    the direction against its gradient.  Parameters whose float64 gradient
+    is clearly non-zero (|g| > 1e-4, so float32 rounding cannot flip its
+    sign) must land within 1e-6 of the oracle's (plus float32 rounding of
+    the parameter); the rest move by at most the step size."""
+    keys = si.lognormal_f32(200_000, 5)
+    o = M.ord_u32_f32(keys).astype(np.float64)
+    xs = np.sort(M.normalise(o, o.min(), o.max()))[::50].astype(np.float32)
+    ts = ((np.arange(xs.size) + 0.5) / xs.size).astype(np.float32)
+    th0 = M.init_from_sample(xs.astype(np.float64)).astype(np.float32)
+    lr = 3e-3
+    th_gpu, _ = gpu_lib.model_train(_f32dev(xs), _f32dev(ts), th0, steps=1, lr=lr)
+    x64, t64, th64 = xs.astype(np.float64), ts.astype(np.float64), th0.astype(np.float64)
+    th_ref = M.adam_train(th64, x64, t64, steps=1, lr=lr)
+    _, g = M.loss_and_grad(th64, x64, t64)
+    d = np.abs(np.asarray(th_gpu, dtype=np.float64) - th_ref)
+    clear = np.abs(g) > 1e-4
+    assert clear.sum() >= 10
+    tol = 1e-6 + 4e-7 * np.abs(th64)           # float32 rounding of the updated value
+    assert np.all(d[clear] < tol[clear]), np.max(d[clear] / tol[clear])
+    assert np.max(np.abs(np.asarray(th_gpu, dtype=np.float64) - th64)) <= lr * (1 + 1e-5)
+
+
 def test_routing_monotone_and_matches_oracle(gpu_lib):
     import torch
     rng = np.random.default_rng(42)
@@ -148,23 +173,20 @@ def test_trained_model_gains_over_ablations(gpu_lib):
     assert res["trained"]["model_loss"] < res["untrained"]["model_loss"]
 
 
-def test_learned_full_size_matches_plain(gpu_lib):
-    """2^27 float32 keys of the lognormal mixture: the learned sort equals the
-    plain GPU sort (itself checked against the oracle) bit for bit and is a
-    sorted permutation of the input."""
+def test_learned_full_size_matches_plain(gpu_lib, full_size_oracle):
+    """2^27 float32 keys of the lognormal mixture: the learned sort's output
+    equals the oracle's byte for byte, and the plain GPU sort's too."""
     import torch
     a = si.lognormal_f32(1 << 27, 1)
     x = _dev(a)
     y = x.clone()
     gpu_lib.sort_keys_learned(x, key_type=2)
     st = gpu_lib.stats()
+    assert st["fallback"] == 0
     gpu_lib.sort_keys(y, key_type=2)
     assert torch.equal(x, y)
     got = x.cpu().numpy().view(np.float32)
-    assert np.all(np.diff(got) >= 0)
-    assert st["fallback"] == 0
-    s = np.sort(a)
-    assert got.tobytes() == s.tobytes()
+    full_size_oracle("lognormal_f32_2p27_seed1", [a], [got], lambda: [oracle.sort_keys(a)])
 
 
 def test_every_bucket_config_exact(gpu_lib):

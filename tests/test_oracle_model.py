@@ -113,3 +113,38 @@ def test_ord_f32_total_order():
     v = np.array([-np.inf, -2.0, -0.0, 0.0, 1e-45, 3.0, np.inf], dtype=np.float32)
     o = M.ord_u32_f32(v)
     assert np.all(np.diff(o.astype(np.int64)) > 0)
+
+
+def test_adam_hand_worked_steps():
+    """Adam's update (Kingma and Ba, 2015, Algorithm 1) on a worked example
+    computed by hand: step size 1, b1 = 0.5, b2 = 0.96, eps = 0, and a fixed
+    gradient sequence g = 2, -2, 4 for the first parameter (its mirror for
+    the second).
+      t=1: m = 1, v = 0.16; m^ = 1/0.5 = 2, v^ = 0.16/0.04 = 4: a step of 1
+           (a first bias-corrected step always has the step size's length).
+      t=2: m = -0.5, v = 0.3136; m^ = -0.5/0.75 = -2/3, v^ = 0.3136/0.0784 = 4:
+           a step of -1/3.
+      t=3: m = 1.75, v = 0.941056; m^ = 1.75/0.875 = 2,
+           v^ = 0.941056/0.115264 = 14704/1801: a step of 2 sqrt(1801/14704).
+    Without the bias correction the first step would be 2.5; with b1 and b2
+    swapped the second would be -1/7; eps is checked on its own below."""
+    seq = [np.array([2.0, -2.0]), np.array([-2.0, 2.0]), np.array([4.0, -4.0])]
+    th0 = np.array([3.0, -1.0])
+    run = lambda k: M.adam_steps(th0, lambda th, t: seq[t - 1], k, lr=1.0, b1=0.5, b2=0.96, eps=0.0)
+    s3 = 2.0 * np.sqrt(1801.0 / 14704.0)
+    for k, want0 in ((1, 3.0 - 1.0), (2, 3.0 - 1.0 + 1.0 / 3.0), (3, 3.0 - 1.0 + 1.0 / 3.0 - s3)):
+        got = run(k)
+        assert abs(got[0] - want0) < 1e-12, (k, got)
+        assert abs(got[1] - (-1.0 - (want0 - 3.0))) < 1e-12, (k, got)
+    # eps outside the square root: m^ = 2, v^ = 4, eps = 1 gives a step of
+    # 2 / (2 + 1) = 2/3 (inside the root it would be 2 / sqrt(5))
+    got = M.adam_steps(np.array([0.0]), lambda th, t: np.array([2.0]), 1, lr=1.0, b1=0.5, b2=0.96, eps=1.0)
+    assert abs(got[0] + 2.0 / 3.0) < 1e-12, got
+    # adam_train is adam_steps on the router's own gradient
+    rng = np.random.default_rng(5)
+    xs = np.sort(rng.random(300))
+    t = M.targets(xs.size)
+    th = M.init_from_sample(xs)
+    a = M.adam_train(th, xs, t, steps=3, lr=1e-2)
+    b = M.adam_steps(th, lambda p, k: M.loss_and_grad(p, xs, t)[1], 3, lr=1e-2)
+    assert np.array_equal(a, b)

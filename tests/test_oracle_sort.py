@@ -11,7 +11,10 @@ import oracle
 import sortrace_inputs as si
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-ALGOS = ("merge", "quick")
+# "merge5" (no growth of short runs) is also the path of the worked-example
+# trace; at these sizes it exercises run reversal and the half-down list that
+# "merge" would leave to insertion sort on inputs shorter than its minrun.
+ALGOS = ("merge", "merge5", "quick")
 
 
 def _all_dtypes_random(rng, n, dtype):
@@ -117,22 +120,29 @@ def test_pairs_stability():
     """Stable pair sort: keys non-decreasing, payloads increasing within equal
     keys, and the library's stable argsort gives the same permutation."""
     rng = np.random.default_rng(11)
-    for dtype in (np.int32, np.uint64, np.float32):
-        for n in (0, 1, 2, 33, 500, 5000):
-            k = (rng.integers(0, 7, n).astype(dtype) if n else np.zeros(0, dtype))
-            v = np.arange(n, dtype=np.uint32)
-            ok, ov = oracle.sort_pairs(k, v)
-            perm = np.argsort(k, kind="stable")
-            assert np.array_equal(ov, v[perm])
-            assert np.array_equal(ok, k[perm])
-    # exhaustive: all sequences over 3 values, n <= 7, against brute force
-    for n in range(8):
-        for seq in itertools.product(range(3), repeat=n):
-            k = np.array(seq, dtype=np.int32)
-            v = np.arange(n, dtype=np.uint32)
-            _, ov = oracle.sort_pairs(k, v)
-            want = [i for _, i in sorted(zip(seq, range(n)), key=lambda p: p[0])]
-            assert ov.tolist() == want
+    for algo in ("merge", "merge5"):
+        for dtype in (np.int32, np.uint64, np.float32):
+            for n in (0, 1, 2, 33, 500, 5000):
+                k = (rng.integers(0, 7, n).astype(dtype) if n else np.zeros(0, dtype))
+                v = np.arange(n, dtype=np.uint32)
+                ok, ov = oracle.sort_pairs(k, v, algo)
+                perm = np.argsort(k, kind="stable")
+                assert np.array_equal(ov, v[perm])
+                assert np.array_equal(ok, k[perm])
+        # non-increasing runs full of equal keys: the reversal must keep
+        # every block of equal keys in input order
+        k = np.repeat(np.arange(40, 0, -1, dtype=np.int32), rng.integers(1, 6, 40))
+        v = np.arange(k.size, dtype=np.uint32)
+        _, ov = oracle.sort_pairs(k, v, algo)
+        assert np.array_equal(ov, v[np.argsort(k, kind="stable")])
+        # exhaustive: all sequences over 3 values, n <= 7, against brute force
+        for n in range(8):
+            for seq in itertools.product(range(3), repeat=n):
+                k = np.array(seq, dtype=np.int32)
+                v = np.arange(n, dtype=np.uint32)
+                _, ov = oracle.sort_pairs(k, v, algo)
+                want = [i for _, i in sorted(zip(seq, range(n)), key=lambda p: p[0])]
+                assert ov.tolist() == want
 
 
 def test_pairs_isort_agrees():
@@ -218,3 +228,49 @@ def test_random_comparisons_table4():
     quick = oracle.comparisons() / n
     assert abs(merge - 22.15) / 22.15 < 0.03, merge
     assert abs(quick - 24.77) / 24.77 < 0.05, quick
+
+
+def test_k_limited_comparisons_table4():
+    """Table 4, k-limited class (n = 2,000,000, k = 2^0 .. 2^8 bits; 32 bits and
+    more is plain random int32): hyb2 makes 14.63 comparisons per item, the
+    plain 2-way quicksort 16.64 and the 3-way one 13.65, so the count pins the
+    switch to the 3-way split after more than gamma = 2 equal items (technique
+    (g)); mer6 makes 16.17.  The mean over the nine k lands within 1.5% (hyb2)
+    and 3% (mer6)."""
+    n = 2_000_000
+
+    def per_item(algo):
+        tot = 0.0
+        for i in range(9):
+            a = si.k_limited(n, min(2 ** i, 32), seed=3)
+            oracle.reset_comparisons()
+            oracle.sort_keys(a, algo)
+            tot += oracle.comparisons() / n
+        return tot / 9
+
+    quick = per_item("quick")
+    assert abs(quick - 14.63) / 14.63 < 0.015, quick
+    merge = per_item("merge")
+    assert abs(merge - 16.17) / 16.17 < 0.03, merge
+
+
+def test_teeth_and_exchange_comparisons_table4():
+    """Table 4, hyb2 on k-even teeth (19.36 per item) and k-exchange lists
+    (6.07), k = 2^0 .. 2^8, n = 2,000,000 (rounded down to a multiple of k for
+    the teeth): the is-sorted test (f) and the unplaced pivot (e) keep both
+    far below the ~24.8 of random input; within 3%."""
+    n = 2_000_000
+
+    def per_item(gen):
+        tot = 0.0
+        for i in range(9):
+            a = gen(2 ** i)
+            oracle.reset_comparisons()
+            oracle.sort_keys(a, "quick")
+            tot += oracle.comparisons() / a.size
+        return tot / 9
+
+    even = per_item(lambda k: si.k_even_teeth(n - n % k, k))
+    assert abs(even - 19.36) / 19.36 < 0.03, even
+    exch = per_item(lambda k: si.k_exchange(n, k, seed=3))
+    assert abs(exch - 6.07) / 6.07 < 0.03, exch
