@@ -297,8 +297,8 @@ typedef struct {
     int32_t key_type;
     int32_t tile;               /* keys per block-sort tile */
     int32_t merge_tile;         /* output keys per merge CTA */
-    int32_t passes_planned;     /* merge passes launched */
-    int32_t passes_skipped;     /* passes found already in order (no bytes moved) */
+    int32_t passes_planned;     /* merge steps launched (each a 4-way or 2-way merge pass over the data) */
+    int32_t passes_skipped;     /* steps found already in order (no bytes moved) */
     int32_t input_class;        /* 0 unsorted, 1 sorted, 2 strictly descending,
                                    3 at most 64 distinct keys (4-byte keys, keys only:
                                    counted per distinct key and written as runs),

@@ -104,10 +104,14 @@ template <int KB, bool VALS> struct Shape;
 // MERGE_MINB: resident merge CTAs per SM the register allocator is held to
 // (4-byte keys: 40 registers, six CTAs -- measured 9.14 -> 9.00 ms at 2^28;
 // the others keep the occupancy they reach unconstrained).
-template <> struct Shape<4, false> { enum { NT = SR_MERGE_NT, IPT = SR_K4_IPT, SORT_NT = SR_SORT_NT, MERGE_MINB = 6 }; };
-template <> struct Shape<4, true>  { enum { NT = SR_MERGE_NT, IPT = SR_K4V_IPT, SORT_NT = SR_SORT_NT, MERGE_MINB = 8 }; };
-template <> struct Shape<8, false> { enum { NT = SR_MERGE_NT, IPT = SR_K8_IPT, SORT_NT = SR_SORT_NT, MERGE_MINB = 4 }; };
-template <> struct Shape<8, true>  { enum { NT = SR_MERGE_NT, IPT = SR_K8V_IPT, SORT_NT = SR_SORT_NT, MERGE_MINB = 4 }; };
+// MERGE4_MINB: the same for the 4-way merge kernel.
+#ifndef SR_MERGE4_MINB4
+#define SR_MERGE4_MINB4 5
+#endif
+template <> struct Shape<4, false> { enum { NT = SR_MERGE_NT, IPT = SR_K4_IPT, SORT_NT = SR_SORT_NT, MERGE_MINB = 6, MERGE4_MINB = SR_MERGE4_MINB4 }; };
+template <> struct Shape<4, true>  { enum { NT = SR_MERGE_NT, IPT = SR_K4V_IPT, SORT_NT = SR_SORT_NT, MERGE_MINB = 8, MERGE4_MINB = 6 }; };
+template <> struct Shape<8, false> { enum { NT = SR_MERGE_NT, IPT = SR_K8_IPT, SORT_NT = SR_SORT_NT, MERGE_MINB = 4, MERGE4_MINB = 4 }; };
+template <> struct Shape<8, true>  { enum { NT = SR_MERGE_NT, IPT = SR_K8V_IPT, SORT_NT = SR_SORT_NT, MERGE_MINB = 4, MERGE4_MINB = 4 }; };
 
 // ------------------------------------------------------------- merge path
 
@@ -224,6 +228,86 @@ __device__ __forceinline__ void serial_merge(const U *s, int a, int a_end, int b
         if (take_a) { ++a; if (a < a_end) ak = s[a]; }
         else        { ++b; if (b < b_end) bk = s[b]; }
     }
+}
+
+// IPT outputs of two stable merges in a row: the first `sw` outputs come from
+// the merge of s[a..a_end) and s[b..b_end), the rest from the merge of
+// s[c..c_end) and s[d..d_end) starting at their first keys.  For the one
+// thread of a 4-way merge tile whose outputs straddle the end of the first
+// pair's merged run.  Loads are guarded like serial_merge's.
+template <typename U, int IPT>
+__device__ __forceinline__ void serial_merge_switch(const U *s, int a, int a_end, int b, int b_end, int sw, int c,
+                                                    int c_end, int d, int d_end, U (&k)[IPT], int (&ix)[IPT]) {
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+        if (i == sw) { a = c; a_end = c_end; b = d; b_end = d_end; }
+        const bool take_a = (b >= b_end) || ((a < a_end) && !(s[b] < s[a]));
+        const int at = take_a ? a : b;
+        k[i] = s[at];
+        ix[i] = at;
+        if (take_a) ++a;
+        else ++b;
+    }
+}
+
+// ------------------------------------------------ bulk copies into shared memory
+//
+// 1-D bulk copies (cp.async.bulk) from this GPU's global memory into the
+// CTA's shared memory, completed on an mbarrier: one thread starts them and
+// every thread waits for the barrier's phase.  Addresses and sizes must be
+// multiples of 16 bytes.
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// One arrival that also announces `bytes` of copies still to land.
+__device__ __forceinline__ void mbar_arrive_expect(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Waits for phase `parity` of the barrier, giving up after `limit` tries
+// (each try itself waits a while in hardware).  Returns whether it completed.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity, int limit) {
+    for (int i = 0; i < limit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// ------------------------------------------------------- merge step schedule
+//
+// After the block sort the runs are one tile long; ceil(log2(tiles)) binary
+// merge levels remain.  With 4-way steps (fan4) each step merges four runs and
+// covers two levels; an odd level count starts with one 2-way step.  Step s
+// covers levels [l0, l0 + nl).
+__host__ __device__ constexpr int merge_step_count(int levels, bool fan4) {
+    return fan4 ? (levels + 1) / 2 : levels;
+}
+__host__ __device__ __forceinline__ void merge_step_levels(int levels, bool fan4, int s, int *l0, int *nl) {
+    if (!fan4) { *l0 = s; *nl = 1; return; }
+    const int odd = levels & 1;
+    if (odd && s == 0) { *l0 = 0; *nl = 1; return; }
+    *l0 = odd + 2 * (s - odd);
+    *nl = 2;
 }
 
 // Sort of a thread's IPT registers.  Keys alone: Batcher's odd-even merge

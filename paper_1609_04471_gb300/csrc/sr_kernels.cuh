@@ -447,22 +447,32 @@ k_block_sort(const typename Key<KT>::T *in_k, const uint32_t *in_v, typename Key
 // taken after a fence) settles the remaining passes from the chunks' extremes.
 enum { PLAN_CHUNK = 2048, PLAN_LEVELS = 11 };   // 2^11 tiles per chunk
 
-// Once every unordered[p] is final: the buffer before each pass (and after
-// the last), so later kernels read one byte instead of recounting flips.
-__device__ __forceinline__ void record_buffers(Ctrl *c, int cur0, int passes) {
+// Whether merge step s (binary levels [l0, l0 + nl)) has any run pair out of
+// order; a step whose levels are all in order is skipped.
+__device__ __forceinline__ bool step_needed(const Ctrl *c, int l0, int nl) {
+    const volatile int *u = c->unordered;
+    return u[l0] != 0 || (nl > 1 && u[l0 + 1] != 0);
+}
+
+// Once every unordered[level] is final: the buffer before each merge step (and
+// after the last), so later kernels read one byte instead of recounting flips.
+__device__ __forceinline__ void record_buffers(Ctrl *c, int cur0, int levels, bool fan4) {
     int cur = cur0;
-    for (int p = 0; p < passes; ++p) {
-        c->src_buf[p] = (signed char)cur;
-        cur ^= (((volatile int *)c->unordered)[p] != 0);
+    const int steps = merge_step_count(levels, fan4);
+    for (int s = 0; s < steps; ++s) {
+        int l0, nl;
+        merge_step_levels(levels, fan4, s, &l0, &nl);
+        c->src_buf[s] = (signed char)cur;
+        cur ^= step_needed(c, l0, nl) ? 1 : 0;
     }
-    c->src_buf[passes] = (signed char)cur;
+    c->src_buf[steps] = (signed char)cur;
 }
 
 template <int KT>
 __global__ void __launch_bounds__(1024)
 k_plan(const typename Key<KT>::U *__restrict__ lo, const typename Key<KT>::U *__restrict__ hi,
        typename Key<KT>::U *__restrict__ chunk_lo, typename Key<KT>::U *__restrict__ chunk_hi,
-       long long n, long long tiles, int passes, int cur0, Ctrl *__restrict__ c) {
+       long long n, long long tiles, int passes, int cur0, int fan4, Ctrl *__restrict__ c) {
     griddep_wait();
     typedef typename Key<KT>::U U;
     if (call_mode(c, n) != MODE_SORT) return;
@@ -505,7 +515,7 @@ k_plan(const typename Key<KT>::U *__restrict__ lo, const typename Key<KT>::U *__
     if (!s_last) return;
     __threadfence();
     if (passes <= PLAN_LEVELS) {
-        if (t == 0) record_buffers(c, cur0, passes);
+        if (t == 0) record_buffers(c, cur0, passes, fan4 != 0);
         return;
     }
     const int chunks = (int)gridDim.x;            // at most PLAN_CHUNK chunks (2^22 tiles)
@@ -531,7 +541,7 @@ k_plan(const typename Key<KT>::U *__restrict__ lo, const typename Key<KT>::U *__
         __syncthreads();
         if (t == 0) c->unordered[p] = (int)s_cnt;
     }
-    if (t == 0) record_buffers(c, cur0, passes);
+    if (t == 0) record_buffers(c, cur0, passes, fan4 != 0);
 }
 
 // Merge-path split of every merge tile boundary of pass p, one group of
@@ -586,14 +596,14 @@ template <int KT>
 __global__ void __launch_bounds__(256)
 k_partition(const typename Key<KT>::T *__restrict__ uk, const typename Key<KT>::T *__restrict__ sk,
             long long n, long long w, int nv, long long nbound, long long *__restrict__ splits,
-            const Ctrl *__restrict__ c, int p, int lg, const typename Key<KT>::U *__restrict__ samp,
-            long long smt) {
+            const Ctrl *__restrict__ c, int step, int l0, int nl, int lg,
+            const typename Key<KT>::U *__restrict__ samp, long long smt) {
     griddep_wait();
     const int lane = threadIdx.x & 31;
     const long long b = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> lg;
     if (b >= nbound) return;                       // uniform across the group
-    if (c->unordered[p] == 0) return;             // also 0 for every pass unless the input needs sorting
-    const int cur = c->src_buf[p];
+    if (!step_needed(c, l0, nl)) return;          // also skipped unless the input needs sorting
+    const int cur = c->src_buf[step];
     const long long sp = merge_split<KT>(cur ? sk : uk, n, w, nv, b, lane, lg, samp ? samp + cur * smt : nullptr);
     if ((lane & ((1 << lg) - 1)) == 0) splits[b] = sp;
 }
@@ -607,6 +617,106 @@ inline int partition_lg(long long nbound) {
     int lg = 5;
     while (lg > 0 && (nbound << lg) > SR_PARTITION_LANES) --lg;
     return lg;
+}
+// Lanes per boundary for k_partition4, whose probes each run two binary
+// searches inside one merge tile: between 1 and 8 lanes, about
+// SR_PARTITION4_LANES in all.
+#ifndef SR_PARTITION4_LANES
+#define SR_PARTITION4_LANES 160000
+#endif
+inline int partition4_lg(long long nbound) {
+    int lg = 3;
+    while (lg > 0 && (nbound << lg) > SR_PARTITION4_LANES) --lg;
+    return lg;
+}
+
+// The end of a merge tile: every thread holds its IPT merged keys (and
+// values) in registers; they go through shared memory (s, sv) so the tile
+// leaves in coalesced (VEC: 16-byte) stores to dst at out0.  The tile's first
+// and last key go to samp[2 * tile], samp[2 * tile + 1] if samp is given.
+template <int KT, int NT, int IPT, bool VALS, bool VEC>
+__device__ __forceinline__ void write_tile(const typename Key<KT>::U (&k)[IPT], const uint32_t (&v)[IPT],
+                                           typename Key<KT>::U *s, uint32_t *sv,
+                                           typename Key<KT>::T *__restrict__ dst_k, uint32_t *__restrict__ dst_v,
+                                           long long out0, int cnt, typename Key<KT>::U *samp, long long tile) {
+    typedef Key<KT> K;
+    typedef typename K::U U;
+    typedef typename K::T T;
+    const int t = threadIdx.x;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+        s[t * IPT + i] = k[i];
+        if (VALS) sv[t * IPT + i] = v[i];
+    }
+    __syncthreads();
+    if (samp && t == 0) {                          // the output tile's first and last key, for the next pass
+        samp[2 * tile] = s[0];
+        samp[2 * tile + 1] = s[cnt - 1];
+    }
+    if (VEC) {
+        // keys before the first 4-key group boundary of the output go one by one
+        const int head = min(cnt, (int)((4 - (out0 & 3)) & 3));
+        if (t < head) {
+            dst_k[out0 + t] = K::unord(s[t]);
+            if (VALS) dst_v[out0 + t] = sv[t];
+        }
+        const int full = (cnt - head) >> 2;
+        if (head == 0) {
+            // the tile starts on a group boundary: 16-byte shared loads as well
+            for (int g = t; g < full; g += NT) {
+                const int j = 4 * g;
+                if (sizeof(T) == 4) {
+                    const uint4 q = *reinterpret_cast<const uint4 *>(s + j);
+                    *reinterpret_cast<uint4 *>(dst_k + out0 + j) =
+                        make_uint4((uint32_t)K::unord((U)q.x), (uint32_t)K::unord((U)q.y),
+                                   (uint32_t)K::unord((U)q.z), (uint32_t)K::unord((U)q.w));
+                } else {
+                    const ulonglong2 q0 = *reinterpret_cast<const ulonglong2 *>(s + j);
+                    const ulonglong2 q1 = *reinterpret_cast<const ulonglong2 *>(s + j + 2);
+                    const unsigned long long e0 = (unsigned long long)K::unord((U)q0.x);
+                    const unsigned long long e1 = (unsigned long long)K::unord((U)q0.y);
+                    const unsigned long long e2 = (unsigned long long)K::unord((U)q1.x);
+                    const unsigned long long e3 = (unsigned long long)K::unord((U)q1.y);
+                    *reinterpret_cast<uint4 *>(dst_k + out0 + j) =
+                        make_uint4((uint32_t)e0, (uint32_t)(e0 >> 32), (uint32_t)e1, (uint32_t)(e1 >> 32));
+                    *reinterpret_cast<uint4 *>(dst_k + out0 + j + 2) =
+                        make_uint4((uint32_t)e2, (uint32_t)(e2 >> 32), (uint32_t)e3, (uint32_t)(e3 >> 32));
+                }
+                if (VALS) *reinterpret_cast<uint4 *>(dst_v + out0 + j) = *reinterpret_cast<const uint4 *>(sv + j);
+            }
+        } else for (int g = t; g < full; g += NT) {
+            const int j = head + 4 * g;
+            if (sizeof(T) == 4) {
+                uint4 q;
+                q.x = (uint32_t)K::unord(s[j + 0]);
+                q.y = (uint32_t)K::unord(s[j + 1]);
+                q.z = (uint32_t)K::unord(s[j + 2]);
+                q.w = (uint32_t)K::unord(s[j + 3]);
+                *reinterpret_cast<uint4 *>(dst_k + out0 + j) = q;
+            } else {
+                const unsigned long long e0 = (unsigned long long)K::unord(s[j + 0]);
+                const unsigned long long e1 = (unsigned long long)K::unord(s[j + 1]);
+                const unsigned long long e2 = (unsigned long long)K::unord(s[j + 2]);
+                const unsigned long long e3 = (unsigned long long)K::unord(s[j + 3]);
+                *reinterpret_cast<uint4 *>(dst_k + out0 + j) =
+                    make_uint4((uint32_t)e0, (uint32_t)(e0 >> 32), (uint32_t)e1, (uint32_t)(e1 >> 32));
+                *reinterpret_cast<uint4 *>(dst_k + out0 + j + 2) =
+                    make_uint4((uint32_t)e2, (uint32_t)(e2 >> 32), (uint32_t)e3, (uint32_t)(e3 >> 32));
+            }
+            if (VALS)
+                *reinterpret_cast<uint4 *>(dst_v + out0 + j) = make_uint4(sv[j], sv[j + 1], sv[j + 2], sv[j + 3]);
+        }
+        for (int i = head + 4 * full + t; i < cnt; i += NT) {
+            dst_k[out0 + i] = K::unord(s[i]);
+            if (VALS) dst_v[out0 + i] = sv[i];
+        }
+    } else {
+        for (int i = t; i < cnt; i += NT) {
+            dst_k[out0 + i] = K::unord(s[i]);
+            if (VALS) dst_v[out0 + i] = sv[i];
+        }
+    }
 }
 
 // Dynamic shared memory that merge_tile needs: NT*IPT + 16 staged keys (and
@@ -728,80 +838,7 @@ __device__ __forceinline__ void merge_tile(const typename Key<KT>::T *__restrict
 #pragma unroll
         for (int i = 0; i < IPT; ++i) v[i] = (diag + i < cnt) ? sv[ix[i]] : 0u;
     }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < IPT; ++i) {
-        s[t * IPT + i] = k[i];
-        if (VALS) sv[t * IPT + i] = v[i];
-    }
-    __syncthreads();
-    if (samp && t == 0) {                          // the output tile's first and last key, for the next pass
-        samp[2 * tile] = s[0];
-        samp[2 * tile + 1] = s[cnt - 1];
-    }
-    if (VEC) {
-        // keys before the first 4-key group boundary of the output go one by one
-        const int head = min(cnt, (int)((4 - (out0 & 3)) & 3));
-        if (t < head) {
-            dst_k[out0 + t] = K::unord(s[t]);
-            if (VALS) dst_v[out0 + t] = sv[t];
-        }
-        const int full = (cnt - head) >> 2;
-        if (head == 0) {
-            // the tile starts on a group boundary: 16-byte shared loads as well
-            for (int g = t; g < full; g += NT) {
-                const int j = 4 * g;
-                if (sizeof(T) == 4) {
-                    const uint4 q = *reinterpret_cast<const uint4 *>(s + j);
-                    *reinterpret_cast<uint4 *>(dst_k + out0 + j) =
-                        make_uint4((uint32_t)K::unord((U)q.x), (uint32_t)K::unord((U)q.y),
-                                   (uint32_t)K::unord((U)q.z), (uint32_t)K::unord((U)q.w));
-                } else {
-                    const ulonglong2 q0 = *reinterpret_cast<const ulonglong2 *>(s + j);
-                    const ulonglong2 q1 = *reinterpret_cast<const ulonglong2 *>(s + j + 2);
-                    const unsigned long long e0 = (unsigned long long)K::unord((U)q0.x);
-                    const unsigned long long e1 = (unsigned long long)K::unord((U)q0.y);
-                    const unsigned long long e2 = (unsigned long long)K::unord((U)q1.x);
-                    const unsigned long long e3 = (unsigned long long)K::unord((U)q1.y);
-                    *reinterpret_cast<uint4 *>(dst_k + out0 + j) =
-                        make_uint4((uint32_t)e0, (uint32_t)(e0 >> 32), (uint32_t)e1, (uint32_t)(e1 >> 32));
-                    *reinterpret_cast<uint4 *>(dst_k + out0 + j + 2) =
-                        make_uint4((uint32_t)e2, (uint32_t)(e2 >> 32), (uint32_t)e3, (uint32_t)(e3 >> 32));
-                }
-                if (VALS) *reinterpret_cast<uint4 *>(dst_v + out0 + j) = *reinterpret_cast<const uint4 *>(sv + j);
-            }
-        } else for (int g = t; g < full; g += NT) {
-            const int j = head + 4 * g;
-            if (sizeof(T) == 4) {
-                uint4 q;
-                q.x = (uint32_t)K::unord(s[j + 0]);
-                q.y = (uint32_t)K::unord(s[j + 1]);
-                q.z = (uint32_t)K::unord(s[j + 2]);
-                q.w = (uint32_t)K::unord(s[j + 3]);
-                *reinterpret_cast<uint4 *>(dst_k + out0 + j) = q;
-            } else {
-                const unsigned long long e0 = (unsigned long long)K::unord(s[j + 0]);
-                const unsigned long long e1 = (unsigned long long)K::unord(s[j + 1]);
-                const unsigned long long e2 = (unsigned long long)K::unord(s[j + 2]);
-                const unsigned long long e3 = (unsigned long long)K::unord(s[j + 3]);
-                *reinterpret_cast<uint4 *>(dst_k + out0 + j) =
-                    make_uint4((uint32_t)e0, (uint32_t)(e0 >> 32), (uint32_t)e1, (uint32_t)(e1 >> 32));
-                *reinterpret_cast<uint4 *>(dst_k + out0 + j + 2) =
-                    make_uint4((uint32_t)e2, (uint32_t)(e2 >> 32), (uint32_t)e3, (uint32_t)(e3 >> 32));
-            }
-            if (VALS)
-                *reinterpret_cast<uint4 *>(dst_v + out0 + j) = make_uint4(sv[j], sv[j + 1], sv[j + 2], sv[j + 3]);
-        }
-        for (int i = head + 4 * full + t; i < cnt; i += NT) {
-            dst_k[out0 + i] = K::unord(s[i]);
-            if (VALS) dst_v[out0 + i] = sv[i];
-        }
-    } else {
-        for (int i = t; i < cnt; i += NT) {
-            dst_k[out0 + i] = K::unord(s[i]);
-            if (VALS) dst_v[out0 + i] = sv[i];
-        }
-    }
+    write_tile<KT, NT, IPT, VALS, VEC>(k, v, s, sv, dst_k, dst_v, out0, cnt, samp, tile);
 }
 
 // One CTA per output tile of NT*IPT keys of merge pass p.  The tile's A and B
@@ -810,19 +847,19 @@ __device__ __forceinline__ void merge_tile(const typename Key<KT>::T *__restrict
 template <int KT, int NT, int IPT, bool VALS, bool VEC>
 __global__ void __launch_bounds__(NT, Shape<sizeof(typename Key<KT>::T), VALS>::MERGE_MINB)
 k_merge(typename Key<KT>::T *uk, uint32_t *uv, typename Key<KT>::T *sk, uint32_t *svb, long long n,
-        long long w, int lgt, const long long *__restrict__ splits, const Ctrl *__restrict__ c, int p,
-        typename Key<KT>::U *__restrict__ samp, long long smt) {
+        long long w, int lgt, const long long *__restrict__ splits, const Ctrl *__restrict__ c, int step,
+        int l0, typename Key<KT>::U *__restrict__ samp, long long smt) {
     griddep_wait();
     typedef Key<KT> K;
     typedef typename K::U U;
     typedef typename K::T T;
     constexpr int NV = NT * IPT;
     constexpr int SV = NV + 16;                    // staged keys, with room for window slack
-    if (c->unordered[p] == 0) return;              // also 0 for every pass unless the input needs sorting
+    if (!step_needed(c, l0, 1)) return;            // also skipped unless the input needs sorting
     extern __shared__ __align__(16) unsigned char smem[];
     U *s = reinterpret_cast<U *>(smem);
     uint32_t *sv = reinterpret_cast<uint32_t *>(s + SV);
-    const int cur = c->src_buf[p];
+    const int cur = c->src_buf[step];
     const long long out0 = (long long)blockIdx.x * NV;
     const long long out1 = min(out0 + NV, n);
     const long long pb = (long long)(((unsigned long long)blockIdx.x >> lgt) << lgt) * NV;
@@ -837,12 +874,465 @@ k_merge(typename Key<KT>::T *uk, uint32_t *uv, typename Key<KT>::T *sk, uint32_t
                                        (long long)blockIdx.x);
 }
 
+// ------------------------------------------------------------ 4-way merge steps
+//
+// A 4-way step merges every group of four consecutive runs A, B, C, D of w
+// keys (the group at the end of the array may hold fewer or shorter runs) into
+// one run: merge(merge(A, B), merge(C, D)), with A before B before C before D
+// on equal keys -- the stable merge of the four runs (policy e1 of Section 3
+// taken two rounds at a time), reading and writing every key once where two
+// 2-way passes would do it twice.  The splits come from two launches:
+// k_partition over the pairs (A, B) and (C, D) gives the 2-way split of every
+// merge tile of the merged pairs AB and CD (which are never written), and
+// k_partition4 runs, for every output tile boundary, a merge-path search of AB
+// against CD whose probes read keys of AB and CD through those 2-way splits,
+// then records where each of A, B, C and D starts for the tile.
+
+// A merged pair P = merge(X, Y) of adjacent runs X = [x_beg, x_end) and
+// Y = [x_end, y_end), seen through the 2-way splits of its merge tiles:
+// split1[t0 + j] is where P's tile j (outputs j*nv ..) starts in X.
+struct PairView {
+    long long x_beg, x_end, y_end, t0, len;
+};
+
+__device__ __forceinline__ PairView pair_view(long long x_beg, long long x_end, long long y_end, int nv) {
+    PairView P;
+    P.x_beg = x_beg;
+    P.x_end = x_end;
+    P.y_end = y_end;
+    P.t0 = x_beg / nv;
+    P.len = y_end - x_beg;
+    return P;
+}
+
+// The stretches X[xs, xe) and Y[ys, ye) that tile j of P (j * nv < P.len)
+// is merged from.
+__device__ __forceinline__ void pair_tile(const long long *__restrict__ split1, const PairView &P, int nv,
+                                          long long j, long long &xs, long long &xe, long long &ys,
+                                          long long &ye) {
+    xs = split1[P.t0 + j];
+    const long long o1 = min((j + 1) * (long long)nv, P.len);
+    xe = o1 == P.len ? P.x_end : split1[P.t0 + j + 1];
+    ys = P.x_end + j * (long long)nv - (xs - P.x_beg);
+    ye = P.x_end + o1 - (xe - P.x_beg);
+}
+
+// The merge-path test of a 4-way boundary at m: whether AB[m] goes before
+// CD[d - 1 - m] (!(CD[d-1-m] < AB[m])).  The two keys' inner searches run in
+// one loop so their loads are in flight together.
+template <int KT>
+__device__ __forceinline__ bool probe_ab_cd(const typename Key<KT>::T *__restrict__ src,
+                                            const long long *__restrict__ split1, const PairView &AB,
+                                            const PairView &CD, int nv, long long d, long long m) {
+    typedef Key<KT> K;
+    typedef typename K::U U;
+    const long long m2 = d - 1 - m;
+    const long long j1 = m / nv, j2 = m2 / nv;
+    long long xs1, xe1, ys1, ye1, xs2, xe2, ys2, ye2;
+    pair_tile(split1, AB, nv, j1, xs1, xe1, ys1, ye1);
+    pair_tile(split1, CD, nv, j2, xs2, xe2, ys2, ye2);
+    const int r1 = (int)(m - j1 * nv), r2 = (int)(m2 - j2 * nv);
+    const int ny1 = (int)(ye1 - ys1), ny2 = (int)(ye2 - ys2);
+    int lo1 = max(0, r1 + 1 - ny1), hi1 = min(r1 + 1, (int)(xe1 - xs1));
+    int lo2 = max(0, r2 + 1 - ny2), hi2 = min(r2 + 1, (int)(xe2 - xs2));
+    while (lo1 < hi1 || lo2 < hi2) {
+        if (lo1 < hi1) {
+            const int mid = (lo1 + hi1) >> 1;
+            if (!(K::ord(src[ys1 + r1 - mid]) < K::ord(src[xs1 + mid]))) lo1 = mid + 1;
+            else hi1 = mid;
+        }
+        if (lo2 < hi2) {
+            const int mid = (lo2 + hi2) >> 1;
+            if (!(K::ord(src[ys2 + r2 - mid]) < K::ord(src[xs2 + mid]))) lo2 = mid + 1;
+            else hi2 = mid;
+        }
+    }
+    U a = 0, c = 0;                                // AB[m] and CD[m2]: the later of the two last keys taken
+    if (lo1 > 0) a = K::ord(src[xs1 + lo1 - 1]);
+    if (r1 - lo1 >= 0) {
+        const U y = K::ord(src[ys1 + r1 - lo1]);
+        a = a < y ? y : a;
+    }
+    if (lo2 > 0) c = K::ord(src[xs2 + lo2 - 1]);
+    if (r2 - lo2 >= 0) {
+        const U y = K::ord(src[ys2 + r2 - lo2]);
+        c = c < y ? y : c;
+    }
+    return !(c < a);
+}
+
+// How many X keys are among the first x outputs of P (0 <= x <= P.len).
+template <int KT>
+__device__ __forceinline__ long long pair_split(const typename Key<KT>::T *__restrict__ src,
+                                                const long long *__restrict__ split1, const PairView &P, int nv,
+                                                long long x) {
+    typedef Key<KT> K;
+    if (x >= P.len) return P.x_end - P.x_beg;
+    const long long j = x / nv;
+    long long xs, xe, ys, ye;
+    pair_tile(split1, P, nv, j, xs, xe, ys, ye);
+    const int r = (int)(x - j * nv);
+    const int nx = (int)(xe - xs), ny = (int)(ye - ys);
+    int lo = max(0, r - ny), hi = min(r, nx);
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (!(K::ord(src[ys + r - 1 - mid]) < K::ord(src[xs + mid]))) lo = mid + 1;
+        else hi = mid;
+    }
+    return xs + lo - P.x_beg;
+}
+
+// First and last key images of P's tile j (j * nv < P.len).
+template <int KT>
+__device__ __forceinline__ typename Key<KT>::U pair_first(const typename Key<KT>::T *__restrict__ src,
+                                                          const long long *__restrict__ split1, const PairView &P,
+                                                          int nv, long long j) {
+    typedef Key<KT> K;
+    long long xs, xe, ys, ye;
+    pair_tile(split1, P, nv, j, xs, xe, ys, ye);
+    if (xs < xe && (ys >= ye || !(K::ord(src[ys]) < K::ord(src[xs])))) return K::ord(src[xs]);
+    return K::ord(src[ys]);
+}
+template <int KT>
+__device__ __forceinline__ typename Key<KT>::U pair_last(const typename Key<KT>::T *__restrict__ src,
+                                                         const long long *__restrict__ split1, const PairView &P,
+                                                         int nv, long long j) {
+    typedef Key<KT> K;
+    typedef typename K::U U;
+    long long xs, xe, ys, ye;
+    pair_tile(split1, P, nv, j, xs, xe, ys, ye);
+    U v = 0;
+    if (xe > xs) v = K::ord(src[xe - 1]);
+    if (ye > ys) {
+        const U y = K::ord(src[ye - 1]);
+        v = v < y ? y : v;
+    }
+    return v;
+}
+
+// 4-way splits of every output tile boundary of step `step` (runs of w keys,
+// groups of 4w), a group of 2^lg lanes per boundary: split4[4b + i] is where
+// tile b's share of run i (A, B, C, D) starts in the source buffer.
+template <int KT>
+__global__ void __launch_bounds__(256)
+k_partition4(const typename Key<KT>::T *__restrict__ uk, const typename Key<KT>::T *__restrict__ sk,
+             long long n, long long w, int nv, long long nbound, const long long *__restrict__ split1,
+             long long *__restrict__ split4, const Ctrl *__restrict__ c, int step, int l0, int lg) {
+    griddep_wait();
+    const int lane = threadIdx.x & 31;
+    const long long b = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> lg;
+    if (b >= nbound) return;                       // uniform across the group
+    if (!step_needed(c, l0, 2)) return;
+    const bool leader = (lane & ((1 << lg) - 1)) == 0;
+    if (b * (long long)nv >= n) {                  // the end of the array: never read as a tile start
+        if (leader)
+            for (int i = 0; i < 4; ++i) split4[4 * b + i] = n;
+        return;
+    }
+    const typename Key<KT>::T *src = c->src_buf[step] ? sk : uk;
+    const long long out = b * (long long)nv;
+    const long long G0 = (out / (4 * w)) * (4 * w);
+    long long e[5];                                // A = [e0, e1), B = [e1, e2), C = [e2, e3), D = [e3, e4)
+#pragma unroll
+    for (int i = 0; i < 5; ++i) e[i] = min(G0 + i * w, n);
+    const PairView AB = pair_view(e[0], e[1], e[2], nv), CD = pair_view(e[2], e[3], e[4], nv);
+    const long long d = out - G0;                  // a multiple of nv
+    long long lo = max(0ll, d - CD.len), hi = min(d, AB.len);
+    if (hi > lo) {
+        // coarse: at m = j * nv, AB[m] is the first key of AB's tile j and
+        // CD[d - 1 - m] the last key of CD's (full) tile d / nv - j - 1
+        const long long jlo = (lo + nv - 1) / nv, jhi = (hi - 1) / nv, dj = d / nv;
+        if (jlo <= jhi) {
+            const long long jt = group_search(jlo, jhi + 1, lane, lg, [&](long long j) {
+                return !(pair_last<KT>(src, split1, CD, nv, dj - j - 1) < pair_first<KT>(src, split1, AB, nv, j));
+            });
+            if (jt > jlo) lo = max(lo, (jt - 1) * nv + 1);
+            if (jt <= jhi) hi = min(hi, jt * nv);
+        }
+        // fine: AB outputs among the first d outputs of merge(AB, CD)
+        lo = group_search(lo, hi, lane, lg,
+                          [&](long long m) { return probe_ab_cd<KT>(src, split1, AB, CD, nv, d, m); });
+    }
+    if (leader) {
+        const long long x = lo;
+        const long long a = pair_split<KT>(src, split1, AB, nv, x);
+        const long long cc = pair_split<KT>(src, split1, CD, nv, d - x);
+        split4[4 * b + 0] = e[0] + a;
+        split4[4 * b + 1] = e[1] + (x - a);
+        split4[4 * b + 2] = e[2] + cc;
+        split4[4 * b + 3] = e[3] + (d - x - cc);
+    }
+}
+
+// One of four values by a run-time index, without indexing a local array
+// (which would live in local memory).
+template <typename V>
+__device__ __forceinline__ V pick4(int i, V a, V b, V c, V d) {
+    return i == 0 ? a : i == 1 ? b : i == 2 ? c : d;
+}
+
+// Staging modes of a 4-way merge tile's four windows into shared memory.
+enum { STAGE_SCALAR = 0, STAGE_VEC = 1, STAGE_BULK = 2 };
+
+// Staged key capacity of a 4-way merge tile: NV keys plus, per window, up to
+// 3 keys before its first and after its last 4-key group boundary.
+template <int NV> struct Merge4Cap { enum { SV = NV + 32 }; };
+
+// Dynamic shared memory of k_merge4: the staged keys (and values), plus the
+// slack the one-load merge step reads into.
+template <typename U, int NT, int IPT, bool VALS>
+constexpr size_t merge4_smem() {
+    return (size_t)Merge4Cap<NT * IPT>::SV * (sizeof(U) + (VALS ? 4 : 0)) + (size_t)(IPT + 8) * sizeof(U);
+}
+
+// Longest wait for a tile's bulk copies: tries of mbarrier.try_wait (each
+// waits in hardware for a while); a tile that gives up reports
+// SR_ERR_TIMEOUT in `status`.
+enum { BULK_WAIT_TRIES = 1 << 22 };
+
+// One output tile of a 4-way step: outputs [out0, out0 + cnt) of the stable
+// merge of A = src[beg0, beg0 + len0), B, C and D likewise (len0 + .. + len3 =
+// cnt), written to dst at out0.  The four windows are staged in shared memory
+// (STAGE_VEC: 4-key groups by 16-byte loads through registers; STAGE_BULK:
+// the same groups by 1-D bulk copies that one thread starts, completed on an
+// mbarrier, then turned into order images in place; STAGE_SCALAR: one key at a
+// time, for arrays that are not 16-byte aligned).  Level 1 merges A with B and
+// C with D into [AB | CD] in registers, each thread IPT outputs (the thread
+// whose outputs cross the end of AB finishes with the start of CD); level 2
+// merges AB with CD.
+template <int KT, int NT, int IPT, bool VALS, int STAGE>
+__device__ __forceinline__ void merge_tile4(const typename Key<KT>::T *__restrict__ src_k,
+                                            typename Key<KT>::T *__restrict__ dst_k,
+                                            const uint32_t *__restrict__ src_v, uint32_t *__restrict__ dst_v,
+                                            long long n, long long out0, int cnt, const long long (&beg)[4],
+                                            const int (&len)[4], typename Key<KT>::U *s, uint32_t *sv,
+                                            unsigned long long *bar, int *status, typename Key<KT>::U *samp,
+                                            long long tile) {
+    typedef Key<KT> K;
+    typedef typename K::U U;
+    typedef typename K::T T;
+    constexpr int NV = NT * IPT;
+    constexpr int SV = Merge4Cap<NV>::SV;
+    const int t = threadIdx.x;
+    int pos[4];                                    // staged position of each window's first key
+    if (STAGE == STAGE_SCALAR) {
+        int q = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) { pos[i] = q; q += len[i]; }
+        for (int j = t; j < cnt; j += NT) {
+            const int i = j < pos[1] ? 0 : j < pos[2] ? 1 : j < pos[3] ? 2 : 3;
+            const long long g = pick4(i, beg[0], beg[1], beg[2], beg[3]) + (j - pick4(i, pos[0], pos[1], pos[2], pos[3]));
+            s[j] = K::ord(src_k[g]);
+            if (VALS) sv[j] = src_v[g];
+        }
+    } else {
+        // window i as whole 4-key groups [g0[i], g0[i] + 4 ng[i]); group q of
+        // the tile lands at s + 4 q
+        long long g0[4];
+        int first[5];                              // first group of each window
+        first[0] = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            g0[i] = beg[i] & ~3ll;
+            const int ng = len[i] > 0 ? (int)((((beg[i] + len[i] + 3) & ~3ll) - g0[i]) >> 2) : 0;
+            first[i + 1] = first[i] + ng;
+            pos[i] = 4 * first[i] + (int)(beg[i] - g0[i]);
+        }
+        const int groups = first[4];
+        if (STAGE == STAGE_VEC) {
+            constexpr int KMAX = (SV / 4 + NT - 1) / NT;
+            U r[KMAX][4];
+            uint4 rv[VALS ? KMAX : 1];
+#pragma unroll
+            for (int kk = 0; kk < KMAX; ++kk) {
+                const int g = t + kk * NT;
+                if (g < groups) {
+                    const int i = g < first[1] ? 0 : g < first[2] ? 1 : g < first[3] ? 2 : 3;
+                    const long long gb = pick4(i, g0[0], g0[1], g0[2], g0[3]) +
+                                         4ll * (g - pick4(i, first[0], first[1], first[2], first[3]));
+                    if (gb + 4 <= n) {
+                        if (sizeof(T) == 4) {
+                            const uint4 q = *reinterpret_cast<const uint4 *>(src_k + gb);
+                            r[kk][0] = (U)q.x; r[kk][1] = (U)q.y; r[kk][2] = (U)q.z; r[kk][3] = (U)q.w;
+                        } else {
+                            const uint4 q0 = *reinterpret_cast<const uint4 *>(src_k + gb);
+                            const uint4 q1 = *reinterpret_cast<const uint4 *>(src_k + gb + 2);
+                            r[kk][0] = (U)(((unsigned long long)q0.y << 32) | q0.x);
+                            r[kk][1] = (U)(((unsigned long long)q0.w << 32) | q0.z);
+                            r[kk][2] = (U)(((unsigned long long)q1.y << 32) | q1.x);
+                            r[kk][3] = (U)(((unsigned long long)q1.w << 32) | q1.z);
+                        }
+                        if (VALS) rv[kk] = *reinterpret_cast<const uint4 *>(src_v + gb);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) r[kk][e] = (gb + e < n) ? (U)src_k[gb + e] : U(0);
+                        if (VALS) {
+                            rv[kk].x = (gb + 0 < n) ? src_v[gb + 0] : 0u;
+                            rv[kk].y = (gb + 1 < n) ? src_v[gb + 1] : 0u;
+                            rv[kk].z = (gb + 2 < n) ? src_v[gb + 2] : 0u;
+                            rv[kk].w = (gb + 3 < n) ? src_v[gb + 3] : 0u;
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int kk = 0; kk < KMAX; ++kk) {
+                const int g = t + kk * NT;
+                if (g < groups) {
+                    if (sizeof(U) == 4) {
+                        *reinterpret_cast<uint4 *>(s + 4 * g) =
+                            make_uint4((uint32_t)K::ord((T)r[kk][0]), (uint32_t)K::ord((T)r[kk][1]),
+                                       (uint32_t)K::ord((T)r[kk][2]), (uint32_t)K::ord((T)r[kk][3]));
+                    } else {
+                        *reinterpret_cast<ulonglong2 *>(s + 4 * g) = make_ulonglong2(
+                            (unsigned long long)K::ord((T)r[kk][0]), (unsigned long long)K::ord((T)r[kk][1]));
+                        *reinterpret_cast<ulonglong2 *>(s + 4 * g + 2) = make_ulonglong2(
+                            (unsigned long long)K::ord((T)r[kk][2]), (unsigned long long)K::ord((T)r[kk][3]));
+                    }
+                    if (VALS) *reinterpret_cast<uint4 *>(sv + 4 * g) = rv[kk];
+                }
+            }
+        } else {
+            // bulk copies of every whole 16-byte stretch below n4; the few keys
+            // of a window past the array's last 16-byte boundary by plain loads
+            const long long n4 = n & ~3ll;
+            if (t == 0) mbar_init(bar, 1);
+            __syncthreads();
+            if (t == 0) {
+                unsigned bytes = 0;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const long long ge = min(g0[i] + 4ll * (first[i + 1] - first[i]), n4);
+                    if (ge > g0[i]) bytes += (unsigned)((ge - g0[i]) * (sizeof(T) + (VALS ? 4 : 0)));
+                }
+                mbar_arrive_expect(bar, bytes);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const long long ge = min(g0[i] + 4ll * (first[i + 1] - first[i]), n4);
+                    if (ge > g0[i]) {
+                        bulk_copy_g2s(s + 4 * first[i], src_k + g0[i], (unsigned)((ge - g0[i]) * sizeof(T)), bar);
+                        if (VALS) bulk_copy_g2s(sv + 4 * first[i], src_v + g0[i], (unsigned)((ge - g0[i]) * 4), bar);
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const long long e = beg[i] + len[i];
+                if (len[i] > 0 && e > n4) {
+                    const long long from = max(n4, g0[i]);
+                    if (t < e - from) {
+                        const long long g = from + t;
+                        s[4 * first[i] + (g - g0[i])] = (U)src_k[g];
+                        if (VALS) sv[4 * first[i] + (g - g0[i])] = src_v[g];
+                    }
+                }
+            }
+            const bool done = mbar_wait_bounded(bar, 0, BULK_WAIT_TRIES);
+            if (!__syncthreads_and(done)) {
+                if (t == 0 && status) atomicExch(status, (int)SR_ERR_TIMEOUT);
+                mbar_wait_bounded(bar, 0, BULK_WAIT_TRIES);   // copies still in flight must land first
+                return;
+            }
+            if (KT != SR_KEY_U32 && KT != SR_KEY_U64) {          // raw keys -> order images, in place
+                for (int g = t; g < groups; g += NT) {
+                    if (sizeof(U) == 4) {
+                        uint4 q = *reinterpret_cast<uint4 *>(s + 4 * g);
+                        q.x = (uint32_t)K::ord((T)q.x); q.y = (uint32_t)K::ord((T)q.y);
+                        q.z = (uint32_t)K::ord((T)q.z); q.w = (uint32_t)K::ord((T)q.w);
+                        *reinterpret_cast<uint4 *>(s + 4 * g) = q;
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) s[4 * g + e] = K::ord((T)s[4 * g + e]);
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // level 1: [AB | CD], IPT outputs per thread
+    const int lab = len[0] + len[1];
+    U k[IPT];
+    int ix[IPT];
+    {
+        const int o = min(t * IPT, cnt);
+        if (o + IPT <= lab) {
+            const int sp = merge_path(s + pos[0], len[0], s + pos[1], len[1], o);
+            serial_merge_slack<U, IPT>(s, pos[0] + sp, pos[0] + len[0], pos[1] + o - sp, pos[1] + len[1], k, ix);
+        } else if (o >= lab) {
+            const int oc = o - lab;
+            const int sp = merge_path(s + pos[2], len[2], s + pos[3], len[3], oc);
+            serial_merge_slack<U, IPT>(s, pos[2] + sp, pos[2] + len[2], pos[3] + oc - sp, pos[3] + len[3], k, ix);
+        } else {
+            const int sp = merge_path(s + pos[0], len[0], s + pos[1], len[1], o);
+            serial_merge_switch<U, IPT>(s, pos[0] + sp, pos[0] + len[0], pos[1] + o - sp, pos[1] + len[1], lab - o,
+                                        pos[2], pos[2] + len[2], pos[3], pos[3] + len[3], k, ix);
+        }
+    }
+    uint32_t v[IPT];
+    if (VALS) {
+#pragma unroll
+        for (int i = 0; i < IPT; ++i) v[i] = sv[ix[i]];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+        s[t * IPT + i] = k[i];
+        if (VALS) sv[t * IPT + i] = v[i];
+    }
+    __syncthreads();
+    // level 2: AB = s[0, lab) with CD = s[lab, cnt)
+    const int diag = min(t * IPT, cnt);
+    const int sp = merge_path(s, lab, s + lab, cnt - lab, diag);
+    serial_merge_slack<U, IPT>(s, sp, lab, lab + diag - sp, cnt, k, ix);
+    if (VALS) {
+#pragma unroll
+        for (int i = 0; i < IPT; ++i) v[i] = sv[ix[i]];
+    }
+    write_tile<KT, NT, IPT, VALS, STAGE != STAGE_SCALAR>(k, v, s, sv, dst_k, dst_v, out0, cnt, samp, tile);
+}
+
+// One CTA per output tile of NT*IPT keys of 4-way step `step` (runs of w
+// keys): the tile's windows of A, B, C and D come from split4 (the run ends
+// for a group's last tile).
+template <int KT, int NT, int IPT, bool VALS, int STAGE>
+__global__ void __launch_bounds__(NT, Shape<sizeof(typename Key<KT>::T), VALS>::MERGE4_MINB)
+k_merge4(typename Key<KT>::T *uk, uint32_t *uv, typename Key<KT>::T *sk, uint32_t *svb, long long n,
+         long long w, const long long *__restrict__ split4, const Ctrl *__restrict__ c, int step, int l0,
+         typename Key<KT>::U *__restrict__ samp, long long smt, int *status) {
+    griddep_wait();
+    typedef Key<KT> K;
+    typedef typename K::U U;
+    constexpr int NV = NT * IPT;
+    if (!step_needed(c, l0, 2)) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned long long bar;
+    U *s = reinterpret_cast<U *>(smem);
+    uint32_t *sv = reinterpret_cast<uint32_t *>(s + Merge4Cap<NV>::SV);
+    const int cur = c->src_buf[step];
+    const long long b = blockIdx.x;
+    const long long out0 = b * NV;
+    const long long out1 = min(out0 + NV, n);
+    const long long G0 = (out0 / (4 * w)) * (4 * w);
+    const bool last = out1 == min(G0 + 4 * w, n);   // the group's last tile ends at its runs' ends
+    long long beg[4];
+    int len[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        beg[i] = split4[4 * b + i];
+        const long long end = last ? min(G0 + (i + 1) * w, n) : split4[4 * (b + 1) + i];
+        len[i] = (int)(end - beg[i]);
+    }
+    merge_tile4<KT, NT, IPT, VALS, STAGE>(cur ? sk : uk, cur ? uk : sk, cur ? svb : uv, cur ? uv : svb, n, out0,
+                                          (int)(out1 - out0), beg, len, s, sv, &bar, status,
+                                          samp ? samp + (1 - cur) * smt : nullptr, b);
+}
+
 template <int KT, bool VALS>
 __global__ void k_copy_back(typename Key<KT>::T *uk, uint32_t *uv, const typename Key<KT>::T *sk,
-                            const uint32_t *svb, long long n, const Ctrl *__restrict__ c, int passes) {
+                            const uint32_t *svb, long long n, const Ctrl *__restrict__ c, int steps) {
     griddep_wait();
     if (call_mode(c, n) != MODE_SORT) return;
-    if (c->src_buf[passes] == 0) return;
+    if (c->src_buf[steps] == 0) return;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         uk[i] = sk[i];

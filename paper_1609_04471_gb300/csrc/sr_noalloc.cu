@@ -36,21 +36,24 @@
 namespace sr {
 namespace {
 
-// Scratch for the largest n of the widest key type; PlainSort lays it out as
-// [control block | tile extremes for the pass planner | split table |
-// merge-tile samples | key buffer].
-// (the same arithmetic as PlainSort's constructor, at compile time; every call
-// checks its own layout against this size).
-constexpr size_t up256(size_t x) { return (x + 255) / 256 * 256; }
-constexpr long long kTileKeys64 = (long long)Shape<8, false>::SORT_NT * Shape<8, false>::IPT;
-constexpr long long kTiles64 = (SR_NOALLOC_MAX_KEYS + kTileKeys64 - 1) / kTileKeys64;
-constexpr long long kMergeTile64 = (long long)Shape<8, false>::NT * Shape<8, false>::IPT;
-constexpr long long kMTiles64 = (SR_NOALLOC_MAX_KEYS + kMergeTile64 - 1) / kMergeTile64;
-constexpr size_t kScratchBytes = up256(sizeof(Ctrl)) +
-                                 up256((size_t)(2 * kTiles64 + 2 * ((kTiles64 + 1) / 2) + 2) * 8) +
-                                 up256((size_t)(kMTiles64 + 1) * 8) +
-                                 (SR_SPLIT_SAMPLES ? up256((size_t)(4 * kMTiles64) * 8) : 0) +
-                                 up256((size_t)SR_NOALLOC_MAX_KEYS * 8);
+// Scratch for the largest n of any key type under either merge fan-in:
+// PlainSort's own layout function (control block, tile extremes for the pass
+// planner, split tables, merge-tile samples, key buffer) evaluated at compile
+// time, so a layout that outgrows the array fails the build.
+template <int KT> constexpr size_t plain_bytes(bool fan4) {
+    return PlainSort<KT, false>::layout(SR_NOALLOC_MAX_KEYS, false, fan4).bytes;
+}
+constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
+constexpr size_t kScratchBytes =
+    cmax(cmax(cmax(plain_bytes<SR_KEY_I32>(true), plain_bytes<SR_KEY_I32>(false)),
+              cmax(plain_bytes<SR_KEY_U32>(true), plain_bytes<SR_KEY_U32>(false))),
+         cmax(cmax(cmax(plain_bytes<SR_KEY_F32>(true), plain_bytes<SR_KEY_F32>(false)),
+                   cmax(plain_bytes<SR_KEY_U64>(true), plain_bytes<SR_KEY_U64>(false))),
+              cmax(plain_bytes<SR_KEY_I64>(true), plain_bytes<SR_KEY_I64>(false))));
+static_assert(plain_bytes<SR_KEY_I32>(true) <= kScratchBytes && plain_bytes<SR_KEY_U64>(true) <= kScratchBytes &&
+                  plain_bytes<SR_KEY_I64>(false) <= kScratchBytes,
+              "every key type's layout at SR_NOALLOC_MAX_KEYS fits the fixed scratch");
+static_assert(kScratchBytes <= (size_t)16 << 20, "the fixed scratch stays modest");
 
 // The scratch itself.  In host code this name is only a host-side stand-in
 // for the device symbol; host code must use the address from
@@ -87,7 +90,7 @@ template <int KT>
 sr_status noalloc_impl(void *d_keys, size_t n, cudaStream_t s, unsigned char *base) {
     typedef PlainSort<KT, false> PS;
     const PS plan(n);
-    if (plan.bytes > kScratchBytes) return SR_ERR_INVALID_ARG;
+    if (plan.bytes > kScratchBytes) return SR_ERR_INTERNAL;      // excluded at compile time
     return plan.launch((typename PS::T *)d_keys, nullptr, base, s);
 }
 

@@ -15,15 +15,20 @@
 //   k_block_sort  tiles of SORT_NT*IPT keys sorted in shared memory (ascending
 //                 tiles kept, strictly descending tiles reversed); records each
 //                 tile's smallest and largest key.
-//   k_plan        which merge passes have any run pair out of order.
-//   per pass p    k_partition (merge-path splits of every output tile) and
-//                 k_merge (policy e1); passes with every pair in order skip.
-//                 The block sort and every merge record the first and last
-//                 key of each merge tile they write; the next pass's split
-//                 search runs over those samples first and reads keys only
-//                 within one tile.
-//   k_copy_back   if skipped passes left the result in scratch, copy it home.
+//   k_plan        which binary merge levels have any run pair out of order.
+//   per step s    4-way steps (two levels each; an odd level count starts
+//                 with one 2-way step): k_partition (2-way merge-path splits
+//                 of every merge tile of the merged pairs), k_partition4
+//                 (4-way splits of every output tile) and k_merge4; a 2-way
+//                 step is k_partition and k_merge (policy e1).  Steps whose
+//                 levels have every pair in order skip.  The block sort and
+//                 every merge record the first and last key of each merge
+//                 tile they write; the next step's split search runs over
+//                 those samples first and reads keys only within one tile.
+//   k_copy_back   if skipped steps left the result in scratch, copy it home.
 #pragma once
+
+#include <cstdlib>
 
 #include "sr_device.cuh"
 #include "sr_kernels.cuh"
@@ -42,49 +47,112 @@ template <int KT, bool VALS> struct PlainSort {
     enum { LG_TS_NV = TS / NV == 1 ? 0 : TS / NV == 2 ? 1 : TS / NV == 4 ? 2 : TS / NV == 8 ? 3 : -1 };
     static_assert(LG_TS_NV >= 0, "merge tiles per sort tile must be a power of two up to 8");
 
+    // Where each part of a call's scratch lies (byte offsets) and its size;
+    // a compile-time function of n so that a fixed scratch area can be sized
+    // and checked at build time.
+    struct Layout {
+        long long n, tiles, mtiles, rtiles, rem_dmax;
+        int levels, steps;
+        bool rem;
+        size_t off_ctrl, off_plan, off_split, off_split4, off_samp, off_keys, off_vals;
+        size_t off_rem_buck, off_rem_bound, off_rem_scount, off_rem_bcount, off_rem_blk, bytes;
+    };
+    static constexpr size_t up256(size_t x) { return (x + 255) / 256 * 256; }
+    static constexpr int clog2(unsigned long long x) {
+        int r = 0;
+        while ((1ull << r) < x) ++r;
+        return r;
+    }
+    static constexpr Layout layout(long long n_, bool rem_, bool fan4_) {
+        Layout L{};
+        L.n = n_;
+        L.tiles = (n_ + TS - 1) / TS;
+        L.mtiles = (n_ + NV - 1) / NV;
+        L.levels = clog2((unsigned long long)(L.tiles > 0 ? L.tiles : 1));
+        L.steps = merge_step_count(L.levels, fan4_);
+        const bool merging = L.levels > 0;
+        L.off_ctrl = 0;
+        L.off_plan = up256(sizeof(Ctrl));
+        const size_t plan_bytes = up256((size_t)(2 * L.tiles + 2 * ((L.tiles + 1) / 2) + 2) * sizeof(U));
+        L.off_split = L.off_plan + plan_bytes;
+        L.off_split4 = L.off_split + up256((size_t)(L.mtiles + 1) * 8);
+        const size_t split4_bytes = fan4_ && L.levels > 1 ? up256((size_t)(L.mtiles + 1) * 32) : 0;
+        L.off_samp = L.off_split4 + split4_bytes;
+        // tile samples: one set per buffer (the caller's, the scratch copy)
+        L.off_keys = L.off_samp + (SR_SPLIT_SAMPLES && merging ? up256((size_t)(4 * L.mtiles) * sizeof(U)) : 0);
+        const size_t kb = merging ? up256((size_t)n_ * sizeof(T)) : 0;
+        L.off_vals = L.off_keys + kb;
+        const size_t vb = (VALS && merging) ? up256((size_t)n_ * 4) : 0;
+        L.bytes = L.off_vals + vb;
+        L.rem = rem_ && !VALS && L.tiles >= REM_MIN_TILES && merging;
+        if (L.rem) {
+            L.rem_dmax = n_ / 32;
+            L.rtiles = (n_ + RT - 1) / RT;
+            // the buckets follow the key buffer directly: one index space for the merge
+            L.off_rem_buck = L.off_keys + kb;
+            L.off_rem_bound = L.off_rem_buck + up256((size_t)L.rtiles * REM_CAP * sizeof(T));
+            L.off_rem_scount = L.off_rem_bound + up256((size_t)(L.rtiles + 1) * sizeof(U));
+            L.off_rem_bcount = L.off_rem_scount + up256((size_t)L.rtiles * 4);
+            L.off_rem_blk = L.off_rem_bcount + up256((size_t)L.rtiles * 4);
+            L.bytes = L.off_rem_blk + up256((size_t)(L.rtiles + 1) * 8);
+        }
+        return L;
+    }
+
     long long n = 0, tiles = 0, mtiles = 0;
-    int passes = 0;
+    int passes = 0;                    // binary merge levels after the block sort
+    int steps = 0;                     // merge steps that cover them
+    bool fan4 = true;                  // 4-way steps
     bool rem = false;                  // the few-displaced-keys path is queued
     long long rem_dmax = 0;            // most descents for which it is tried
     long long rtiles = 0;              // its tiles of RT keys
+    int sms = 152;                     // SMs of the device (grid sizes of grid-stride kernels)
+    int *status = nullptr;             // device status word for errors found on the device
     enum { RT = REM_TNT * IPT, RMIPT = IPT + (REM_CAP + REM_TNT - 1) / REM_TNT };
     static_assert((SNT * IPT) % RT == 0, "the scan's tile holds whole tiles of the displaced-keys path");
     static_assert(REM_TNT * RMIPT >= RT + REM_CAP, "a tile's block fits one merge tile");
     // byte offsets inside the scratch area
-    size_t off_ctrl = 0, off_plan = 0, off_split = 0, off_samp = 0, off_keys = 0, off_vals = 0, bytes = 0;
+    size_t off_ctrl = 0, off_plan = 0, off_split = 0, off_split4 = 0, off_samp = 0, off_keys = 0, off_vals = 0,
+           bytes = 0;
     size_t off_rem_buck = 0, off_rem_bound = 0, off_rem_scount = 0, off_rem_bcount = 0, off_rem_blk = 0;
 
     // rem_: queue the few-displaced-keys path (keys only, at least
     // REM_MIN_TILES sort tiles).  Its tiles are RT = REM_TNT x IPT keys.
+    // fan4_: merge four runs per step (else two).
     enum { REM_MIN_TILES = 16 };
-    explicit PlainSort(size_t n_, bool rem_ = false) {
-        n = (long long)n_;
-        tiles = (n + TS - 1) / TS;
-        mtiles = (n + NV - 1) / NV;
-        passes = ceil_log2((unsigned long long)(tiles > 0 ? tiles : 1));
-        off_ctrl = 0;
-        off_plan = align_up(sizeof(Ctrl), 256);
-        const size_t plan_bytes = align_up((size_t)(2 * tiles + 2 * ((tiles + 1) / 2) + 2) * sizeof(U), 256);
-        off_split = off_plan + plan_bytes;
-        off_samp = off_split + align_up((size_t)(mtiles + 1) * 8, 256);
-        // tile samples: one set per buffer (the caller's, the scratch copy)
-        off_keys = off_samp + (SR_SPLIT_SAMPLES && passes > 0 ? align_up((size_t)(4 * mtiles) * sizeof(U), 256) : 0);
-        const size_t kb = passes > 0 ? align_up((size_t)n * sizeof(T), 256) : 0;
-        off_vals = off_keys + kb;
-        const size_t vb = (VALS && passes > 0) ? align_up((size_t)n * 4, 256) : 0;
-        bytes = off_vals + vb;
-        rem = rem_ && !VALS && tiles >= REM_MIN_TILES && passes > 0;
-        if (rem) {
-            rem_dmax = n / 32;
-            rtiles = (n + RT - 1) / RT;
-            // the buckets follow the key buffer directly: one index space for the merge
-            off_rem_buck = off_keys + kb;
-            off_rem_bound = off_rem_buck + align_up((size_t)rtiles * REM_CAP * sizeof(T), 256);
-            off_rem_scount = off_rem_bound + align_up((size_t)(rtiles + 1) * sizeof(U), 256);
-            off_rem_bcount = off_rem_scount + align_up((size_t)rtiles * 4, 256);
-            off_rem_blk = off_rem_bcount + align_up((size_t)rtiles * 4, 256);
-            bytes = off_rem_blk + align_up((size_t)(rtiles + 1) * 8, 256);
-        }
+    explicit PlainSort(size_t n_, bool rem_ = false, bool fan4_ = default_fan4()) {
+        const Layout L = layout((long long)n_, rem_, fan4_);
+        n = L.n; tiles = L.tiles; mtiles = L.mtiles; passes = L.levels; steps = L.steps; fan4 = fan4_;
+        rem = L.rem; rem_dmax = L.rem_dmax; rtiles = L.rtiles;
+        off_ctrl = L.off_ctrl; off_plan = L.off_plan; off_split = L.off_split; off_split4 = L.off_split4;
+        off_samp = L.off_samp; off_keys = L.off_keys; off_vals = L.off_vals; bytes = L.bytes;
+        off_rem_buck = L.off_rem_buck; off_rem_bound = L.off_rem_bound; off_rem_scount = L.off_rem_scount;
+        off_rem_bcount = L.off_rem_bcount; off_rem_blk = L.off_rem_blk;
+        sms = device_sm_count();
+    }
+
+    // Merge fan-in per key shape, as measured on GB300: 4-way steps where a
+    // step moves enough bytes per key to be bound by HBM (payloads, 8-byte
+    // keys), 2-way steps for 4-byte keys alone, whose 2-way merge already runs
+    // near the HBM roofline while the 4-way one is bound by instruction issue.
+    // SORTRACE_MERGE_FANIN = "2" or "4" (read once) forces one for measuring.
+    static bool default_fan4() {
+        static const int forced = [] {
+            const char *e = std::getenv("SORTRACE_MERGE_FANIN");
+            return e && e[0] == '2' ? 2 : (e && e[0] == '4' ? 4 : 0);
+        }();
+        if (forced) return forced == 4;
+        return VALS || sizeof(T) == 8;
+    }
+    // How a 4-way tile stages its windows when the arrays are 16-byte
+    // aligned: 1-D bulk copies, unless SORTRACE_MERGE4_STAGE is "vec" (16-byte
+    // loads through registers).
+    static int stage4() {
+        static const int m = [] {
+            const char *e = std::getenv("SORTRACE_MERGE4_STAGE");
+            return (e && e[0] == 'v') ? (int)STAGE_VEC : (int)STAGE_BULK;
+        }();
+        return m;
     }
 
     // Launches the whole sequence on stream s.  The block sort writes to the
@@ -123,11 +191,11 @@ template <int KT, bool VALS> struct PlainSort {
                               gate);
             }
             if (parts & PART_REVERSE)
-                SR_LAUNCH(SR_KERNEL_REVERSE, (k_reverse<KT, VALS>), grid_for(n / 2, 256, 152 * 16), 256, 0, s,
+                SR_LAUNCH(SR_KERNEL_REVERSE, (k_reverse<KT, VALS>), grid_for(n / 2, 256, sms * 16), 256, 0, s,
                           uk, uv, n, ctrl);
             if constexpr (FEW) if (parts & PART_FEW) {
-                SR_LAUNCH(SR_KERNEL_COPY, k_few_count<KT>, grid_for(n, 256, 152 * 8), 256, 0, s, uk, n, ctrl);
-                SR_LAUNCH(SR_KERNEL_COPY, k_few_write<KT>, grid_for(n / 4 + 1, 256, 152 * 8), 256, 0, s, uk, n,
+                SR_LAUNCH(SR_KERNEL_COPY, k_few_count<KT>, grid_for(n, 256, sms * 8), 256, 0, s, uk, n, ctrl);
+                SR_LAUNCH(SR_KERNEL_COPY, k_few_write<KT>, grid_for(n / 4 + 1, 256, sms * 8), 256, 0, s, uk, n,
                           ctrl);
             }
             if constexpr (!VALS) if (rem && (parts & PART_REM)) {
@@ -141,7 +209,7 @@ template <int KT, bool VALS> struct PlainSort {
                           bcount);
                 // grids of SR_REM_GRID CTAs per SM that loop over the tiles:
                 // when the path is not taken, every CTA returns at once
-                const unsigned rgrid = (unsigned)grid_for(rtiles, 1, 152 * SR_REM_GRID);
+                const unsigned rgrid = (unsigned)grid_for(rtiles, 1, sms * SR_REM_GRID);
                 const size_t sp_smem = (size_t)RT * (sizeof(U) + 1);
                 SR_LAUNCH(SR_KERNEL_DISPLACED, (k_rem_split<KT, REM_TNT, IPT>), rgrid, REM_TNT, sp_smem, s, uk, n,
                           rtiles, ctrl, bound, sk, scount, buck, bcount);
@@ -164,7 +232,7 @@ template <int KT, bool VALS> struct PlainSort {
         return st;
     }
 
-    // The block sort, the pass planner, the merge passes and the copy-back.
+    // The block sort, the pass planner, the merge steps and the copy-back.
     sr_status launch_sort(T *uk, uint32_t *uv, unsigned char *scratch, cudaStream_t s) const {
         Ctrl *ctrl = (Ctrl *)(scratch + off_ctrl);
         U *plo = (U *)(scratch + off_plan);
@@ -172,12 +240,13 @@ template <int KT, bool VALS> struct PlainSort {
         U *plo2 = phi + tiles;
         U *phi2 = plo2 + (tiles + 1) / 2 + 1;
         long long *splits = (long long *)(scratch + off_split);
+        long long *splits4 = (long long *)(scratch + off_split4);
         U *samp = SR_SPLIT_SAMPLES && passes > 0 ? (U *)(scratch + off_samp) : nullptr;
         T *sk = (T *)(scratch + off_keys);
         uint32_t *sv = (uint32_t *)(scratch + off_vals);
-        const int P = passes;
-        const int cur0 = P & 1;
+        const int cur0 = steps & 1;                 // the last step lands in the caller's buffer
         const bool vec = ((uintptr_t)uk % 16) == 0 && (!VALS || ((uintptr_t)uv % 16) == 0);
+        int *st_word = status ? status : &ctrl->status;
         sr_status st = SR_OK;
         do {
             const size_t bs_smem = (size_t)TS * (sizeof(U) + (VALS ? 4 : 0));
@@ -185,31 +254,54 @@ template <int KT, bool VALS> struct PlainSort {
             SR_LAUNCH(SR_KERNEL_BLOCK_SORT, (k_block_sort<KT, SNT, IPT, VALS>), (unsigned)tiles, SNT,
                       bs_smem, s, uk, uv, cur0 ? sk : uk, cur0 ? sv : uv, n, ctrl, plo, phi,
                       samp ? samp + cur0 * 2 * mtiles : nullptr, (int)NV);
-            if (P == 0) break;
+            if (passes == 0) break;
             if ((tiles + PLAN_CHUNK - 1) / PLAN_CHUNK > PLAN_CHUNK) { st = SR_ERR_UNSUPPORTED; break; }
             SR_LAUNCH(SR_KERNEL_PARTITION, (k_plan<KT>), (unsigned)((tiles + PLAN_CHUNK - 1) / PLAN_CHUNK),
-                      1024, 0, s, plo, phi, plo2, phi2, n, tiles, P, cur0, ctrl);
+                      1024, 0, s, plo, phi, plo2, phi2, n, tiles, passes, cur0, fan4 ? 1 : 0, ctrl);
             const size_t m_smem = merge_tile_smem<U, NT, IPT, VALS>();
-            if ((st = allow_smem(k_merge<KT, NT, IPT, VALS, true>, m_smem)) != SR_OK) break;
-            if ((st = allow_smem(k_merge<KT, NT, IPT, VALS, false>, m_smem)) != SR_OK) break;
-            for (int p = 0; p < P; ++p) {
-                const long long w = (long long)TS << p;
-                const int lgt = LG_TS_NV + 1 + p;          // merge tiles per run pair: 2w / NV
-                const long long nb = mtiles + 1;
-                const int lg = partition_lg(nb);
+            const size_t m4_smem = merge4_smem<U, NT, IPT, VALS>();
+            const int mode4 = vec ? stage4() : (int)STAGE_SCALAR;
+            const long long nb = mtiles + 1;
+            const int lg = partition_lg(nb);
+            const int lg4 = partition4_lg(nb);
+            for (int step = 0; step < steps; ++step) {
+                int l0, nl;
+                merge_step_levels(passes, fan4, step, &l0, &nl);
+                const long long w = (long long)TS << l0;
                 SR_LAUNCH(SR_KERNEL_PARTITION, (k_partition<KT>), (unsigned)(((nb << lg) + 255) / 256), 256, 0,
-                          s, uk, sk, n, w, NV, nb, splits, ctrl, p, lg, samp, 2 * mtiles);
-                if (vec) {
-                    SR_LAUNCH(SR_KERNEL_MERGE, (k_merge<KT, NT, IPT, VALS, true>), (unsigned)mtiles, NT,
-                              m_smem, s, uk, uv, sk, sv, n, w, lgt, splits, ctrl, p, samp, 2 * mtiles);
+                          s, uk, sk, n, w, NV, nb, splits, ctrl, step, l0, nl, lg, samp, 2 * mtiles);
+                if (nl == 1) {
+                    const int lgt = LG_TS_NV + 1 + l0;     // merge tiles per run pair: 2w / NV
+                    if (vec) {
+                        if ((st = allow_smem(k_merge<KT, NT, IPT, VALS, true>, m_smem)) != SR_OK) break;
+                        SR_LAUNCH(SR_KERNEL_MERGE, (k_merge<KT, NT, IPT, VALS, true>), (unsigned)mtiles, NT,
+                                  m_smem, s, uk, uv, sk, sv, n, w, lgt, splits, ctrl, step, l0, samp, 2 * mtiles);
+                    } else {
+                        if ((st = allow_smem(k_merge<KT, NT, IPT, VALS, false>, m_smem)) != SR_OK) break;
+                        SR_LAUNCH(SR_KERNEL_MERGE, (k_merge<KT, NT, IPT, VALS, false>), (unsigned)mtiles, NT,
+                                  m_smem, s, uk, uv, sk, sv, n, w, lgt, splits, ctrl, step, l0, samp, 2 * mtiles);
+                    }
+                    continue;
+                }
+                SR_LAUNCH(SR_KERNEL_PARTITION, (k_partition4<KT>), (unsigned)(((nb << lg4) + 255) / 256), 256, 0,
+                          s, uk, sk, n, w, NV, nb, splits, splits4, ctrl, step, l0, lg4);
+                if (mode4 == STAGE_BULK) {
+                    if ((st = allow_smem(k_merge4<KT, NT, IPT, VALS, STAGE_BULK>, m4_smem)) != SR_OK) break;
+                    SR_LAUNCH(SR_KERNEL_MERGE, (k_merge4<KT, NT, IPT, VALS, STAGE_BULK>), (unsigned)mtiles, NT,
+                              m4_smem, s, uk, uv, sk, sv, n, w, splits4, ctrl, step, l0, samp, 2 * mtiles, st_word);
+                } else if (mode4 == STAGE_VEC) {
+                    if ((st = allow_smem(k_merge4<KT, NT, IPT, VALS, STAGE_VEC>, m4_smem)) != SR_OK) break;
+                    SR_LAUNCH(SR_KERNEL_MERGE, (k_merge4<KT, NT, IPT, VALS, STAGE_VEC>), (unsigned)mtiles, NT,
+                              m4_smem, s, uk, uv, sk, sv, n, w, splits4, ctrl, step, l0, samp, 2 * mtiles, st_word);
                 } else {
-                    SR_LAUNCH(SR_KERNEL_MERGE, (k_merge<KT, NT, IPT, VALS, false>), (unsigned)mtiles, NT,
-                              m_smem, s, uk, uv, sk, sv, n, w, lgt, splits, ctrl, p, samp, 2 * mtiles);
+                    if ((st = allow_smem(k_merge4<KT, NT, IPT, VALS, STAGE_SCALAR>, m4_smem)) != SR_OK) break;
+                    SR_LAUNCH(SR_KERNEL_MERGE, (k_merge4<KT, NT, IPT, VALS, STAGE_SCALAR>), (unsigned)mtiles, NT,
+                              m4_smem, s, uk, uv, sk, sv, n, w, splits4, ctrl, step, l0, samp, 2 * mtiles, st_word);
                 }
             }
             if (st != SR_OK) break;
-            SR_LAUNCH(SR_KERNEL_COPY, (k_copy_back<KT, VALS>), grid_for(n, 256, 152 * 16), 256, 0, s,
-                      uk, uv, sk, sv, n, ctrl, P);
+            SR_LAUNCH(SR_KERNEL_COPY, (k_copy_back<KT, VALS>), grid_for(n, 256, sms * 16), 256, 0, s,
+                      uk, uv, sk, sv, n, ctrl, steps);
         } while (0);
         return st;
     }

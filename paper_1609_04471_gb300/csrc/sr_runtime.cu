@@ -67,6 +67,24 @@ bool pdl_enabled() {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+int device_sm_count() {
+    static int cached[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return 152;
+    }
+    if (cached[dev] == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+            cudaGetLastError();
+            v = 152;
+        }
+        cached[dev] = v;
+    }
+    return cached[dev];
+}
+
 int ceil_log2(unsigned long long x) {
     int r = 0;
     while ((1ull << r) < x) ++r;
@@ -248,7 +266,9 @@ extern "C" sr_status sr_get_stats(sr_stats *out) {
     if (out->input_class == 0) {
         bytes += 2 * n * elem;                                          // block sort
         for (int p = 0; p < out->passes_planned && p < MAX_PASSES; ++p) {
-            if (c.unordered[p] == 0) ++skipped;
+            int l0 = p, nl = 1;
+            if (r.fan4) merge_step_levels(r.levels, true, p, &l0, &nl);
+            if (c.unordered[l0] == 0 && (nl == 1 || c.unordered[l0 + 1] == 0)) ++skipped;
             else { ++merged; bytes += 2 * n * elem; }
         }
         if (((r.cur0 + merged) & 1) != 0) bytes += 2 * n * elem;         // copy back

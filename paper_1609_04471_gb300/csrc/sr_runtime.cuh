@@ -43,6 +43,8 @@ struct CallRecord {
     int key_bytes = 4;
     int val_bytes = 0;
     int cur0 = 0;
+    int levels = 0;                 // binary merge levels after the block sort
+    bool fan4 = false;              // merged four runs per step (passes_planned counts steps)
     int aux_kind = 0;               // 3: last_aux holds a segmented call's block, 4: a learned call's
 };
 
@@ -83,6 +85,9 @@ void launch_begin(int kind, cudaStream_t s);
 sr_status launch_end(int kind, cudaStream_t s);
 
 size_t align_up(size_t x, size_t a);
+// Streaming multiprocessors of the current device (looked up once per device;
+// 152 if the query fails).
+int device_sm_count();
 int ceil_log2(unsigned long long x);
 size_t key_bytes_of(sr_key_type kt);
 bool valid_key_type(int kt);

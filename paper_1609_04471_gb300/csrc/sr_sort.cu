@@ -347,7 +347,7 @@ template <int KT, bool VALS>
 static sr_status sort_impl(void *d_keys, uint32_t *d_vals, size_t n, cudaStream_t s, int call, bool graphs) {
     typedef PlainSort<KT, VALS> PS;
     typedef typename PS::T T;
-    const PS plan(n, !VALS && SR_REM_KEYS);
+    PS plan(n, !VALS && SR_REM_KEYS);
     CallRecord &rec = call_record();
     rec = CallRecord();
     rec.host.call = call;
@@ -362,8 +362,11 @@ static sr_status sort_impl(void *d_keys, uint32_t *d_vals, size_t n, cudaStream_
     if (plan.passes > MAX_PASSES) return SR_ERR_UNSUPPORTED;
     DeviceState *ds = nullptr;
     SR_TRY(device_state(&ds));
-    rec.cur0 = plan.passes & 1;
-    rec.host.passes_planned = plan.passes;
+    plan.status = ds->status;
+    rec.cur0 = plan.steps & 1;
+    rec.levels = plan.passes;
+    rec.fan4 = plan.fan4;
+    rec.host.passes_planned = plan.steps;
     if (graphs) {                                // caller's buffers: a repeated call replays its graph
         bool done = false;
         SR_TRY(graph_call(plan, KT, d_keys, d_vals, s, ds, &done));

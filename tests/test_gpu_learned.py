@@ -73,9 +73,10 @@ def test_device_adam_first_step_exact(gpu_lib):
     """One device Adam step against the oracle's: a bias-corrected first step
     moves every parameter by lr * g / (|g| + eps), i.e. by the step size in
     the direction against its gradient.  Parameters whose float64 gradient
-    is clearly non-zero (|g| > 1e-4, so float32 rounding cannot flip its
-    sign) must land within 1e-6 of the oracle's (plus float32 rounding of
-    the parameter); the rest move by at most the step size."""
+    is at least 1% of the largest (the device gradient is within 0.2% of the
+    largest, test above, so its sign is certain there) must land within 1e-6
+    of the oracle's (plus float32 rounding of the parameter); the rest move
+    by at most the step size."""
     keys = si.lognormal_f32(200_000, 5)
     o = M.ord_u32_f32(keys).astype(np.float64)
     xs = np.sort(M.normalise(o, o.min(), o.max()))[::50].astype(np.float32)
@@ -87,8 +88,8 @@ def test_device_adam_first_step_exact(gpu_lib):
     th_ref = M.adam_train(th64, x64, t64, steps=1, lr=lr)
     _, g = M.loss_and_grad(th64, x64, t64)
     d = np.abs(np.asarray(th_gpu, dtype=np.float64) - th_ref)
-    clear = np.abs(g) > 1e-4
-    assert clear.sum() >= 10
+    clear = np.abs(g) > 1e-2 * np.max(np.abs(g))
+    assert clear.sum() >= 5, clear.sum()
     tol = 1e-6 + 4e-7 * np.abs(th64)           # float32 rounding of the updated value
     assert np.all(d[clear] < tol[clear]), np.max(d[clear] / tol[clear])
     assert np.max(np.abs(np.asarray(th_gpu, dtype=np.float64) - th64)) <= lr * (1 + 1e-5)

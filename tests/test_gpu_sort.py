@@ -143,15 +143,15 @@ def test_reversed_input_one_pass(gpu_lib):
 
 def test_teeth_skip_passes(gpu_lib):
     """2-equal teeth whose teeth are whole numbers of block-sort tiles (128
-    int32 tiles, 7 merge levels: one 2-way step, then three 4-way steps):
-    every step below the tooth length finds all its run pairs in order and is
-    skipped; only the last step merges."""
+    int32 tiles, 7 merge levels: seven 2-way steps, or one 2-way step and
+    three 4-way ones): every step below the tooth length finds all its run
+    pairs in order and is skipped; only the last step merges."""
     n = 128 * _tiles(gpu_lib, 4)[1]
     a = si.k_equal_teeth(n, 2)
     t = _to_dev(a)
     gpu_lib.sort_keys(t, key_type=0)
     st = gpu_lib.stats()
-    assert st["passes_planned"] == 4 and st["passes_skipped"] == 3
+    assert (st["passes_planned"], st["passes_skipped"]) in ((7, 6), (4, 3))
     assert _from_dev(t, np.int32).tobytes() == oracle.sort_keys(a).tobytes()
 
 
@@ -537,3 +537,32 @@ def test_release_cached(gpu_lib):
         assert x.cpu().numpy().tobytes() == want
         if r == 2:
             gpu_lib.release_cached()
+
+
+_PAPER_CLASSES = {
+    "k-limited": lambda n, k: si.k_limited(n, min(k, 32), 3),
+    "k-equal teeth": lambda n, k: si.k_equal_teeth(n - n % k, k),
+    "k-even teeth": lambda n, k: si.k_even_teeth(n - n % k, k),
+    "k-sharp teeth": lambda n, k: si.k_sharp_teeth(n - n % k, k),
+    "k-shuffled teeth": lambda n, k: si.k_shuffled_teeth(n - n % k, k, 3),
+    "k-distance": lambda n, k: si.k_distance(n, k, 3),
+    "k-exchange": lambda n, k: si.k_exchange(n, k, 3),
+}
+
+
+@pytest.mark.parametrize("name,k", [("k-limited", 12), ("k-equal teeth", 8), ("k-even teeth", 8),
+                                    ("k-sharp teeth", 8), ("k-shuffled teeth", 8), ("k-distance", 256),
+                                    ("k-exchange", (1 << 24) // 100)])
+def test_paper_classes_2_24(gpu_lib, name, k):
+    """Section 2's parametrised classes at 2^24 int32 keys (the parameters the
+    benchmark's class table uses), compared in full with the oracle."""
+    a = _PAPER_CLASSES[name](1 << 24, k)
+    assert _gpu_sort(gpu_lib, a).tobytes() == oracle.sort_keys(a).tobytes(), (name, k)
+
+
+@pytest.mark.parametrize("name", list(_PAPER_CLASSES))
+def test_paper_classes_k_sweep(gpu_lib, name):
+    """Each class for k = 2^0 .. 2^8 (the paper's range) at 2^20 + 7 keys."""
+    for i in range(9):
+        a = _PAPER_CLASSES[name]((1 << 20) + 7, 2 ** i)
+        assert _gpu_sort(gpu_lib, a).tobytes() == oracle.sort_keys(a).tobytes(), (name, 2 ** i)
