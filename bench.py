@@ -38,7 +38,7 @@ N_KEYS = 1 << 24
 CLASSES = ("uniform", "reversed", "nearly_sorted", "few_unique")
 SEED = 1
 FLUSH_BYTES = 512 << 20
-CPU_SAMPLE = 1 << 22          # keys of each array the CPU baseline sorts
+CPU_SAMPLE = 1 << 22          # keys of each array one reference-arm step sorts
 
 
 def _args():
@@ -79,9 +79,11 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _ncu_traffic(kernel_tag: str):
-    """Per-launch DRAM bytes of a kernel from its committed ncu summary, or
-    None if the summary is missing or the kernel's sources changed since."""
+def _ncu_traffic(kernel_tag: str, scale: float = 1.0):
+    """Per-launch DRAM bytes of a kernel from its committed ncu summary (times
+    `scale`, for a summary taken on a smaller array whose traffic grows with
+    the keys), or None if the summary is missing or the kernel's sources
+    changed since."""
     import hashlib
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
     try:
@@ -98,7 +100,7 @@ def _ncu_traffic(kernel_tag: str):
             src += f.read()
     if hashlib.sha256(src).hexdigest()[:16] != h.group(1)[:16]:
         return None
-    return int(m.group(1))
+    return int(int(m.group(1)) * scale)
 
 
 class Clocks:
@@ -172,31 +174,44 @@ def _dist():
     return ws, rank, local
 
 
-def _cpu_baseline(arrays, sample=CPU_SAMPLE):
-    """The oracle (single-threaded C mergesort) on the first `sample` keys of
-    each array of the workload, pinned to host core 0 while it runs; returns
-    (Gkeys/s, seconds, keys)."""
+def _cpu_baseline(arrays, sample=None, algos=("merge", "quick")):
+    """The oracle's two sorts (single-threaded C: the natural mergesort and the
+    hybrid quicksort) on the arrays of the workload (their first `sample` keys
+    if given), pinned to host core 0 while they run; returns
+    {algo: (Gkeys/s, seconds, keys)}."""
     import oracle
     oracle.build()
-    keys = 0
     try:
         old = os.sched_getaffinity(0)
         os.sched_setaffinity(0, {sorted(old)[0]})
     except (AttributeError, OSError):
         old = None
+    out = {}
     try:
-        t0 = time.perf_counter()
-        for a in arrays:
-            oracle.sort_keys(a[:sample], "merge")
-            keys += min(sample, a.size)
-        dt = time.perf_counter() - t0
+        for algo in algos:
+            keys = 0
+            t0 = time.perf_counter()
+            for a in arrays:
+                part = a if sample is None else a[:sample]
+                oracle.sort_keys(part, algo)
+                keys += part.size
+            dt = time.perf_counter() - t0
+            out[algo] = (keys / dt / 1e9, dt, keys)
     finally:
         if old is not None:
             os.sched_setaffinity(0, old)
-    return keys / dt / 1e9, dt, keys
+    return out
 
 
 def _cpu_model():
+    """The host CPU's model name (lscpu's, else /proc/cpuinfo's)."""
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for line in r.stdout.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
     try:
         with open("/proc/cpuinfo") as f:
             for line in f:
@@ -220,11 +235,11 @@ def run_reference(args):
     import sortrace_inputs as si
     arrays = [si.int32_input(k, N_KEYS, SEED) for k in CLASSES]
     for _ in range(args.warmup):
-        _cpu_baseline(arrays)
+        _cpu_baseline(arrays, CPU_SAMPLE, ("merge",))
     times = []
     keys = 0
     for _ in range(args.steps):
-        v, dt, keys = _cpu_baseline(arrays)
+        v, dt, keys = _cpu_baseline(arrays, CPU_SAMPLE, ("merge",))["merge"]
         times.append(dt)
     ms = 1e3 * sum(times) / len(times)
     value = keys / (ms / 1e3) / 1e9
@@ -342,12 +357,21 @@ def run_ours(args):
     dominant = max(kinds.items(), key=lambda kv: kv[1][1])[0]
     merge_bytes_launch = 2 * N_KEYS * 4            # read + write of every key
     achieved = merge_bytes_launch / (merge_ms_work / work_merges / 1e3) / 1e9 if work_merges else None
-    traffic = _ncu_traffic("merge_pass_2p24_int32")
+    timed_region = {
+        "where": "the timed region (4 x 2^24 int32, uniform array's merge steps); input and output of a "
+                 "step fit the 129 MB L2 together, so part of each step's traffic is L2 hits",
+        "achieved": achieved, "frac": (achieved / peak) if achieved else None,
+        "frac_nominal": (achieved / NOMINAL_HBM_GBS) if achieved else None,
+        "avg_launch_ms": merge_ms_work / work_merges if work_merges else None,
+        "launches_timed": work_merges, "algorithmic_bytes_per_launch": merge_bytes_launch,
+        "traffic": _ncu_traffic("merge_step_2p24_int32"),
+    }
     roofline = {
-        "bound": "hbm", "kernel": "k_merge (global merge pass)", "achieved": achieved, "peak": peak,
-        "unit": "GB/s", "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
-        "frac_nominal": (achieved / NOMINAL_HBM_GBS) if achieved else None, "nominal_peak": NOMINAL_HBM_GBS,
-        "algorithmic_bytes_per_launch": merge_bytes_launch, "traffic": traffic,
+        "bound": "hbm", "kernel": "merge step (k_merge: 2-way, the fan-in of 4-byte keys alone)",
+        "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
+        "peak_kind": peak_kind, "frac_nominal": (achieved / NOMINAL_HBM_GBS) if achieved else None,
+        "nominal_peak": NOMINAL_HBM_GBS, "algorithmic_bytes_per_launch": merge_bytes_launch,
+        "traffic": timed_region["traffic"], "where": timed_region["where"],
         "avg_launch_ms": merge_ms_work / work_merges if work_merges else None,
         "launches_timed": work_merges,
         "dominant_by_time": dominant,
@@ -390,15 +414,39 @@ def run_ours(args):
     sweep = None
     if not args.no_sweep:
         sweep = _sweep(sr, torch, dev, stream, peak)
+        # headline roofline out of L2: the merge steps of the 2^28 sort (2 GiB
+        # in, 2 GiB out per step), each launch timed with CUDA events on the
+        # sorting stream; the timed region's L2-assisted figure stays beside it
+        big = sweep.get("2^28", {}).get("kernels", {})
+        m28 = big.get("merge")
+        if m28:
+            roofline.update({
+                "achieved": m28["achieved_gbs"], "frac": m28["frac"], "frac_nominal": m28["frac_nominal"],
+                "algorithmic_bytes_per_launch": m28["bytes_per_launch"], "avg_launch_ms": m28["avg_launch_ms"],
+                "launches_timed": m28["launches"],
+                "where": "2^28 uniform int32 sort of the size sweep (2 GiB per step in and out, far above L2), "
+                         "every launch bracketed by CUDA events on the sorting stream",
+                "traffic": _ncu_traffic("merge_step_2p26_int32", scale=4),
+                "traffic_note": "dram read + write bytes of one k_merge launch at 2^26 (ncu, "
+                                "profiles/merge_step_2p26_int32.md) times 4, the keys of a 2^28 launch",
+                "timed_region_2p24_l2_assisted": timed_region,
+                "other_kernels_2p28": {kname: big[kname] for kname in ("block_sort", "detect") if kname in big},
+            })
     forms = None
     if not args.no_forms and rank == 0:
         forms = _forms(sr, torch, dev, stream, peak)
+        forms["classes_2^24_int32"] = _classes(sr, torch)
 
     cpu = None
     if rank == 0:
-        v, dt, keys = _cpu_baseline(arrays)
+        cb = _cpu_baseline(arrays)
+        v, dt, keys = cb["merge"]
+        vq, dtq, _ = cb["quick"]
         cpu = {"value": v, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
-               "sample": f"first {CPU_SAMPLE} keys of each of the 4 arrays ({keys} keys, {dt:.2f} s)",
+               "sample": f"the whole workload: the 4 arrays of 2^24 keys ({keys} keys); "
+                         f"mergesort {dt:.2f} s, quicksort {dtq:.2f} s",
+               "algorithm": "natural mergesort (mer6 techniques, Section 3)",
+               "quicksort_value": vq, "quicksort_algorithm": "hybrid quicksort (hyb2, Section 4)",
                "cpu": _cpu_model(), "nproc": os.cpu_count()}
 
     if rank == 0:
@@ -448,11 +496,29 @@ def _sweep(sr, torch, dev, stream, peak, reps=3):
                 ms = e0.elapsed_time(e1)
                 best = ms if best is None else min(best, ms)
         st = sr.stats()
+        # the same sort once more with every launch bracketed by CUDA events on
+        # the sorting stream: per-kernel time, hence each kernel's own roofline
+        x.copy_(big[:n])
+        flush.fill_(0x5A)
+        torch.cuda.synchronize()
+        sr.profile_begin()
+        sr.sort_keys(x)
+        k = sr.profile_end()
+        kern = {}
+        for name, per_key in (("merge", 8), ("block_sort", 8), ("detect", 4)):
+            launches, t_ms = k.get(name, (0, 0.0))
+            if launches:
+                avg = t_ms / launches
+                gbs = per_key * n / (avg / 1e3) / 1e9
+                kern[name] = {"launches": launches, "avg_launch_ms": avg, "bytes_per_launch": per_key * n,
+                              "achieved_gbs": gbs, "frac": gbs / peak, "frac_nominal": gbs / NOMINAL_HBM_GBS}
         out[f"2^{lg}"] = {"ms": best, "gkeys_s": n / (best / 1e3) / 1e9,
                           "passes_frac": st["bytes_moved"] / (best / 1e3) / 1e9 / peak,
                           "passes_frac_nominal": st["bytes_moved"] / (best / 1e3) / 1e9 / NOMINAL_HBM_GBS,
                           "lower_bound_frac": 8 * n / (best / 1e3) / 1e9 / peak,
-                          "bytes_moved": st["bytes_moved"]}
+                          "bytes_moved": st["bytes_moved"], "merge_steps": st["passes_planned"],
+                          "kernels": kern,
+                          "kernel_ms": {name: round(v[1], 4) for name, v in k.items() if v[0]}}
         del x
     return out
 
@@ -501,17 +567,14 @@ def run_profile_case(args):
                       "passes_planned": st["passes_planned"], "passes_skipped": st["passes_skipped"], "ok": True}))
 
 
-def run_classes(args):
+def _classes(sr, torch, reps=5):
     """The paper's input classes with a parameter k (Section 2) at 2^24 int32
-    keys: per class the sort time (median of 5 after 3 warm-ups, L2 flushed,
-    input restored untimed), the path the call took and the passes it skipped.
-    Every output is compared with numpy's sort of the same keys."""
+    keys: per class the sort time (median of `reps` after 3 warm-ups, L2
+    flushed, input restored untimed), the path the call took and the merge
+    steps it skipped.  Every output is compared with numpy's sort of the same
+    keys (the parity tests compare them with the oracle)."""
     import numpy as np
-    import torch
-    import paper_1609_04471_gb300 as sr
     import sortrace_inputs as si
-    torch.cuda.set_device(0)
-    sr.load()
     n = 1 << 24
     classes = {
         "random": lambda: si.uniform_i32(n, SEED),
@@ -530,7 +593,7 @@ def run_classes(args):
         src = torch.from_numpy(a).cuda()
         x = torch.empty_like(src)
         ts = []
-        for r in range(8):
+        for r in range(3 + reps):
             x.copy_(src)
             flush.fill_(r & 0xFF)
             torch.cuda.synchronize()
@@ -549,7 +612,17 @@ def run_classes(args):
                      "input_class": st["input_class"], "runs": st["runs"],
                      "passes_planned": st["passes_planned"], "passes_skipped": st["passes_skipped"],
                      "bytes_moved": st["bytes_moved"]}
-    print(json.dumps({"classes": out, "n": n, "key": "int32", "data": "synthetic (Section 2 generators)"}))
+        del src, x
+    return out
+
+
+def run_classes(args):
+    import torch
+    import paper_1609_04471_gb300 as sr
+    torch.cuda.set_device(0)
+    sr.load()
+    out = _classes(sr, torch)
+    print(json.dumps({"classes": out, "n": 1 << 24, "key": "int32", "data": "synthetic (Section 2 generators)"}))
 
 
 def _timed(torch, stream, fn, restore, reps):
@@ -667,12 +740,17 @@ def _forms(sr, torch, dev, stream, peak):
         for v in views:
             sr.sort_keys(v)
     per_ms = _timed(torch, stream, per_array, lambda: x.copy_(src), 2)
+    # the same keys as one array in one plain call (a different output: one
+    # sorted array instead of 200,000), for scale
+    one_ms = _timed(torch, stream, lambda: sr.sort_keys(x), lambda: x.copy_(src), 2)
     out["batched_200k_arrays_i32"] = {
         "keys": n, "graph_ms": graph_ms, "eager_ms": eager_ms,
         "graph_gkeys_s": n / (graph_ms / 1e3) / 1e9,
         "per_array_sample_arrays": sample, "per_array_sample_keys": sample_keys, "per_array_ms": per_ms,
         "per_array_gkeys_s": sample_keys / (per_ms / 1e3) / 1e9,
         "batched_over_per_array": (n / graph_ms) / (sample_keys / per_ms),
+        "one_plain_call_ms": one_ms, "one_plain_call_gkeys_s": n / (one_ms / 1e3) / 1e9,
+        "batched_over_one_plain_call": one_ms / graph_ms,
         "big_segments": sts["big_segments"],
         "autotuned": {"config": best,
                       "shape": {k: cfgs[best][k] for k in ("strategy", "sort_threads", "pack_items",

@@ -108,10 +108,12 @@ template <int KB, bool VALS> struct Shape;
 #ifndef SR_MERGE4_MINB4
 #define SR_MERGE4_MINB4 5
 #endif
-template <> struct Shape<4, false> { enum { NT = SR_MERGE_NT, IPT = SR_K4_IPT, SORT_NT = SR_SORT_NT, MERGE_MINB = 6, MERGE4_MINB = SR_MERGE4_MINB4 }; };
-template <> struct Shape<4, true>  { enum { NT = SR_MERGE_NT, IPT = SR_K4V_IPT, SORT_NT = SR_SORT_NT, MERGE_MINB = 8, MERGE4_MINB = 6 }; };
-template <> struct Shape<8, false> { enum { NT = SR_MERGE_NT, IPT = SR_K8_IPT, SORT_NT = SR_SORT_NT, MERGE_MINB = 4, MERGE4_MINB = 4 }; };
-template <> struct Shape<8, true>  { enum { NT = SR_MERGE_NT, IPT = SR_K8V_IPT, SORT_NT = SR_SORT_NT, MERGE_MINB = 4, MERGE4_MINB = 4 }; };
+// SORT_MINB: block-sort CTAs per SM the register allocator is held to (4-byte
+// keys alone: 40 registers, three CTAs of 512 threads, as measured best).
+template <> struct Shape<4, false> { enum { NT = SR_MERGE_NT, IPT = SR_K4_IPT, SORT_NT = SR_SORT_NT, MERGE_MINB = 6, MERGE4_MINB = SR_MERGE4_MINB4, SORT_MINB = 3 }; };
+template <> struct Shape<4, true>  { enum { NT = SR_MERGE_NT, IPT = SR_K4V_IPT, SORT_NT = SR_SORT_NT, MERGE_MINB = 8, MERGE4_MINB = 6, SORT_MINB = 3 }; };
+template <> struct Shape<8, false> { enum { NT = SR_MERGE_NT, IPT = SR_K8_IPT, SORT_NT = SR_SORT_NT, MERGE_MINB = 4, MERGE4_MINB = 4, SORT_MINB = 1 }; };
+template <> struct Shape<8, true>  { enum { NT = SR_MERGE_NT, IPT = SR_K8V_IPT, SORT_NT = SR_SORT_NT, MERGE_MINB = 4, MERGE4_MINB = 4, SORT_MINB = 1 }; };
 
 // ------------------------------------------------------------- merge path
 
@@ -295,19 +297,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsig
 
 // ------------------------------------------------------- merge step schedule
 //
-// After the block sort the runs are one tile long; ceil(log2(tiles)) binary
-// merge levels remain.  With 4-way steps (fan4) each step merges four runs and
-// covers two levels; an odd level count starts with one 2-way step.  Step s
-// covers levels [l0, l0 + nl).
+// After the block sort the runs are one tile long at most; ceil(log2(tiles))
+// binary merge levels remain.  Steps of fan-in 4 cover two levels each, so a
+// call launches ceil(log_f(tiles)) steps; the run planner (k_runs) then tells
+// each step whether the input's natural runs need it.
 __host__ __device__ constexpr int merge_step_count(int levels, bool fan4) {
     return fan4 ? (levels + 1) / 2 : levels;
-}
-__host__ __device__ __forceinline__ void merge_step_levels(int levels, bool fan4, int s, int *l0, int *nl) {
-    if (!fan4) { *l0 = s; *nl = 1; return; }
-    const int odd = levels & 1;
-    if (odd && s == 0) { *l0 = 0; *nl = 1; return; }
-    *l0 = odd + 2 * (s - odd);
-    *nl = 2;
 }
 
 // Sort of a thread's IPT registers.  Keys alone: Batcher's odd-even merge
@@ -402,8 +397,18 @@ __device__ __forceinline__ void block_sort(U (&k)[IPT], uint32_t (&v)[IPT], U *s
 
 enum { MODE_SORT = 0, MODE_SORTED = 1, MODE_REVERSE = 2, MODE_FEW = 3, MODE_REM = 4 };
 enum { MAX_PASSES = 48 };
-// Few distinct keys: at most FEW_MAX distinct order images (4-byte keys).
-enum { FEW_MAX = 64, FEW_SLOTS = 128 };
+// Few distinct keys: at most FEW_MAX distinct order images (4-byte keys),
+// found in a FEW_SAMPLE-key sample through a hash set of FEW_SLOTS slots.
+enum { FEW_MAX = 4096, FEW_SLOTS_LOG2 = 14, FEW_SLOTS = 1 << FEW_SLOTS_LOG2 };
+
+// The few-distinct-keys path's tables, in the call's scratch (zeroed at the
+// start of every call): the set of sampled order images (image + 1 per slot,
+// 0 = empty), the distinct images ascending, and the keys equal to each.
+struct FewTables {
+    unsigned long long slot[FEW_SLOTS];
+    unsigned int sorted[FEW_MAX];
+    unsigned long long count[FEW_MAX];
+};
 
 // Lives in the call's scratch; zeroed at the start of every call.
 struct Ctrl {
@@ -411,25 +416,31 @@ struct Ctrl {
     unsigned long long nondescents;     // pairs a[i] <= a[i+1]
     unsigned long long tiles_ascending;
     unsigned long long tiles_descending;
-    int unordered[MAX_PASSES];          // per merge pass: run pairs not already in order
+    // written by the run planner (k_runs) after the block sort: the natural
+    // runs of whole tiles, the merge steps they need, and which buffer (0 =
+    // caller's, 1 = scratch) holds the data before step s (and after the last)
+    int nruns;
+    int nsteps;
+    // Neighbour repair: after the block sort no tile's keys exceed those of
+    // the tile two places on (repair), and no tile boundary's window of keys
+    // out of order is larger than a merge tile (else repair_fail): then each
+    // window is merged in place and no merge step runs.
+    int tile_perm;                               // the block sort writes reversed chains of tiles reversed
+    int repair;
+    int repair_fail;
+    unsigned long long repair_keys;              // keys in the merged windows
     int status;
-    unsigned int plan_ticket;           // CTAs of the pass planner that finished
-    // written by the pass planner once every unordered[p] is final: which
-    // buffer (0 = caller's, 1 = scratch) holds the data before pass p
     signed char src_buf[MAX_PASSES + 1];
     // Few distinct keys (4-byte keys, keys only): a sample of the keys goes
-    // into a hash set of order images (each slot holds image + 1; 0 is empty)
-    // until more than FEW_MAX appear (few_over); the counting pass then checks
-    // every key against it.
+    // into a hash set of order images (FewTables) until more than FEW_MAX
+    // appear (few_over); the counting pass then checks every key against it.
     int few_over;
     unsigned int few_n;                          // distinct images in the set
-    unsigned int few_ticket;                     // CTAs of the sampling kernel that finished
-    int few_cand;                                // the set is a candidate (sorted into few_sorted)
+    unsigned int few_ticket;                     // CTAs of the sampling kernels that finished
+    unsigned int few_ticket2;
+    int few_cand;                                // the set is a candidate (sorted into FewTables::sorted)
     int few_miss;                                // some key is not in the set
     int few_active;                              // the call took MODE_FEW (output written)
-    unsigned long long few_slot[FEW_SLOTS];
-    unsigned int few_sorted[FEW_MAX];            // the distinct images, ascending
-    unsigned long long few_count[FEW_MAX];       // keys equal to each
     // Few displaced keys (keys only): the path was tried (rem_active), a
     // bucket overflowed (rem_over), or it wrote the output (rem_gate).
     int rem_active;
@@ -437,6 +448,12 @@ struct Ctrl {
     int rem_gate;
     unsigned long long rem_dcount;               // keys that went through the buckets
 };
+
+// Merge steps the call runs: none after a neighbour repair, else the steps
+// the natural runs need.
+__device__ __forceinline__ int steps_of(const Ctrl *c) {
+    return (c->repair && !c->repair_fail) ? 0 : c->nsteps;
+}
 
 __device__ __forceinline__ int call_mode(const Ctrl *c, long long n) {
     if (c->descents == 0) return MODE_SORTED;
@@ -446,17 +463,18 @@ __device__ __forceinline__ int call_mode(const Ctrl *c, long long n) {
     return MODE_SORT;
 }
 
-// Inserts order image u into the hash set `set` (FEW_SLOTS slots of image + 1,
+// Inserts order image u into the hash set `set` (2^LOG2 slots of image + 1,
 // 0 = empty) shared by the threads that can see it; `cnt` counts distinct
-// images and `over` is raised past `limit` of them (or after 16 probes, which
-// with at most 64 of 128 slots used is rare and only costs the fast path).  No
-// waiting on other threads.
+// images and `over` is raised past `limit` of them (or after 32 probes, which
+// at most a quarter of the slots used makes rare and only costs the fast
+// path).  No waiting on other threads.
+template <int LOG2>
 __device__ __forceinline__ void few_insert(unsigned long long *set, unsigned int *cnt, int *over, unsigned int u,
-                                           unsigned int limit = FEW_MAX) {
+                                           unsigned int limit) {
     const unsigned long long v = (unsigned long long)u + 1ull;
-    const unsigned int h = (u * 2654435761u) >> 25;          // 7 bits: FEW_SLOTS = 128
-    for (int probe = 0; probe < 16; ++probe) {               // a longer probe counts as "too many"
-        const unsigned int i = (h + probe) & (FEW_SLOTS - 1);
+    const unsigned int h = (u * 2654435761u) >> (32 - LOG2);
+    for (int probe = 0; probe < 32; ++probe) {               // a longer probe counts as "too many"
+        const unsigned int i = (h + probe) & ((1u << LOG2) - 1u);
         const unsigned long long cur = ((volatile unsigned long long *)set)[i];
         if (cur == v) return;
         if (cur == 0ull) {

@@ -3,6 +3,8 @@
 // sequence that drives them is described in sr_sort.cu.
 #pragma once
 
+#include <climits>
+
 #include "sr_device.cuh"
 
 #ifndef SR_SPLIT_SAMPLES
@@ -19,6 +21,16 @@
 #endif
 
 namespace sr {
+
+enum { RUNS_NT = 1024 };          // threads of the one-CTA planners (k_tile_order, k_runs)
+// Longest wait for a tile's bulk copies: tries of mbarrier.try_wait (each
+// waits in hardware for a while); a tile that gives up reports
+// SR_ERR_TIMEOUT in its status word.
+enum { BULK_WAIT_TRIES = 1 << 22 };
+// How a merge tile stages its windows into shared memory: one key at a time
+// (arrays not 16-byte aligned), 4-key groups by 16-byte loads through
+// registers, or the same groups by 1-D bulk copies.
+enum { STAGE_SCALAR = 0, STAGE_VEC = 1, STAGE_BULK = 2 };
 
 // ------------------------------------------------------------- kernels
 
@@ -55,11 +67,14 @@ __device__ __forceinline__ typename Key<KT>::U median9_image(const typename Key<
 // `med` (optional): the scan also records, for every multiple b*mt of mt
 // below n (mt divides NT*IPT), the median of the 9 keys around it in med[b]
 // (med[0] = 0), for the few-displaced-keys path's value bounds.
+// `tmin`, `tmax` (optional): the tile's smallest and largest key images.
 template <int KT, int NT, int IPT>
 __global__ void __launch_bounds__(NT) k_detect(const typename Key<KT>::T *__restrict__ keys,
                                                long long n, Ctrl *__restrict__ c,
                                                const int *__restrict__ gate,
-                                               typename Key<KT>::U *__restrict__ med, int mt) {
+                                               typename Key<KT>::U *__restrict__ med, int mt,
+                                               typename Key<KT>::U *__restrict__ tmin,
+                                               typename Key<KT>::U *__restrict__ tmax) {
     griddep_wait();
     if (gate && *gate == 0) return;
     typedef Key<KT> K;
@@ -68,14 +83,17 @@ __global__ void __launch_bounds__(NT) k_detect(const typename Key<KT>::T *__rest
     constexpr int TS = NT * IPT;
     constexpr int VW = 16 / sizeof(T);             // keys per 16-byte vector
     __shared__ unsigned int red[4];
+    __shared__ U s_min, s_max;
     const int t = threadIdx.x;
     const long long base = (long long)blockIdx.x * TS;
     const int cnt = (int)(n - base < (long long)TS ? n - base : (long long)TS);   // keys of the tile
     const bool more = base + cnt < n;              // a key follows the tile
     const bool vec = (((uintptr_t)(keys + base)) & 15) == 0;
     if (t < 4) red[t] = 0;
+    if (t == 0) { s_min = umax_of<U>(); s_max = U(0); }
     __syncthreads();
     unsigned int d = 0, nd = 0, din = 0, ndin = 0;
+    U kmin = umax_of<U>(), kmax = U(0);
     const int ng = (cnt + VW - 1) / VW;
     for (int g = t; g < ng; g += NT) {
         const int j0 = g * VW;                     // tile index of the vector's first key
@@ -97,6 +115,10 @@ __global__ void __launch_bounds__(NT) k_detect(const typename Key<KT>::T *__rest
 #pragma unroll
         for (int e = 0; e < VW; ++e) {
             const int j = j0 + e;                  // pair (j, j+1)
+            if (j < cnt) {
+                kmin = x[e] < kmin ? x[e] : kmin;
+                kmax = x[e] > kmax ? x[e] : kmax;
+            }
             if (j + 1 < cnt || (j + 1 == cnt && more)) {
                 const bool de = x[e] > x[e + 1];
                 d += de;
@@ -109,13 +131,29 @@ __global__ void __launch_bounds__(NT) k_detect(const typename Key<KT>::T *__rest
     nd = __reduce_add_sync(0xffffffffu, nd);
     din = __reduce_or_sync(0xffffffffu, din);
     ndin = __reduce_or_sync(0xffffffffu, ndin);
+    if (tmin) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const U a = __shfl_xor_sync(0xffffffffu, kmin, o), b = __shfl_xor_sync(0xffffffffu, kmax, o);
+            kmin = a < kmin ? a : kmin;
+            kmax = b > kmax ? b : kmax;
+        }
+    }
     if ((t & 31) == 0) {
         if (d) atomicAdd(&red[0], d);
         if (nd) atomicAdd(&red[1], nd);
         if (din) atomicOr(&red[2], din);
         if (ndin) atomicOr(&red[3], ndin);
+        if (tmin) {
+            atomicMin(&s_min, kmin);
+            atomicMax(&s_max, kmax);
+        }
     }
     __syncthreads();
+    if (tmin && t == 0) {
+        tmin[blockIdx.x] = s_min;
+        tmax[blockIdx.x] = s_max;
+    }
     if (t == 0) {
         if (red[0]) atomicAdd(&c->descents, (unsigned long long)red[0]);
         if (red[1]) atomicAdd(&c->nondescents, (unsigned long long)red[1]);
@@ -129,46 +167,197 @@ __global__ void __launch_bounds__(NT) k_detect(const typename Key<KT>::T *__rest
     }
 }
 
-// Few distinct keys, step 1: FEW_SAMPLE keys spread over the whole array go
-// into the call's set of distinct order images (until more than FEW_MAX
-// appear); the last CTA to finish (a ticket after a fence) then, if the call
-// would sort and the set is small, sorts the set into few_sorted as the
-// candidate.  The counting pass checks every key against the set, so a
-// sample that misses a key only costs that pass.  This is the k-way form of
-// the fat (3-way) partition of the paper's quicksorts: keys equal to a pivot
-// need no further comparisons.
-enum { FEW_SAMPLE = 4096, FEW_NT = 256 };
-static_assert(FEW_NT >= FEW_SLOTS, "one thread per set slot");
+// Technique (a) of Section 3 at the granularity of tiles: a chain of whole
+// tiles in descending order (every key of tile t >= every key of tile t+1;
+// strictly, when payloads must stay stable, since equal keys would change
+// order) is a reversed run; the block sort writes its tiles in reversed order,
+// so the chain leaves the block sort as one ascending run.  A chain is turned
+// only when that lowers the count of natural runs (two tiles at the seam of
+// two ascending runs also form a chain, and turning them would cut both runs).
+// One CTA, from the scan's per-tile extremes: dest[t] = the tile position the
+// block sort writes tile t to (dest[t] = t outside turned chains).  Only when the block sort writes to
+// the other buffer (cur0 = 1): in place, a tile written elsewhere could
+// overwrite one not yet read.  Sets c->tile_perm when some chain exists.
 template <int KT>
-__global__ void __launch_bounds__(FEW_NT) k_few_sample(const typename Key<KT>::T *__restrict__ keys, long long n,
-                                                       Ctrl *__restrict__ c, const int *__restrict__ gate) {
+__global__ void __launch_bounds__(RUNS_NT)
+k_tile_order(const typename Key<KT>::U *__restrict__ tmin, const typename Key<KT>::U *__restrict__ tmax,
+             long long n, long long ts, long long tiles, int strict, int cur0, int *__restrict__ dest,
+             Ctrl *__restrict__ c) {
     griddep_wait();
-    __shared__ unsigned int s_v[FEW_MAX];
-    __shared__ unsigned int s_k;
-    __shared__ int s_last;
-    __shared__ unsigned long long s_set[FEW_SLOTS];
-    __shared__ unsigned int s_n;
+    if (call_mode(c, n) != MODE_SORT || !cur0) return;
+    __shared__ int s_carry;
+    __shared__ int s_any;
+    const int t = threadIdx.x;
+    const long long full_tiles = n / ts;           // tiles of ts keys; a short last tile never moves
+    // desc(q): tiles q-1 and q are full and in descending order (and not in
+    // ascending order, which also holds when every key of both is equal)
+    auto desc = [&](long long q) -> bool {
+        if (q <= 0 || q >= full_tiles) return false;
+        const bool down = strict ? tmax[q] < tmin[q - 1] : tmax[q] <= tmin[q - 1];
+        return down && !(tmax[q - 1] <= tmin[q]);
+    };
+    if (t == 0) { s_carry = 0; s_any = 0; }
+    __syncthreads();
+    // forward: the first tile of each tile's chain, into dest
+    for (long long t0 = 0; t0 < tiles; t0 += RUNS_NT) {
+        const long long q = t0 + t;
+        int start = (q < tiles && !desc(q)) ? (int)q : -1;
+        // block-wide running maximum (chains start where desc is false)
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, start, o);
+            if ((t & 31) >= o) start = max(start, u);
+        }
+        __shared__ int s_w[RUNS_NT / 32];
+        if ((t & 31) == 31) s_w[t >> 5] = start;
+        __syncthreads();
+        int before = s_carry;
+        for (int w = 0; w < (t >> 5); ++w) before = max(before, s_w[w]);
+        start = max(start, before);
+        if (q < tiles) dest[q] = start;
+        __syncthreads();
+        if (t == RUNS_NT - 1) s_carry = start;
+        __syncthreads();
+    }
+    // backward: the last tile of each chain; dest[q] = first + last - q
+    if (t == 0) s_carry = (int)tiles - 1;
+    __syncthreads();
+    for (long long t1 = tiles; t1 > 0; t1 -= RUNS_NT) {
+        const long long q = t1 - RUNS_NT + t;      // q < 0 for the first chunk's missing lanes
+        int end = (q >= 0 && q < tiles && !desc(q + 1)) ? (int)q : INT_MAX;
+        // block-wide running minimum from the right
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_down_sync(0xffffffffu, end, o);
+            if ((t & 31) + o < 32) end = min(end, u);
+        }
+        __shared__ int s_w2[RUNS_NT / 32];
+        if ((t & 31) == 0) s_w2[t >> 5] = end;
+        __syncthreads();
+        int after = s_carry;
+        for (int w = (t >> 5) + 1; w < RUNS_NT / 32; ++w) after = min(after, s_w2[w]);
+        end = min(end, after);
+        if (q >= 0 && q < tiles) {
+            const int first = dest[q];
+            // reverse the chain only if that leaves fewer natural runs: its
+            // L - 1 inner links become ascending, the links with the tiles on
+            // either side may be lost or made
+            auto asc = [&](long long x, long long y) -> int {   // tile x then tile y, in order
+                return (x >= 0 && y < tiles && tmax[x] <= tmin[y]) ? 1 : 0;
+            };
+            const int gain = (end - first) + asc(first - 1, end) + asc(first, end + 1) - asc(first - 1, first) -
+                             asc(end, end + 1);
+            const bool flip = end > first && gain > 0;
+            if (flip) s_any = 1;
+            dest[q] = flip ? first + end - (int)q : (int)q;
+        }
+        __syncthreads();
+        if (t == 0) s_carry = end;
+        __syncthreads();
+    }
+    if (t == 0 && s_any) c->tile_perm = 1;
+}
+
+// Few distinct keys, step 1: FEW_SAMPLE keys spread over the whole array go
+// into the call's set of distinct order images, in two phases.  Phase A
+// (one CTA) takes the first FEW_SAMPLE_A keys of the sample; if
+// they hold more than FEW_A_MAX distinct images the input has more than
+// FEW_MAX (drawing FEW_SAMPLE_A keys from at most FEW_MAX values gives about
+// 2,590 distinct ones when all are equally likely, fewer otherwise), the set
+// is closed and phase B returns at once.  Phase B (k_few_sample2) takes the
+// rest of the sample; its last CTA to finish (a ticket after a fence), if the
+// call would sort and the set holds at most FEW_MAX images, sorts the set (a
+// bitonic network in shared memory) into FewTables::sorted as the candidate.
+// The counting pass checks every key against the set, so a sample that misses
+// a key only costs that pass.  This is the multiway form of the fat (3-way)
+// split of the paper's quicksorts (Section 4, techniques (d) and (g)): every
+// distinct key is a pivot, keys equal to a pivot need no further comparisons,
+// so the split alone sorts the input.
+enum { FEW_SAMPLE = 65536, FEW_SAMPLE_A = 4096, FEW_A_MAX = 3072, FEW_NT2 = 1024 };
+
+// This CTA's `per` samples (sample indices from `first`) into a shared-memory
+// set, then its images not yet in the call's set into it; the number it added
+// goes to the call's count once.  Returns the CTA's added count (thread 0).
+template <int KT, int NTH, int LOG2>
+__device__ __forceinline__ void few_sample_cta(const typename Key<KT>::T *__restrict__ keys, long long n,
+                                               long long first, Ctrl *__restrict__ c, FewTables *__restrict__ ft,
+                                               unsigned long long *s_set, unsigned int *s_n, unsigned int *s_new,
+                                               int *s_over) {
+    const int t = threadIdx.x;
+    for (int i = t; i < (1 << LOG2); i += NTH) s_set[i] = 0ull;
+    if (t == 0) { *s_n = 0u; *s_over = 0; *s_new = 0u; }
+    __syncthreads();
+    const long long i = first + t;
+    if (i < FEW_SAMPLE && n > 0)
+        few_insert<LOG2>(s_set, s_n, s_over, (unsigned int)Key<KT>::ord(__ldg(keys + (i * n) / FEW_SAMPLE)),
+                         NTH);
+    __syncthreads();
+    if (*s_over) {
+        if (t == 0) atomicExch(&c->few_over, 1);
+    } else {
+        for (int q = t; q < (1 << LOG2); q += NTH)
+            if (s_set[q] != 0ull && !((volatile int *)&c->few_over)[0])
+                few_insert<FEW_SLOTS_LOG2>(ft->slot, s_new, &c->few_over, (unsigned int)(s_set[q] - 1ull),
+                                           0xffffffffu);
+    }
+    __syncthreads();
+    if (t == 0 && *s_new && atomicAdd(&c->few_n, *s_new) + *s_new > (unsigned int)FEW_MAX)
+        atomicExch(&c->few_over, 1);
+}
+
+// Phase A: one CTA of FEW_NT2 threads puts the first FEW_SAMPLE_A samples
+// into a set in shared memory (FEW_A_SLOTS slots, dynamic shared memory); more
+// than FEW_A_MAX distinct images close the call's set at once, else the
+// images go into the call's set in global memory.
+enum { FEW_A_SLOTS_LOG2 = 13, FEW_A_SLOTS = 1 << FEW_A_SLOTS_LOG2 };
+template <int KT>
+__global__ void __launch_bounds__(FEW_NT2) k_few_sample(const typename Key<KT>::T *__restrict__ keys, long long n,
+                                                        Ctrl *__restrict__ c, FewTables *__restrict__ ft,
+                                                        const int *__restrict__ gate) {
+    griddep_wait();
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned long long *s_tab = reinterpret_cast<unsigned long long *>(smem);
+    __shared__ unsigned int s_n, s_new;
     __shared__ int s_over;
     if (gate && *gate == 0) return;
     const int t = threadIdx.x;
-    if (t < FEW_SLOTS) s_set[t] = 0ull;
-    if (t == 0) { s_n = 0u; s_over = 0; }
+    for (int q = t; q < FEW_A_SLOTS; q += FEW_NT2) s_tab[q] = 0ull;
+    if (t == 0) { s_n = 0u; s_new = 0u; s_over = 0; }
     __syncthreads();
-    // this CTA's samples go into a shared-memory set first; only a CTA that saw
-    // at most FEW_MAX distinct keys touches the call's set in global memory
-    const long long i = (long long)blockIdx.x * FEW_NT + t;
-    if (i < FEW_SAMPLE && n > 0)
-        few_insert(s_set, &s_n, &s_over, (unsigned int)Key<KT>::ord(__ldg(keys + (i * n) / FEW_SAMPLE)));
+    if (n > 0)
+        for (int i = t; i < FEW_SAMPLE_A; i += FEW_NT2)
+            few_insert<FEW_A_SLOTS_LOG2>(s_tab, &s_n, &s_over,
+                                         (unsigned int)Key<KT>::ord(__ldg(keys + ((long long)i * n) / FEW_SAMPLE)),
+                                         FEW_A_MAX);
     __syncthreads();
-    if (s_over) {
+    if (s_over) {                                  // too many distinct keys: the path is off
         if (t == 0) atomicExch(&c->few_over, 1);
-    } else if (t < FEW_SLOTS && s_set[t] != 0ull && !((volatile int *)&c->few_over)[0]) {
-        few_insert(c->few_slot, &c->few_n, &c->few_over, (unsigned int)(s_set[t] - 1ull));
+        return;
     }
+    for (int q = t; q < FEW_A_SLOTS; q += FEW_NT2)
+        if (s_tab[q] != 0ull)
+            few_insert<FEW_SLOTS_LOG2>(ft->slot, &s_new, &c->few_over, (unsigned int)(s_tab[q] - 1ull), 0xffffffffu);
     __syncthreads();
+    if (t == 0) atomicAdd(&c->few_n, s_new);
+}
+
+template <int KT>
+__global__ void __launch_bounds__(FEW_NT2) k_few_sample2(const typename Key<KT>::T *__restrict__ keys, long long n,
+                                                         Ctrl *__restrict__ c, FewTables *__restrict__ ft,
+                                                         const int *__restrict__ gate) {
+    griddep_wait();
+    __shared__ unsigned int s_v[FEW_MAX];
+    __shared__ unsigned long long s_set[2 * FEW_NT2];
+    __shared__ unsigned int s_n, s_new, s_k;
+    __shared__ int s_over, s_last;
+    if (gate && *gate == 0) return;
+    if (((volatile int *)&c->few_over)[0]) return;
+    const int t = threadIdx.x;
+    few_sample_cta<KT, FEW_NT2, 11>(keys, n, FEW_SAMPLE_A + (long long)blockIdx.x * FEW_NT2, c, ft, s_set, &s_n,
+                                    &s_new, &s_over);
     if (t == 0) {
         __threadfence();
-        s_last = atomicAdd(&c->few_ticket, 1u) == gridDim.x - 1;
+        s_last = atomicAdd(&c->few_ticket2, 1u) == gridDim.x - 1;
         s_k = 0u;
     }
     __syncthreads();
@@ -178,56 +367,87 @@ __global__ void __launch_bounds__(FEW_NT) k_few_sample(const typename Key<KT>::T
     const int over = ((volatile int *)&c->few_over)[0];
     const unsigned int nd = ((volatile unsigned int *)&c->few_n)[0];
     if (over || nd == 0u || nd > (unsigned int)FEW_MAX) return;
-    if (t < FEW_SLOTS) {
-        const unsigned long long v = ((volatile unsigned long long *)c->few_slot)[t];
+    for (int q = t; q < FEW_SLOTS; q += FEW_NT2) {
+        const unsigned long long v = ((volatile unsigned long long *)ft->slot)[q];
         if (v != 0ull) {
-            const unsigned int q = atomicAdd(&s_k, 1u);
-            if (q < (unsigned int)FEW_MAX) s_v[q] = (unsigned int)(v - 1ull);
+            const unsigned int r = atomicAdd(&s_k, 1u);
+            if (r < (unsigned int)FEW_MAX) s_v[r] = (unsigned int)(v - 1ull);
         }
     }
     __syncthreads();
     const unsigned int k = s_k;
     if (k != nd) return;                           // cannot happen; the ordinary sort then runs
-    if (t < (int)k) {
-        unsigned int r = 0;
-        for (unsigned int q = 0; q < k; ++q) r += s_v[q] < s_v[t];
-        c->few_sorted[r] = s_v[t];
-    }
+    unsigned int P = 1;
+    while (P < k) P <<= 1;
+    for (unsigned int q = k + t; q < P; q += FEW_NT2) s_v[q] = 0xffffffffu;
     __syncthreads();
-    if (t == 0) c->few_cand = 1;
+    // bitonic sort of s_v[0, P) ascending
+    for (unsigned int size = 2; size <= P; size <<= 1) {
+        for (unsigned int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (unsigned int q = t; q < P / 2; q += FEW_NT2) {
+                const unsigned int lo = 2 * stride * (q / stride) + (q % stride), hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const unsigned int a = s_v[lo], b = s_v[hi];
+                if ((a > b) == up) { s_v[lo] = b; s_v[hi] = a; }
+            }
+            __syncthreads();
+        }
+    }
+    for (unsigned int q = t; q < k; q += FEW_NT2) ft->sorted[q] = s_v[q];
+    __syncthreads();
+    if (t == 0) {
+        __threadfence();
+        c->few_cand = 1;
+    }
 }
 
-// Few distinct keys, step 2: counts the keys equal to each candidate image (a
-// binary search over at most FEW_MAX images per key, one shared-memory
-// histogram per warp); a key outside the set raises few_miss and the ordinary
-// sort runs instead.
+// Few distinct keys, step 2: counts the keys equal to each candidate image.
+// Each CTA builds, in shared memory, a hash table from every image of the
+// sorted set to its rank (FEW_A_SLOTS slots of image << 32 | rank + 1, at most
+// half full), looks each key up in it (about 1.5 probes) and adds one to its
+// own histogram, which goes to row blockIdx.x of `hist` with plain stores; a
+// key outside the set raises few_miss and the ordinary sort runs instead.  At
+// most FEW_COUNT_CTAS CTAs; dynamic shared memory: few_count_smem().
+enum { FEW_COUNT_CTAS = 160, FEW_COUNT_NT = 1024 };
+constexpr size_t few_count_smem() { return (size_t)FEW_A_SLOTS * 8 + (size_t)FEW_MAX * 4; }
 template <int KT>
-__global__ void __launch_bounds__(256) k_few_count(const typename Key<KT>::T *__restrict__ keys, long long n,
-                                                   Ctrl *__restrict__ c) {
+__global__ void __launch_bounds__(FEW_COUNT_NT) k_few_count(const typename Key<KT>::T *__restrict__ keys, long long n,
+                                                            Ctrl *__restrict__ c, const FewTables *__restrict__ ft,
+                                                            unsigned int *__restrict__ hist) {
     griddep_wait();
     typedef Key<KT> K;
     typedef typename K::T T;
-    constexpr int NW = 256 / 32;
-    __shared__ unsigned int s_v[FEW_MAX];
-    __shared__ unsigned int s_h[NW][FEW_MAX];    // one histogram per warp
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned long long *s_tab = reinterpret_cast<unsigned long long *>(smem);
+    unsigned int *s_h = reinterpret_cast<unsigned int *>(s_tab + FEW_A_SLOTS);
     if (!c->few_cand) return;
     const int t = threadIdx.x;
     const int k = (int)c->few_n;
-    if (t < FEW_MAX) s_v[t] = t < k ? c->few_sorted[t] : 0xffffffffu;
-    for (int q = t; q < NW * FEW_MAX; q += 256) (&s_h[0][0])[q] = 0u;
+    for (int q = t; q < FEW_A_SLOTS; q += FEW_COUNT_NT) s_tab[q] = 0ull;
+    for (int q = t; q < k; q += FEW_COUNT_NT) s_h[q] = 0u;
     __syncthreads();
-    unsigned int *h = s_h[t >> 5];
+    constexpr unsigned int MASK = FEW_A_SLOTS - 1;
+    for (int q = t; q < k; q += FEW_COUNT_NT) {    // the images are distinct: one slot each
+        const unsigned int u = ft->sorted[q];
+        const unsigned long long v = ((unsigned long long)u << 32) | (unsigned long long)(q + 1);
+        for (unsigned int h = (u * 2654435761u) >> (32 - FEW_A_SLOTS_LOG2), probe = 0; probe < FEW_A_SLOTS;
+             ++probe, h = (h + 1) & MASK)
+            if (atomicCAS(&s_tab[h], 0ull, v) == 0ull) break;
+    }
+    __syncthreads();
     bool miss = false;
     auto count = [&](T key) {
         const unsigned int u = (unsigned int)K::ord(key);
-        int lo = 0, hi = k - 1;                    // the last image <= u
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (s_v[mid] <= u) lo = mid;
-            else hi = mid - 1;
+        unsigned int h = (u * 2654435761u) >> (32 - FEW_A_SLOTS_LOG2);
+        for (int probe = 0; probe < FEW_A_SLOTS; ++probe, h = (h + 1) & MASK) {   // ends at an empty slot
+            const unsigned long long e2 = s_tab[h];
+            if (e2 == 0ull) { miss = true; return; }
+            if ((unsigned int)(e2 >> 32) == u) {
+                atomicAdd(&s_h[(unsigned int)e2 - 1u], 1u);
+                return;
+            }
         }
-        if (s_v[lo] != u) miss = true;             // not in the sample's set
-        else atomicAdd(&h[lo], 1u);
+        miss = true;
     };
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long gtid = (long long)blockIdx.x * blockDim.x + t;
@@ -244,12 +464,20 @@ __global__ void __launch_bounds__(256) k_few_count(const typename Key<KT>::T *__
     for (long long i = tail + gtid; i < n; i += stride) count(__ldg(keys + i));
     if (miss && !((volatile int *)&c->few_miss)[0]) atomicExch(&c->few_miss, 1);
     __syncthreads();
-    if (t < k) {
-        unsigned int sum = 0;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) sum += s_h[w][t];
-        if (sum) atomicAdd(&c->few_count[t], (unsigned long long)sum);
-    }
+    for (int q = t; q < k; q += FEW_COUNT_NT) hist[(long long)blockIdx.x * FEW_MAX + q] = s_h[q];
+}
+
+// Few distinct keys, step 2b: the count of every distinct image, summed over
+// the rows of the count pass's histograms (one thread per image).
+static __global__ void __launch_bounds__(256) k_few_reduce(const unsigned int *__restrict__ hist, int rows,
+                                                    const Ctrl *__restrict__ c, FewTables *__restrict__ ft) {
+    griddep_wait();
+    if (!c->few_cand || c->few_miss) return;
+    const int j = blockIdx.x * 256 + threadIdx.x;
+    if (j >= (int)c->few_n) return;
+    unsigned long long s = 0;
+    for (int r = 0; r < rows; ++r) s += hist[(long long)r * FEW_MAX + j];
+    ft->count[j] = s;
 }
 
 // Few distinct keys, step 3: when every key was in the set, writes the sorted
@@ -258,24 +486,55 @@ __global__ void __launch_bounds__(256) k_few_count(const typename Key<KT>::T *__
 // the ordinary sequence then returns at once.
 template <int KT>
 __global__ void __launch_bounds__(256) k_few_write(typename Key<KT>::T *__restrict__ keys, long long n,
-                                                   Ctrl *__restrict__ c) {
+                                                   Ctrl *__restrict__ c, const FewTables *__restrict__ ft) {
     griddep_wait();
     typedef Key<KT> K;
-    typedef typename K::T T;
+    constexpr int PER = FEW_MAX / 256;             // counts per thread in the scan
     __shared__ unsigned long long s_start[FEW_MAX + 1];
-    __shared__ T s_key[FEW_MAX];
+    __shared__ unsigned long long s_part[256];
     if (!c->few_cand || c->few_miss) return;
     const int t = threadIdx.x;
     if (blockIdx.x == 0 && t == 0) c->few_active = 1;
     const int k = (int)c->few_n;
-    if (t == 0) {
-        unsigned long long a = 0;
-        for (int q = 0; q < k; ++q) { s_start[q] = a; a += c->few_count[q]; }
-        for (int q = k; q <= FEW_MAX; ++q) s_start[q] = a;
-    }
-    if (t < k) s_key[t] = K::unord((typename K::U)c->few_sorted[t]);
+    // s_start[q] = keys before distinct key q (an exclusive scan of the
+    // counts): coalesced loads into shared memory, then PER contiguous per thread
+    for (int q = t; q < FEW_MAX; q += 256) s_start[q] = q < k ? ft->count[q] : 0ull;
     __syncthreads();
-    // the last q with s_start[q] <= i
+    unsigned long long run = 0;
+#pragma unroll
+    for (int e = 0; e < PER; ++e) run += s_start[t * PER + e];
+    s_part[t] = run;
+    __syncthreads();
+    if (t < 32) {
+        unsigned long long acc = 0;
+        for (int w = 0; w < 8; ++w) {              // 8 partial sums per lane, then a warp scan
+            const unsigned long long x = s_part[t * 8 + w];
+            s_part[t * 8 + w] = acc;
+            acc += x;
+        }
+        unsigned long long incl = acc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (t >= o) incl += u;
+        }
+        const unsigned long long excl = incl - acc;
+        for (int w = 0; w < 8; ++w) s_part[t * 8 + w] += excl;
+    }
+    __syncthreads();
+    unsigned long long cnt[PER];
+#pragma unroll
+    for (int e = 0; e < PER; ++e) cnt[e] = s_start[t * PER + e];
+    __syncthreads();
+    run = s_part[t];
+#pragma unroll
+    for (int e = 0; e < PER; ++e) {
+        s_start[t * PER + e] = run;
+        run += cnt[e];
+    }
+    if (t == 255) s_start[FEW_MAX] = run;
+    __syncthreads();
+    // the last q < k with s_start[q] <= i
     auto which = [&](long long i) {
         int lo = 0, hi = k - 1;
         while (lo < hi) {
@@ -285,25 +544,39 @@ __global__ void __launch_bounds__(256) k_few_write(typename Key<KT>::T *__restri
         }
         return lo;
     };
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    const long long gtid = (long long)blockIdx.x * blockDim.x + t;
+    auto key_of = [&](int j) { return K::unord((typename K::U)__ldg(ft->sorted + j)); };
     if ((((uintptr_t)keys) & 15) == 0) {
+        // each warp writes chunks of FEW_W_CHUNK consecutive 16-byte groups,
+        // lane l the groups l, l + 32, ...: one search per lane per chunk, then
+        // a key index that only moves forward
         const long long nv = n / 4;
         uint4 *q4 = reinterpret_cast<uint4 *>(keys);
-        for (long long v = gtid; v < nv; v += stride) {
-            const long long i = 4 * v;
-            int j = which(i);
-            uint32_t e[4];
+        const int lane = t & 31;
+        const long long warps = (long long)gridDim.x * (blockDim.x / 32);
+        const long long wid = (long long)blockIdx.x * (blockDim.x / 32) + (t >> 5);
+        constexpr int FEW_W_CHUNK = 32 * 8;
+        for (long long c0 = wid * FEW_W_CHUNK; c0 < nv; c0 += warps * FEW_W_CHUNK) {
+            const long long end = min(c0 + FEW_W_CHUNK, nv);
+            long long v = c0 + lane;
+            if (v >= end) continue;
+            int j = which(4 * v);
+            for (; v < end; v += 32) {
+                const long long i = 4 * v;
+                uint32_t e4[4];
 #pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                while (j + 1 < k && (long long)s_start[j + 1] <= i + m) ++j;
-                e[m] = (uint32_t)s_key[j];
+                for (int m = 0; m < 4; ++m) {
+                    while (j + 1 < k && (long long)s_start[j + 1] <= i + m) ++j;
+                    e4[m] = (uint32_t)key_of(j);
+                }
+                q4[v] = make_uint4(e4[0], e4[1], e4[2], e4[3]);
             }
-            q4[v] = make_uint4(e[0], e[1], e[2], e[3]);
         }
-        for (long long i = 4 * nv + gtid; i < n; i += stride) keys[i] = s_key[which(i)];
+        const long long stride = (long long)gridDim.x * blockDim.x;
+        for (long long i = 4 * nv + (long long)blockIdx.x * blockDim.x + t; i < n; i += stride)
+            keys[i] = key_of(which(i));
     } else {
-        for (long long i = gtid; i < n; i += stride) keys[i] = s_key[which(i)];
+        const long long stride = (long long)gridDim.x * blockDim.x;
+        for (long long i = (long long)blockIdx.x * blockDim.x + t; i < n; i += stride) keys[i] = key_of(which(i));
     }
 }
 
@@ -346,11 +619,11 @@ __global__ void k_reverse(typename Key<KT>::T *__restrict__ k, uint32_t *__restr
 // Sorts tile blockIdx.x of NT*IPT keys; records the tile's smallest and
 // largest key images in tile_lo / tile_hi (if given) for the pass planner.
 template <int KT, int NT, int IPT, bool VALS>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, Shape<sizeof(typename Key<KT>::T), VALS>::SORT_MINB)
 k_block_sort(const typename Key<KT>::T *in_k, const uint32_t *in_v, typename Key<KT>::T *out_k,
              uint32_t *out_v, long long n, const Ctrl *__restrict__ c,
              typename Key<KT>::U *__restrict__ tile_lo, typename Key<KT>::U *__restrict__ tile_hi,
-             typename Key<KT>::U *__restrict__ samp, int mv) {
+             typename Key<KT>::U *__restrict__ samp, int mv, const int *__restrict__ dest) {
     griddep_wait();
     typedef Key<KT> K;
     typedef typename K::U U;
@@ -362,6 +635,12 @@ k_block_sort(const typename Key<KT>::T *in_k, const uint32_t *in_v, typename Key
     const int t = threadIdx.x;
     const long long base = (long long)blockIdx.x * NV;
     const int cnt = (int)(n - base < (long long)NV ? n - base : (long long)NV);
+    // the tile's place in the output: reversed chains of descending tiles
+    // (k_tile_order) land in reversed order; every moved tile is full.  Read
+    // where the tile is written, so it is not held through the sort.
+    auto out_tile = [&]() -> long long {
+        return (dest && c && c->tile_perm) ? (long long)dest[blockIdx.x] : (long long)blockIdx.x;
+    };
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
         const int idx = i * NT + t;
@@ -383,32 +662,34 @@ k_block_sort(const typename Key<KT>::T *in_k, const uint32_t *in_v, typename Key
     const int any_nondesc = __syncthreads_or(nondesc);
     // first and last key of every merge tile of mv keys in this tile, for the
     // first merge pass's split search; `rev` reads the tile back to front
-    auto samples = [&](bool rev) {
+    auto samples = [&](bool rev, long long otile) {
         if (!samp) return;
         const int per = NV / mv;
         for (int q = t; q < per && q * mv < cnt; q += NT) {
             const int f = q * mv, l = min(f + mv, cnt) - 1;
-            samp[2 * ((long long)blockIdx.x * per + q)] = rev ? s[cnt - 1 - f] : s[f];
-            samp[2 * ((long long)blockIdx.x * per + q) + 1] = rev ? s[cnt - 1 - l] : s[l];
+            samp[2 * (otile * per + q)] = rev ? s[cnt - 1 - f] : s[f];
+            samp[2 * (otile * per + q) + 1] = rev ? s[cnt - 1 - l] : s[l];
         }
     };
     if (!any_desc) {                       // already ascending
-        if (t == 0 && tile_lo) { tile_lo[blockIdx.x] = s[0]; tile_hi[blockIdx.x] = s[cnt - 1]; }
-        samples(false);
-        if (out_k != in_k) {
+        const long long otile = out_tile(), obase = otile * NV;
+        if (t == 0 && tile_lo) { tile_lo[otile] = s[0]; tile_hi[otile] = s[cnt - 1]; }
+        samples(false, otile);
+        if (out_k != in_k || obase != base) {
             for (int idx = t; idx < cnt; idx += NT) {
-                out_k[base + idx] = K::unord(s[idx]);
-                if (VALS) out_v[base + idx] = sv[idx];
+                out_k[obase + idx] = K::unord(s[idx]);
+                if (VALS) out_v[obase + idx] = sv[idx];
             }
         }
         return;
     }
     if (!any_nondesc) {                    // strictly descending: reverse
-        if (t == 0 && tile_lo) { tile_lo[blockIdx.x] = s[cnt - 1]; tile_hi[blockIdx.x] = s[0]; }
-        samples(true);
+        const long long otile = out_tile(), obase = otile * NV;
+        if (t == 0 && tile_lo) { tile_lo[otile] = s[cnt - 1]; tile_hi[otile] = s[0]; }
+        samples(true, otile);
         for (int idx = t; idx < cnt; idx += NT) {
-            out_k[base + idx] = K::unord(s[cnt - 1 - idx]);
-            if (VALS) out_v[base + idx] = sv[cnt - 1 - idx];
+            out_k[obase + idx] = K::unord(s[cnt - 1 - idx]);
+            if (VALS) out_v[obase + idx] = sv[cnt - 1 - idx];
         }
         return;
     }
@@ -427,149 +708,154 @@ k_block_sort(const typename Key<KT>::T *in_k, const uint32_t *in_v, typename Key
         if (VALS) sv[t * IPT + i] = v[i];
     }
     __syncthreads();
-    if (t == 0 && tile_lo) { tile_lo[blockIdx.x] = s[0]; tile_hi[blockIdx.x] = s[cnt - 1]; }
-    samples(false);
+    const long long otile = out_tile(), obase = otile * NV;
+    if (t == 0 && tile_lo) { tile_lo[otile] = s[0]; tile_hi[otile] = s[cnt - 1]; }
+    samples(false, otile);
     for (int idx = t; idx < cnt; idx += NT) {
-        out_k[base + idx] = K::unord(s[idx]);
-        if (VALS) out_v[base + idx] = sv[idx];
+        out_k[obase + idx] = K::unord(s[idx]);
+        if (VALS) out_v[obase + idx] = sv[idx];
     }
 }
 
-// Pass planner (after the block sort): a merged run's smallest and largest
-// keys are the smallest and largest of its tiles', so whether the two runs of a
-// pair at pass p are already in order (A.last <= B.first) is known for every
-// pass from the tile extremes alone.  Adds to c->unordered[p] the number of
-// pairs of pass p that must be merged; a pass with none is skipped (technique
-// (f) applied to whole passes).
+// Run planner (after the block sort), the natural runs of Section 3 at the
+// granularity of whole tiles: tile t starts a new run unless the previous
+// tile's largest key is <= its smallest (then the two sorted tiles are one
+// sorted run already).  Merge step s of fan-in f merges groups of f
+// consecutive runs of the step before, i.e. groups of f^(s+1) natural runs
+// (policy e1 over the input's own runs), so an input made of m presorted
+// stretches needs ceil(log_f(m)) steps whatever its length; an input with no
+// presorted stretch longer than a tile has one run per tile.
 //
-// Each CTA reduces a chunk of PLAN_CHUNK tiles in shared memory, which settles
-// every pass whose pairs lie inside one chunk; the last CTA to finish (a ticket
-// taken after a fence) settles the remaining passes from the chunks' extremes.
-enum { PLAN_CHUNK = 2048, PLAN_LEVELS = 11 };   // 2^11 tiles per chunk
-
-// Whether merge step s (binary levels [l0, l0 + nl)) has any run pair out of
-// order; a step whose levels are all in order is skipped.
-__device__ __forceinline__ bool step_needed(const Ctrl *c, int l0, int nl) {
-    const volatile int *u = c->unordered;
-    return u[l0] != 0 || (nl > 1 && u[l0 + 1] != 0);
-}
-
-// Once every unordered[level] is final: the buffer before each merge step (and
-// after the last), so later kernels read one byte instead of recounting flips.
-__device__ __forceinline__ void record_buffers(Ctrl *c, int cur0, int levels, bool fan4) {
-    int cur = cur0;
-    const int steps = merge_step_count(levels, fan4);
-    for (int s = 0; s < steps; ++s) {
-        int l0, nl;
-        merge_step_levels(levels, fan4, s, &l0, &nl);
-        c->src_buf[s] = (signed char)cur;
-        cur ^= step_needed(c, l0, nl) ? 1 : 0;
-    }
-    c->src_buf[steps] = (signed char)cur;
-}
-
+// One CTA: rs0[q] = the first tile of natural run q (q < nruns), rs0[nruns] =
+// tiles; nsteps = ceil(log_f(nruns)); src_buf[s] = the buffer holding the data
+// before step s (the block sort's output buffer is cur0).  Steps s >= nsteps of
+// the launched sequence return at once.
 template <int KT>
-__global__ void __launch_bounds__(1024)
-k_plan(const typename Key<KT>::U *__restrict__ lo, const typename Key<KT>::U *__restrict__ hi,
-       typename Key<KT>::U *__restrict__ chunk_lo, typename Key<KT>::U *__restrict__ chunk_hi,
-       long long n, long long tiles, int passes, int cur0, int fan4, Ctrl *__restrict__ c) {
+__global__ void __launch_bounds__(RUNS_NT)
+k_runs(const typename Key<KT>::U *__restrict__ lo, const typename Key<KT>::U *__restrict__ hi, long long n,
+       long long tiles, int fan, int cur0, int *__restrict__ rs0, Ctrl *__restrict__ c) {
     griddep_wait();
-    typedef typename Key<KT>::U U;
     if (call_mode(c, n) != MODE_SORT) return;
-    __shared__ U s_lo[PLAN_CHUNK], s_hi[PLAN_CHUNK];
-    __shared__ unsigned int s_cnt;
-    __shared__ int s_last;
-    const int t = threadIdx.x;
-    const long long base = (long long)blockIdx.x * PLAN_CHUNK;
-    const int cnt = (int)min((long long)PLAN_CHUNK, tiles - base);
-    for (int i = t; i < cnt; i += blockDim.x) { s_lo[i] = lo[base + i]; s_hi[i] = hi[base + i]; }
-    // run r of pass p is kept at index r << p: the pair of runs starting at
-    // ia = 2j << p and ib = ia + (1 << p) folds into ia
-    const int inner = passes < PLAN_LEVELS ? passes : PLAN_LEVELS;
-    for (int p = 0; p < inner; ++p) {
-        if (t == 0) s_cnt = 0;
+    __shared__ int s_warp[RUNS_NT / 32];
+    __shared__ int s_total;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    int base = 0;
+    int far = 0;                                   // some tile's keys exceed the tile's two places on
+    for (long long t0 = 0; t0 < tiles; t0 += RUNS_NT) {
+        const long long q = t0 + t;
+        const bool first = q < tiles && (q == 0 || hi[q - 1] > lo[q]);
+        if (q + 2 < tiles && hi[q] > lo[q + 2]) far = 1;
+        const unsigned ball = __ballot_sync(0xffffffffu, first);
+        if (lane == 0) s_warp[wid] = __popc(ball);
         __syncthreads();
-        const int stride = 1 << p;
-        unsigned int mine = 0;
-        for (int ia = 2 * stride * t; ia < cnt; ia += 2 * stride * blockDim.x) {
-            const int ib = ia + stride;
-            if (ib < cnt) {
-                mine += s_hi[ia] > s_lo[ib];
-                s_lo[ia] = s_lo[ia] < s_lo[ib] ? s_lo[ia] : s_lo[ib];
-                s_hi[ia] = s_hi[ia] > s_hi[ib] ? s_hi[ia] : s_hi[ib];
+        if (wid == 0) {
+            const int v = s_warp[lane];
+            int incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += u;
             }
+            s_warp[lane] = incl - v;               // exclusive prefix of the warps' counts
+            if (lane == 31) s_total = incl;
         }
-        mine = __reduce_add_sync(0xffffffffu, mine);
-        if ((t & 31) == 0 && mine) atomicAdd(&s_cnt, mine);
         __syncthreads();
-        if (t == 0 && s_cnt) atomicAdd(&c->unordered[p], (int)s_cnt);
+        if (first) rs0[base + s_warp[wid] + __popc(ball & ((1u << lane) - 1u))] = (int)q;
+        base += s_total;
+        __syncthreads();
     }
-    // the chunk is fully reduced into index 0
+    far = __syncthreads_or(far);
     if (t == 0) {
-        chunk_lo[blockIdx.x] = s_lo[0];
-        chunk_hi[blockIdx.x] = s_hi[0];
-        __threadfence();
-        s_last = atomicAdd(&c->plan_ticket, 1u) == gridDim.x - 1;
+        rs0[base] = (int)tiles;
+        int steps = 0;
+        for (long long m = base; m > 1; m = (m + fan - 1) / fan) ++steps;
+        c->nruns = base;
+        c->nsteps = steps;
+        c->repair = (!far && steps > 0 && tiles >= 3) ? 1 : 0;
+        for (int s = 0; s <= steps; ++s) c->src_buf[s] = (signed char)(cur0 ^ (s & 1));
     }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    if (passes <= PLAN_LEVELS) {
-        if (t == 0) record_buffers(c, cur0, passes, fan4 != 0);
-        return;
-    }
-    const int chunks = (int)gridDim.x;            // at most PLAN_CHUNK chunks (2^22 tiles)
-    for (int i = t; i < chunks; i += blockDim.x) {
-        s_lo[i] = ((volatile U *)chunk_lo)[i];
-        s_hi[i] = ((volatile U *)chunk_hi)[i];
-    }
-    for (int p = PLAN_LEVELS; p < passes; ++p) {
-        if (t == 0) s_cnt = 0;
-        __syncthreads();
-        const int stride = 1 << (p - PLAN_LEVELS);
-        unsigned int mine = 0;
-        for (int ia = 2 * stride * t; ia < chunks; ia += 2 * stride * blockDim.x) {
-            const int ib = ia + stride;
-            if (ib < chunks) {
-                mine += s_hi[ia] > s_lo[ib];
-                s_lo[ia] = s_lo[ia] < s_lo[ib] ? s_lo[ia] : s_lo[ib];
-                s_hi[ia] = s_hi[ia] > s_hi[ib] ? s_hi[ia] : s_hi[ib];
-            }
-        }
-        mine = __reduce_add_sync(0xffffffffu, mine);
-        if ((t & 31) == 0 && mine) atomicAdd(&s_cnt, mine);
-        __syncthreads();
-        if (t == 0) c->unordered[p] = (int)s_cnt;
-    }
-    if (t == 0) record_buffers(c, cur0, passes, fan4 != 0);
 }
 
-// Merge-path split of every merge tile boundary of pass p, one group of
-// 2^lg lanes per boundary (the host picks lg: wide groups take fewer
-// dependent rounds, narrow ones fewer scattered loads when there are many
-// boundaries).
-// The merge-path split of output tile b (outputs from b*nv) of a merge pass
-// over runs of w keys of src: the index in src where the tile's share of run
-// A starts.  A group of 2^lg lanes computes it together (all lanes of the
-// group get it).  samp (optional): the first and last key of every merge
-// tile of src, as recorded when src was written; with it the search first
-// narrows the split to one tile's stretch and then reads keys only there.
+// Neighbour repair, step 1 (when only neighbouring tiles overlap: every
+// tile's keys are <= those of the tile two places on).  For each boundary
+// between tiles t and t + 1 of the block sort's output: the keys of tile t
+// above tile t+1's smallest (a suffix of t) and the keys of tile t+1 below
+// tile t's largest (a prefix of t+1) are the only ones out of order there;
+// win[2t], win[2t+1] = their counts.  A window larger than a merge tile
+// (cap keys) sets repair_fail and the merge steps run instead.  These
+// windows never overlap: a key of tile t below tile t-1's largest is <= tile
+// t+1's smallest.
 template <int KT>
-__device__ __forceinline__ long long merge_split(const typename Key<KT>::T *__restrict__ src, long long n,
-                                                 long long w, int nv, long long b, int lane, int lg,
-                                                 const typename Key<KT>::U *__restrict__ samp) {
+__global__ void __launch_bounds__(256)
+k_repair_plan(const typename Key<KT>::T *__restrict__ uk, const typename Key<KT>::T *__restrict__ sk,
+              const typename Key<KT>::U *__restrict__ lo, const typename Key<KT>::U *__restrict__ hi, long long n,
+              long long ts, long long tiles, int cap, int *__restrict__ win, Ctrl *__restrict__ c) {
+    griddep_wait();
     typedef Key<KT> K;
     typedef typename K::U U;
-    const long long out = min(b * (long long)nv, n);
-    const long long pb = (out / (2 * w)) * (2 * w);
-    const long long a_beg = pb, a_end = min(pb + w, n);
-    const long long b_beg = a_end, b_end = min(pb + 2 * w, n);
-    const long long na = a_end - a_beg, nb = b_end - b_beg, d = out - pb;
+    if (call_mode(c, n) != MODE_SORT || !c->repair) return;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t + 1 >= tiles) return;
+    const typename K::T *src = c->src_buf[0] ? sk : uk;
+    const long long x0 = t * ts, x1 = x0 + ts, y0 = x1, y1 = min(y0 + ts, n);
+    const U ymin = lo[t + 1], xmax = hi[t];
+    long long a = x0, b = x1;                      // first key of tile t above ymin
+    while (a < b) {
+        const long long m = (a + b) >> 1;
+        if (K::ord(src[m]) <= ymin) a = m + 1;
+        else b = m;
+    }
+    long long e = y0, f = y1;                      // first key of tile t+1 not below xmax
+    while (e < f) {
+        const long long m = (e + f) >> 1;
+        if (K::ord(src[m]) < xmax) e = m + 1;
+        else f = m;
+    }
+    const long long na = x1 - a, nb = e - y0;
+    win[2 * t] = (int)min(na, (long long)cap + 1);
+    win[2 * t + 1] = (int)min(nb, (long long)cap + 1);
+    if (na + nb > cap) atomicExch(&c->repair_fail, 1);
+    else if (na && nb) atomicAdd(&c->repair_keys, (unsigned long long)(na + nb));
+}
+
+// Where natural run q starts (n for q >= nruns; keys, not tiles).
+__device__ __forceinline__ long long nrun_pos(const int *__restrict__ rs0, int nruns, long long q, long long ts,
+                                              long long n) {
+    return q >= nruns ? n : min((long long)rs0[q] * ts, n);
+}
+
+// The natural run that holds tile t (the last q with rs0[q] <= t).
+__device__ __forceinline__ long long nrun_of(const int *__restrict__ rs0, int nruns, long long tiles, long long t) {
+    if (nruns == tiles) return t;                  // every tile a run of its own
+    int lo = 0, hi = nruns - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (rs0[mid] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// The merge-path split of output position out of the merge of the adjacent
+// sorted runs A = src[a_beg, a_end) and B = src[a_end, b_end) (run starts and
+// out - a_beg are multiples of nv): the index in src where the share of A of
+// the outputs from `out` on starts.  A group of 2^lg lanes computes it
+// together (all lanes of the group get it).  samp (optional): the first and
+// last key of every merge tile of src, as recorded when src was written; with
+// it the search first narrows the split to one tile's stretch and then reads
+// keys only there.
+template <int KT>
+__device__ __forceinline__ long long merge_split(const typename Key<KT>::T *__restrict__ src, long long a_beg,
+                                                 long long a_end, long long b_end, long long out, int nv,
+                                                 int lane, int lg, const typename Key<KT>::U *__restrict__ samp) {
+    typedef Key<KT> K;
+    typedef typename K::U U;
+    const long long b_beg = a_end;
+    const long long na = a_end - a_beg, nb = b_end - b_beg, d = out - a_beg;
     long long lo = max(0ll, d - nb), hi = min(d, na);
-    if (samp && out < n && hi > lo) {
+    if (samp && out < b_end && hi > lo) {
         // Coarse: the merge-path test at the multiples m = j*nv uses only the
-        // first key of A's tile j and the last key of B's tile d/nv - j - 1;
-        // d, a_beg and b_beg are multiples of nv here.
+        // first key of A's tile j and the last key of B's tile d/nv - j - 1.
         const long long jlo = (lo + nv - 1) / nv, jhi = (hi - 1) / nv, dj = d / nv;
         const long long ta = a_beg / nv, tb = b_beg / nv;
         const long long jt = group_search(jlo, jhi + 1, lane, lg, [&](long long j) {
@@ -589,23 +875,45 @@ __device__ __forceinline__ long long merge_split(const typename Key<KT>::T *__re
     return a_beg + sp;
 }
 
-// Splits of every output tile boundary of pass p, a group of 2^lg lanes per
-// boundary.  The tile samples of the buffer a pass reads are at samp +
-// smt * (that buffer: 0 the caller's, 1 the scratch copy).
+// Split of every output tile boundary b of merge step `step`, whose pairs
+// are consecutive runs of `span` natural runs each (the pairs a 2-way step
+// merges, or the AB and CD pairs of a 4-way step's groups); a group of 2^lg
+// lanes per boundary.  splits[4b .. 4b + 3] = {where the tile's share of A
+// starts, A's start, A's end = B's start, B's end}.  The tile samples of the
+// buffer the step reads are at samp + smt * (that buffer).
 template <int KT>
 __global__ void __launch_bounds__(256)
 k_partition(const typename Key<KT>::T *__restrict__ uk, const typename Key<KT>::T *__restrict__ sk,
-            long long n, long long w, int nv, long long nbound, long long *__restrict__ splits,
-            const Ctrl *__restrict__ c, int step, int l0, int nl, int lg,
+            long long n, long long ts, long long tiles, int nv, long long nbound, long long *__restrict__ splits,
+            const int *__restrict__ rs0, long long span, const Ctrl *__restrict__ c, int step, int lg,
             const typename Key<KT>::U *__restrict__ samp, long long smt) {
     griddep_wait();
     const int lane = threadIdx.x & 31;
     const long long b = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> lg;
     if (b >= nbound) return;                       // uniform across the group
-    if (!step_needed(c, l0, nl)) return;          // also skipped unless the input needs sorting
+    if (step >= steps_of(c)) return;               // also when the input needs no sorting
+    const bool leader = (lane & ((1 << lg) - 1)) == 0;
+    const long long out = b * (long long)nv;
+    if (out >= n) {                                // the end of the array: never a tile's start
+        if (leader)
+            for (int i = 0; i < 4; ++i) splits[4 * b + i] = n;
+        return;
+    }
     const int cur = c->src_buf[step];
-    const long long sp = merge_split<KT>(cur ? sk : uk, n, w, nv, b, lane, lg, samp ? samp + cur * smt : nullptr);
-    if ((lane & ((1 << lg) - 1)) == 0) splits[b] = sp;
+    const int nruns = c->nruns;
+    const long long q = nrun_of(rs0, nruns, tiles, out / ts);
+    const long long p0 = (q / (2 * span)) * (2 * span);
+    const long long a_beg = nrun_pos(rs0, nruns, p0, ts, n);
+    const long long a_end = nrun_pos(rs0, nruns, p0 + span, ts, n);
+    const long long b_end = nrun_pos(rs0, nruns, p0 + 2 * span, ts, n);
+    const long long sp = merge_split<KT>(cur ? sk : uk, a_beg, a_end, b_end, out, nv, lane, lg,
+                                         samp ? samp + cur * smt : nullptr);
+    if (leader) {
+        splits[4 * b + 0] = sp;
+        splits[4 * b + 1] = a_beg;
+        splits[4 * b + 2] = a_end;
+        splits[4 * b + 3] = b_end;
+    }
 }
 
 // Lanes per boundary for k_partition: about SR_PARTITION_LANES searching
@@ -740,13 +1048,20 @@ constexpr size_t merge_tile_smem() {
 // output tile (which must start on a group boundary) leaves with 128-bit
 // stores between scalar head and tail keys.  Keys before a range's start
 // inside its first group are staged and ignored.
+//
+// bar (optional, VEC only): stage the two windows' whole 16-byte stretches by
+// 1-D bulk copies that one thread starts, completed on this mbarrier (the
+// keys past the array's last 16-byte boundary by plain loads), then turn them
+// into order images in place; a tile whose copies do not complete within the
+// wait's limit reports SR_ERR_TIMEOUT in `status` and writes nothing.
 template <int KT, int NT, int IPT, bool VALS, bool VEC>
 __device__ __forceinline__ void merge_tile(const typename Key<KT>::T *__restrict__ src_k,
                                            typename Key<KT>::T *__restrict__ dst_k,
                                            const uint32_t *__restrict__ src_v, uint32_t *__restrict__ dst_v,
                                            long long n, long long out0, int cnt, long long a0, long long a1,
                                            long long b0, typename Key<KT>::U *s, uint32_t *sv,
-                                           typename Key<KT>::U *samp = nullptr, long long tile = 0) {
+                                           typename Key<KT>::U *samp = nullptr, long long tile = 0,
+                                           unsigned long long *bar = nullptr, int *status = nullptr) {
     typedef Key<KT> K;
     typedef typename K::U U;
     typedef typename K::T T;
@@ -756,7 +1071,67 @@ __device__ __forceinline__ void merge_tile(const typename Key<KT>::T *__restrict
     const int acnt = (int)(a1 - a0);
     const int bcnt = cnt - acnt;
     int sa, sb;                                    // staged positions of A[a0] and B[b0]
-    if (VEC) {
+    if (VEC && bar) {
+        const long long g0[2] = {a0 & ~3ll, b0 & ~3ll};
+        const long long ge[2] = {(a1 + 3) & ~3ll, (b0 + bcnt + 3) & ~3ll};
+        const int nag = acnt > 0 ? (int)((ge[0] - g0[0]) >> 2) : 0;
+        const int nbg = bcnt > 0 ? (int)((ge[1] - g0[1]) >> 2) : 0;
+        const int first[2] = {0, nag};
+        const int ng[2] = {nag, nbg};
+        sa = (int)(a0 - g0[0]);
+        sb = 4 * nag + (int)(b0 - g0[1]);
+        const long long n4 = n & ~3ll;
+        if (t == 0) mbar_init(bar, 1);
+        __syncthreads();
+        if (t == 0) {
+            unsigned bytes = 0;
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const long long hi = min(g0[i] + 4ll * ng[i], n4);
+                if (hi > g0[i]) bytes += (unsigned)((hi - g0[i]) * (sizeof(T) + (VALS ? 4 : 0)));
+            }
+            mbar_arrive_expect(bar, bytes);
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const long long hi = min(g0[i] + 4ll * ng[i], n4);
+                if (hi > g0[i]) {
+                    bulk_copy_g2s(s + 4 * first[i], src_k + g0[i], (unsigned)((hi - g0[i]) * sizeof(T)), bar);
+                    if (VALS) bulk_copy_g2s(sv + 4 * first[i], src_v + g0[i], (unsigned)((hi - g0[i]) * 4), bar);
+                }
+            }
+        }
+        const long long e[2] = {a1, b0 + bcnt};
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            if (ng[i] > 0 && e[i] > n4) {
+                const long long from = max(n4, g0[i]);
+                if (t < e[i] - from) {
+                    const long long g = from + t;
+                    s[4 * first[i] + (g - g0[i])] = (U)src_k[g];
+                    if (VALS) sv[4 * first[i] + (g - g0[i])] = src_v[g];
+                }
+            }
+        }
+        const bool done = mbar_wait_bounded(bar, 0, BULK_WAIT_TRIES);
+        if (!__syncthreads_and(done)) {
+            if (t == 0 && status) atomicExch(status, (int)SR_ERR_TIMEOUT);
+            mbar_wait_bounded(bar, 0, BULK_WAIT_TRIES);   // copies still in flight must land first
+            return;
+        }
+        if (KT != SR_KEY_U32 && KT != SR_KEY_U64) {       // raw keys -> order images, in place
+            for (int g = t; g < nag + nbg; g += NT) {
+                if (sizeof(U) == 4) {
+                    uint4 q = *reinterpret_cast<uint4 *>(s + 4 * g);
+                    q.x = (uint32_t)K::ord((T)q.x); q.y = (uint32_t)K::ord((T)q.y);
+                    q.z = (uint32_t)K::ord((T)q.z); q.w = (uint32_t)K::ord((T)q.w);
+                    *reinterpret_cast<uint4 *>(s + 4 * g) = q;
+                } else {
+#pragma unroll
+                    for (int e2 = 0; e2 < 4; ++e2) s[4 * g + e2] = K::ord((T)s[4 * g + e2]);
+                }
+            }
+        }
+    } else if (VEC) {
         const long long a0g = a0 & ~3ll, b0g = b0 & ~3ll;
         const int nag = (int)((((a1 + 3) & ~3ll) - a0g) >> 2);
         const int nbg = (int)((((b0 + bcnt + 3) & ~3ll) - b0g) >> 2);
@@ -841,37 +1216,64 @@ __device__ __forceinline__ void merge_tile(const typename Key<KT>::T *__restrict
     write_tile<KT, NT, IPT, VALS, VEC>(k, v, s, sv, dst_k, dst_v, out0, cnt, samp, tile);
 }
 
-// One CTA per output tile of NT*IPT keys of merge pass p.  The tile's A and B
-// ranges come from the split table and are merged by merge_tile.  A run pair
-// (2w keys) spans 2^lgt whole tiles.
-template <int KT, int NT, int IPT, bool VALS, bool VEC>
+// One CTA per output tile of NT*IPT keys of a 2-way merge step.  The tile's
+// pair of runs and its share of each come from the split table.
+template <int KT, int NT, int IPT, bool VALS, int STAGE>
 __global__ void __launch_bounds__(NT, Shape<sizeof(typename Key<KT>::T), VALS>::MERGE_MINB)
 k_merge(typename Key<KT>::T *uk, uint32_t *uv, typename Key<KT>::T *sk, uint32_t *svb, long long n,
-        long long w, int lgt, const long long *__restrict__ splits, const Ctrl *__restrict__ c, int step,
-        int l0, typename Key<KT>::U *__restrict__ samp, long long smt) {
+        const long long *__restrict__ splits, const Ctrl *__restrict__ c, int step,
+        typename Key<KT>::U *__restrict__ samp, long long smt, int *status) {
     griddep_wait();
     typedef Key<KT> K;
     typedef typename K::U U;
-    typedef typename K::T T;
     constexpr int NV = NT * IPT;
     constexpr int SV = NV + 16;                    // staged keys, with room for window slack
-    if (!step_needed(c, l0, 1)) return;            // also skipped unless the input needs sorting
+    if (step >= steps_of(c)) return;               // also when the input needs no sorting
     extern __shared__ __align__(16) unsigned char smem[];
     U *s = reinterpret_cast<U *>(smem);
     uint32_t *sv = reinterpret_cast<uint32_t *>(s + SV);
     const int cur = c->src_buf[step];
-    const long long out0 = (long long)blockIdx.x * NV;
+    const long long b = blockIdx.x;
+    const long long out0 = b * NV;
     const long long out1 = min(out0 + NV, n);
-    const long long pb = (long long)(((unsigned long long)blockIdx.x >> lgt) << lgt) * NV;
-    const long long a_beg = pb, a_end = min(pb + w, n);
-    const long long b_beg = a_end, b_end = min(pb + 2 * w, n);
-    const long long a0 = splits[blockIdx.x];
-    const long long a1 = (out1 == b_end) ? a_end : splits[blockIdx.x + 1];
-    const long long b0 = b_beg + (out0 - pb) - (a0 - a_beg);
+    const long long a0 = splits[4 * b], a_beg = splits[4 * b + 1], a_end = splits[4 * b + 2];
+    const long long b_end = splits[4 * b + 3];
+    const long long a1 = (out1 == b_end) ? a_end : splits[4 * (b + 1)];
+    const long long b0 = a_end + (out0 - a_beg) - (a0 - a_beg);
     // the output's tile samples go with the buffer it lands in
-    merge_tile<KT, NT, IPT, VALS, VEC>(cur ? sk : uk, cur ? uk : sk, cur ? svb : uv, cur ? uv : svb, n, out0,
-                                       (int)(out1 - out0), a0, a1, b0, s, sv, samp ? samp + (1 - cur) * smt : nullptr,
-                                       (long long)blockIdx.x);
+    __shared__ unsigned long long bar;
+    merge_tile<KT, NT, IPT, VALS, STAGE != STAGE_SCALAR>(cur ? sk : uk, cur ? uk : sk, cur ? svb : uv,
+                                                         cur ? uv : svb, n, out0, (int)(out1 - out0), a0, a1, b0, s,
+                                                         sv, samp ? samp + (1 - cur) * smt : nullptr, b,
+                                                         STAGE == STAGE_BULK ? &bar : nullptr, status);
+}
+
+// Neighbour repair, step 2: one CTA per tile boundary merges its window (the
+// suffix of tile t and the prefix of tile t+1 found by k_repair_plan) in place,
+// stably; keys outside the windows stay where the block sort put them.  After
+// it the whole array is sorted: left of a window every key is <= tile t+1's
+// smallest, right of it every key is >= tile t's largest.
+template <int KT, int NT, int IPT, bool VALS>
+__global__ void __launch_bounds__(NT)
+k_repair(typename Key<KT>::T *uk, uint32_t *uv, typename Key<KT>::T *sk, uint32_t *svb, long long n, long long ts,
+         long long tiles, const int *__restrict__ win, const Ctrl *__restrict__ c) {
+    griddep_wait();
+    typedef Key<KT> K;
+    typedef typename K::U U;
+    constexpr int SV = NT * IPT + 16;
+    if (call_mode(c, n) != MODE_SORT || !c->repair || c->repair_fail) return;
+    const long long t = blockIdx.x;
+    if (t + 1 >= tiles) return;
+    const int na = win[2 * t], nb = win[2 * t + 1];
+    if (na == 0 || nb == 0) return;                // the boundary is already in order
+    extern __shared__ __align__(16) unsigned char smem[];
+    U *s = reinterpret_cast<U *>(smem);
+    uint32_t *sv = reinterpret_cast<uint32_t *>(s + SV);
+    const bool scratch = c->src_buf[0] != 0;
+    typename K::T *buf = scratch ? sk : uk;
+    uint32_t *vbuf = scratch ? svb : uv;
+    const long long mid = (t + 1) * ts;
+    merge_tile<KT, NT, IPT, VALS, false>(buf, buf, vbuf, vbuf, n, mid - na, na + nb, mid - na, mid, mid, s, sv);
 }
 
 // ------------------------------------------------------------ 4-way merge steps
@@ -890,7 +1292,7 @@ k_merge(typename Key<KT>::T *uk, uint32_t *uv, typename Key<KT>::T *sk, uint32_t
 
 // A merged pair P = merge(X, Y) of adjacent runs X = [x_beg, x_end) and
 // Y = [x_end, y_end), seen through the 2-way splits of its merge tiles:
-// split1[t0 + j] is where P's tile j (outputs j*nv ..) starts in X.
+// split1[4 (t0 + j)] is where P's tile j (outputs j*nv ..) starts in X.
 struct PairView {
     long long x_beg, x_end, y_end, t0, len;
 };
@@ -910,9 +1312,9 @@ __device__ __forceinline__ PairView pair_view(long long x_beg, long long x_end, 
 __device__ __forceinline__ void pair_tile(const long long *__restrict__ split1, const PairView &P, int nv,
                                           long long j, long long &xs, long long &xe, long long &ys,
                                           long long &ye) {
-    xs = split1[P.t0 + j];
+    xs = split1[4 * (P.t0 + j)];
     const long long o1 = min((j + 1) * (long long)nv, P.len);
-    xe = o1 == P.len ? P.x_end : split1[P.t0 + j + 1];
+    xe = o1 == P.len ? P.x_end : split1[4 * (P.t0 + j + 1)];
     ys = P.x_end + j * (long long)nv - (xs - P.x_beg);
     ye = P.x_end + o1 - (xe - P.x_beg);
 }
@@ -1010,33 +1412,38 @@ __device__ __forceinline__ typename Key<KT>::U pair_last(const typename Key<KT>:
     return v;
 }
 
-// 4-way splits of every output tile boundary of step `step` (runs of w keys,
-// groups of 4w), a group of 2^lg lanes per boundary: split4[4b + i] is where
-// tile b's share of run i (A, B, C, D) starts in the source buffer.
+// 4-way splits of every output tile boundary of step `step`, whose groups
+// are four consecutive runs of `span` natural runs each; a group of 2^lg
+// lanes per boundary.  split4[8b + i] is where tile b's share of run i (A, B,
+// C, D) starts in the source buffer, split4[8b + 4 + i] where run i of the
+// tile's group ends.
 template <int KT>
 __global__ void __launch_bounds__(256)
 k_partition4(const typename Key<KT>::T *__restrict__ uk, const typename Key<KT>::T *__restrict__ sk,
-             long long n, long long w, int nv, long long nbound, const long long *__restrict__ split1,
-             long long *__restrict__ split4, const Ctrl *__restrict__ c, int step, int l0, int lg) {
+             long long n, long long ts, long long tiles, int nv, long long nbound,
+             const long long *__restrict__ split1, long long *__restrict__ split4, const int *__restrict__ rs0,
+             long long span, const Ctrl *__restrict__ c, int step, int lg) {
     griddep_wait();
     const int lane = threadIdx.x & 31;
     const long long b = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> lg;
     if (b >= nbound) return;                       // uniform across the group
-    if (!step_needed(c, l0, 2)) return;
+    if (step >= steps_of(c)) return;
     const bool leader = (lane & ((1 << lg) - 1)) == 0;
-    if (b * (long long)nv >= n) {                  // the end of the array: never read as a tile start
+    const long long out = b * (long long)nv;
+    if (out >= n) {                                // the end of the array: never a tile's start
         if (leader)
-            for (int i = 0; i < 4; ++i) split4[4 * b + i] = n;
+            for (int i = 0; i < 8; ++i) split4[8 * b + i] = n;
         return;
     }
     const typename Key<KT>::T *src = c->src_buf[step] ? sk : uk;
-    const long long out = b * (long long)nv;
-    const long long G0 = (out / (4 * w)) * (4 * w);
+    const int nruns = c->nruns;
+    const long long q = nrun_of(rs0, nruns, tiles, out / ts);
+    const long long g0 = (q / (4 * span)) * (4 * span);
     long long e[5];                                // A = [e0, e1), B = [e1, e2), C = [e2, e3), D = [e3, e4)
 #pragma unroll
-    for (int i = 0; i < 5; ++i) e[i] = min(G0 + i * w, n);
+    for (int i = 0; i < 5; ++i) e[i] = nrun_pos(rs0, nruns, g0 + i * span, ts, n);
     const PairView AB = pair_view(e[0], e[1], e[2], nv), CD = pair_view(e[2], e[3], e[4], nv);
-    const long long d = out - G0;                  // a multiple of nv
+    const long long d = out - e[0];                // a multiple of nv
     long long lo = max(0ll, d - CD.len), hi = min(d, AB.len);
     if (hi > lo) {
         // coarse: at m = j * nv, AB[m] is the first key of AB's tile j and
@@ -1057,10 +1464,12 @@ k_partition4(const typename Key<KT>::T *__restrict__ uk, const typename Key<KT>:
         const long long x = lo;
         const long long a = pair_split<KT>(src, split1, AB, nv, x);
         const long long cc = pair_split<KT>(src, split1, CD, nv, d - x);
-        split4[4 * b + 0] = e[0] + a;
-        split4[4 * b + 1] = e[1] + (x - a);
-        split4[4 * b + 2] = e[2] + cc;
-        split4[4 * b + 3] = e[3] + (d - x - cc);
+        split4[8 * b + 0] = e[0] + a;
+        split4[8 * b + 1] = e[1] + (x - a);
+        split4[8 * b + 2] = e[2] + cc;
+        split4[8 * b + 3] = e[3] + (d - x - cc);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) split4[8 * b + 4 + i] = e[i + 1];
     }
 }
 
@@ -1071,8 +1480,6 @@ __device__ __forceinline__ V pick4(int i, V a, V b, V c, V d) {
     return i == 0 ? a : i == 1 ? b : i == 2 ? c : d;
 }
 
-// Staging modes of a 4-way merge tile's four windows into shared memory.
-enum { STAGE_SCALAR = 0, STAGE_VEC = 1, STAGE_BULK = 2 };
 
 // Staged key capacity of a 4-way merge tile: NV keys plus, per window, up to
 // 3 keys before its first and after its last 4-key group boundary.
@@ -1084,11 +1491,6 @@ template <typename U, int NT, int IPT, bool VALS>
 constexpr size_t merge4_smem() {
     return (size_t)Merge4Cap<NT * IPT>::SV * (sizeof(U) + (VALS ? 4 : 0)) + (size_t)(IPT + 8) * sizeof(U);
 }
-
-// Longest wait for a tile's bulk copies: tries of mbarrier.try_wait (each
-// waits in hardware for a while); a tile that gives up reports
-// SR_ERR_TIMEOUT in `status`.
-enum { BULK_WAIT_TRIES = 1 << 22 };
 
 // One output tile of a 4-way step: outputs [out0, out0 + cnt) of the stable
 // merge of A = src[beg0, beg0 + len0), B, C and D likewise (len0 + .. + len3 =
@@ -1291,19 +1693,18 @@ __device__ __forceinline__ void merge_tile4(const typename Key<KT>::T *__restric
     write_tile<KT, NT, IPT, VALS, STAGE != STAGE_SCALAR>(k, v, s, sv, dst_k, dst_v, out0, cnt, samp, tile);
 }
 
-// One CTA per output tile of NT*IPT keys of 4-way step `step` (runs of w
-// keys): the tile's windows of A, B, C and D come from split4 (the run ends
-// for a group's last tile).
+// One CTA per output tile of NT*IPT keys of a 4-way step: the tile's windows
+// of A, B, C and D come from split4 (the runs' ends for a group's last tile).
 template <int KT, int NT, int IPT, bool VALS, int STAGE>
 __global__ void __launch_bounds__(NT, Shape<sizeof(typename Key<KT>::T), VALS>::MERGE4_MINB)
 k_merge4(typename Key<KT>::T *uk, uint32_t *uv, typename Key<KT>::T *sk, uint32_t *svb, long long n,
-         long long w, const long long *__restrict__ split4, const Ctrl *__restrict__ c, int step, int l0,
+         const long long *__restrict__ split4, const Ctrl *__restrict__ c, int step,
          typename Key<KT>::U *__restrict__ samp, long long smt, int *status) {
     griddep_wait();
     typedef Key<KT> K;
     typedef typename K::U U;
     constexpr int NV = NT * IPT;
-    if (!step_needed(c, l0, 2)) return;
+    if (step >= steps_of(c)) return;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned long long bar;
     U *s = reinterpret_cast<U *>(smem);
@@ -1312,14 +1713,13 @@ k_merge4(typename Key<KT>::T *uk, uint32_t *uv, typename Key<KT>::T *sk, uint32_
     const long long b = blockIdx.x;
     const long long out0 = b * NV;
     const long long out1 = min(out0 + NV, n);
-    const long long G0 = (out0 / (4 * w)) * (4 * w);
-    const bool last = out1 == min(G0 + 4 * w, n);   // the group's last tile ends at its runs' ends
+    const bool last = out1 == split4[8 * b + 7];   // the group's last tile ends at its runs' ends
     long long beg[4];
     int len[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        beg[i] = split4[4 * b + i];
-        const long long end = last ? min(G0 + (i + 1) * w, n) : split4[4 * (b + 1) + i];
+        beg[i] = split4[8 * b + i];
+        const long long end = last ? split4[8 * b + 4 + i] : split4[8 * (b + 1) + i];
         len[i] = (int)(end - beg[i]);
     }
     merge_tile4<KT, NT, IPT, VALS, STAGE>(cur ? sk : uk, cur ? uk : sk, cur ? svb : uv, cur ? uv : svb, n, out0,
@@ -1329,10 +1729,10 @@ k_merge4(typename Key<KT>::T *uk, uint32_t *uv, typename Key<KT>::T *sk, uint32_
 
 template <int KT, bool VALS>
 __global__ void k_copy_back(typename Key<KT>::T *uk, uint32_t *uv, const typename Key<KT>::T *sk,
-                            const uint32_t *svb, long long n, const Ctrl *__restrict__ c, int steps) {
+                            const uint32_t *svb, long long n, const Ctrl *__restrict__ c) {
     griddep_wait();
     if (call_mode(c, n) != MODE_SORT) return;
-    if (c->src_buf[steps] == 0) return;
+    if (c->src_buf[steps_of(c)] == 0) return;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         uk[i] = sk[i];

@@ -265,12 +265,11 @@ extern "C" sr_status sr_get_stats(sr_stats *out) {
     int skipped = 0, merged = 0;
     if (out->input_class == 0) {
         bytes += 2 * n * elem;                                          // block sort
-        for (int p = 0; p < out->passes_planned && p < MAX_PASSES; ++p) {
-            int l0 = p, nl = 1;
-            if (r.fan4) merge_step_levels(r.levels, true, p, &l0, &nl);
-            if (c.unordered[l0] == 0 && (nl == 1 || c.unordered[l0 + 1] == 0)) ++skipped;
-            else { ++merged; bytes += 2 * n * elem; }
-        }
+        const bool repaired = c.repair && !c.repair_fail;
+        merged = out->passes_planned > 0 && !repaired ? c.nsteps : 0;   // steps the natural runs needed
+        skipped = out->passes_planned - merged;
+        bytes += (unsigned long long)merged * 2 * n * elem;
+        if (repaired) bytes += 2 * c.repair_keys * elem;                  // the boundary windows, in place
         if (((r.cur0 + merged) & 1) != 0) bytes += 2 * n * elem;         // copy back
     } else if (out->input_class == 2) {
         bytes += 2 * n * elem;                                          // one reversal

@@ -43,8 +43,6 @@ struct CallRecord {
     int key_bytes = 4;
     int val_bytes = 0;
     int cur0 = 0;
-    int levels = 0;                 // binary merge levels after the block sort
-    bool fan4 = false;              // merged four runs per step (passes_planned counts steps)
     int aux_kind = 0;               // 3: last_aux holds a segmented call's block, 4: a learned call's
 };
 

@@ -364,8 +364,6 @@ static sr_status sort_impl(void *d_keys, uint32_t *d_vals, size_t n, cudaStream_
     SR_TRY(device_state(&ds));
     plan.status = ds->status;
     rec.cur0 = plan.steps & 1;
-    rec.levels = plan.passes;
-    rec.fan4 = plan.fan4;
     rec.host.passes_planned = plan.steps;
     if (graphs) {                                // caller's buffers: a repeated call replays its graph
         bool done = false;
@@ -423,7 +421,8 @@ static sr_status detect_impl(const void *d_keys, size_t n, sr_run_info *out, cud
     do {
         if (cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s) != cudaSuccess) { st = launch_status(); break; }
         SR_LAUNCH(SR_KERNEL_DETECT, (k_detect<KT, SNT, IPT>), (unsigned)tiles, SNT, 0, s,
-                  (const T *)d_keys, N, ctrl, (const int *)nullptr, (typename K::U *)nullptr, 1);
+                  (const T *)d_keys, N, ctrl, (const int *)nullptr, (typename K::U *)nullptr, 1,
+                  (typename K::U *)nullptr, (typename K::U *)nullptr);
         if (cudaMemcpyAsync(&h, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) {
             st = launch_status();

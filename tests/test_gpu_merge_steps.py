@@ -150,11 +150,13 @@ print("child ok", sr.stats()["passes_planned"])
 
 @pytest.mark.parametrize("env", [{"SORTRACE_MERGE_FANIN": "4"},
                                  {"SORTRACE_MERGE_FANIN": "4", "SORTRACE_MERGE4_STAGE": "vec"},
-                                 {"SORTRACE_MERGE_FANIN": "2"}])
+                                 {"SORTRACE_MERGE_FANIN": "2"},
+                                 {"SORTRACE_MERGE_FANIN": "2", "SORTRACE_MERGE2_STAGE": "bulk"}])
 def test_other_staging_and_fanin(env):
     """Every key shape forced to 4-way steps (bulk-copy staging, then 16-byte
-    register staging), and to 2-way steps, in child processes: the same sizes
-    and classes against the oracle."""
+    register staging), and to 2-way steps (16-byte register staging, then
+    bulk copies), in child processes: the same sizes and classes against the
+    oracle."""
     e = dict(os.environ)
     e.update(env)
     r = subprocess.run([sys.executable, "-c", _CHILD.format(root=ROOT)], env=e, capture_output=True, text=True,
@@ -163,4 +165,36 @@ def test_other_staging_and_fanin(env):
     assert "child ok" in r.stdout
     planned = int(r.stdout.split("child ok")[1].split()[0])
     levels = 11                                  # 2^24 int32 keys: 1311 tiles of 12,800
-    assert planned == (levels if env.get("SORTRACE_MERGE_FANIN") == "2" else (levels + 1) // 2)
+    assert planned == ((levels + 1) // 2 if env.get("SORTRACE_MERGE_FANIN") == "4" else levels)
+
+
+def test_descending_tile_chains(gpu_lib):
+    """Inputs whose block-sorted tiles come in descending order (k-even and
+    k-sharp teeth, non-increasing lists with long blocks of equal keys that
+    straddle tile boundaries): the block sort writes such chains reversed, the
+    merge steps finish; keys and stable pairs equal the oracle's at sizes
+    where the block sort writes to the other buffer and where it works in
+    place."""
+    import torch
+    ts = 12800
+    for n in (64 * ts, 64 * ts + 77, 32 * ts + 5, 33 * ts):
+        rng = np.random.default_rng(n)
+        cases = [si.k_even_teeth(n - n % 4, 4), si.k_sharp_teeth(n - n % 8, 8),
+                 np.repeat(np.arange(n // 5000 + 1, dtype=np.int32)[::-1], 5000)[:n],
+                 np.sort(rng.integers(0, 50, n).astype(np.int32))[::-1].copy()]
+        for a in cases:
+            x = torch.from_numpy(a.copy()).cuda()
+            gpu_lib.sort_keys(x, key_type=0)
+            assert x.cpu().numpy().tobytes() == oracle.sort_keys(a).tobytes(), n
+            v = np.arange(a.size, dtype=np.uint32)
+            xk = torch.from_numpy(a.copy()).cuda()
+            xv = torch.from_numpy(v.view(np.int32).copy()).cuda()
+            gpu_lib.sort_pairs(xk, xv, key_type=0)
+            ok, ov = oracle.sort_pairs(a, v)
+            assert xk.cpu().numpy().tobytes() == ok.tobytes(), n
+            assert xv.cpu().numpy().view(np.uint32).tobytes() == ov.tobytes(), n
+            u = a.astype(np.int64) * 3 - 7
+            x8 = torch.from_numpy(u.copy()).cuda()
+            gpu_lib.sort_keys(x8, key_type=4)
+            assert x8.cpu().numpy().tobytes() == oracle.sort_keys(u).tobytes(), n
+    assert gpu_lib.stream_status() == 0

@@ -285,14 +285,15 @@ def test_oom_injection(gpu_lib, monkeypatch):
 
 @pytest.mark.parametrize("dtype", [np.int32, np.uint32, np.float32])
 def test_few_distinct_keys(gpu_lib, dtype):
-    """At most 64 distinct keys (4-byte keys): a 4,096-key sample spread over
-    the array builds the set of distinct keys; when it holds every key the call
-    counts them and writes runs (input_class 3, 12 bytes per key moved).  65 or
-    more distinct keys, or a key the sample missed, take the ordinary sort.
-    Output bit-exact against the oracle either way, including float32 -0.0 /
-    +0.0 as distinct keys."""
+    """At most 4,096 distinct keys (4-byte keys): a 65,536-key sample spread
+    over the array builds the set of distinct keys; when it holds every key the
+    call counts them and writes runs (input_class 3, 12 bytes per key moved).
+    4,097 or more distinct keys, or a key the sample missed, take the ordinary
+    sort.  Output bit-exact against the oracle either way, including float32
+    -0.0 / +0.0 as distinct keys."""
     rng = np.random.default_rng(60)
-    for d, n in ((2, 1000), (16, 1 << 20), (64, (1 << 20) + 3), (64, 12345), (65, 300_001), (1000, 300_001)):
+    for d, n in ((2, 1000), (16, 1 << 20), (64, (1 << 20) + 3), (65, 300_001), (1000, 300_001),
+                 (4096, (1 << 22) + 5), (4097, 1 << 22), (20000, 300_001)):
         vals = _random(rng, d, dtype)
         if dtype == np.float32 and d >= 2:
             vals[:2] = np.array([0x00000000, 0x80000000], np.uint32).view(np.float32)
@@ -301,10 +302,10 @@ def test_few_distinct_keys(gpu_lib, dtype):
         got = _gpu_sort(gpu_lib, a)
         assert got.tobytes() == oracle.sort_keys(a).tobytes(), (dtype, d, n)
         st = gpu_lib.stats()
-        if vals.size <= 64 and n >= 1000 * vals.size:
-            # every distinct key is in the sample (4,096 draws)
+        if np.unique(a.view(np.uint32)).size <= 4096 and n >= 256 * vals.size:
+            # every distinct key is in the sample (65,536 draws)
             assert st["input_class"] == 3 and st["bytes_moved"] == 12 * n, (d, n, st["input_class"])
-        elif vals.size > 64:
+        elif vals.size > 4096:
             assert st["input_class"] == 0
     # the 65th distinct key appears once, at the end: the sample misses it, the
     # counting pass finds it and the ordinary sort runs
@@ -421,8 +422,10 @@ def test_few_displaced_keys_fallbacks(gpu_lib):
     pairs (payload order); an unaligned key pointer still takes it."""
     import torch
     rng = np.random.default_rng(63)
-    # few distinct values (more than 64): equal keys pile into a few buckets
-    a = _exchanged(rng, np.sort(rng.integers(-50, 50, 400_000).astype(np.int32)), 0.005)
+    # heavily repeated values (and 20,000 single ones, too many distinct keys
+    # for the few-distinct path): equal keys pile into a few buckets
+    base = np.concatenate([rng.integers(-50, 50, 380_000), rng.integers(-2**31, 2**31 - 1, 20_000)])
+    a = _exchanged(rng, np.sort(base.astype(np.int32)), 0.005)
     assert _gpu_sort(gpu_lib, a).tobytes() == oracle.sort_keys(a).tobytes()
     assert gpu_lib.stats()["input_class"] == 0
     # fewer descents than tiles

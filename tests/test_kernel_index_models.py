@@ -184,9 +184,9 @@ class _Checked:
 def _pair_tile(split1, P, nv, j):
     x_beg, x_end, y_end, t0, ln = P
     assert 0 <= j * nv < ln
-    xs = split1[t0 + j]
+    xs = split1[t0 + j][0]
     o1 = min((j + 1) * nv, ln)
-    xe = x_end if o1 == ln else split1[t0 + j + 1]
+    xe = x_end if o1 == ln else split1[t0 + j + 1][0]
     ys = x_end + j * nv - (xs - x_beg)
     ye = x_end + o1 - (xe - x_beg)
     assert x_beg <= xs <= xe <= x_end and x_end <= ys <= ye <= y_end
@@ -249,17 +249,72 @@ def _pair_last(src, split1, P, nv, j):
     return v
 
 
-def _partition4(src, n, w, nv, split1, b, G):
-    """k_partition4 for boundary b: where tile b's share of A, B, C, D starts."""
-    if b * nv >= n:
-        return [n] * 4
+def _nrun_pos(rs0, nruns, q, ts, n):
+    return n if q >= nruns else min(rs0[q] * ts, n)
+
+
+def _nrun_of(rs0, nruns, tiles, t):
+    if nruns == tiles:
+        return t
+    lo, hi = 0, nruns - 1
+    while lo < hi:
+        mid = (lo + hi + 1) >> 1
+        if rs0[mid] <= t:
+            lo = mid
+        else:
+            hi = mid - 1
+    assert rs0[lo] <= t < rs0[lo + 1]
+    return lo
+
+
+def _runs(lo_, hi_, tiles, fan):
+    """k_runs: natural runs of whole tiles and the steps they need."""
+    rs0 = [t for t in range(tiles) if t == 0 or hi_[t - 1] > lo_[t]]
+    nruns = len(rs0)
+    rs0.append(tiles)
+    steps, m = 0, nruns
+    while m > 1:
+        m = (m + fan - 1) // fan
+        steps += 1
+    return rs0, nruns, steps
+
+
+def _partition2(src, n, ts, tiles, nv, rs0, nruns, span, b):
+    """k_partition for boundary b: (split, a_beg, a_end, b_end)."""
     out = b * nv
-    G0 = (out // (4 * w)) * (4 * w)
-    e = [min(G0 + i * w, n) for i in range(5)]
+    if out >= n:
+        return (n, n, n, n)
+    q = _nrun_of(rs0, nruns, tiles, out // ts)
+    p0 = (q // (2 * span)) * (2 * span)
+    a_beg = _nrun_pos(rs0, nruns, p0, ts, n)
+    a_end = _nrun_pos(rs0, nruns, p0 + span, ts, n)
+    b_end = _nrun_pos(rs0, nruns, p0 + 2 * span, ts, n)
+    assert a_beg <= out < b_end and a_beg % nv == 0 and a_end % ts == 0 or a_end == n
+    A = _Checked(src, "A", a_beg, a_end)
+    B = _Checked(src, "B", a_end, b_end)
+    d = out - a_beg
+    lo, hi = max(0, d - (b_end - a_end)), min(d, a_end - a_beg)
+    while lo < hi:                                 # the fine search (samples only narrow it)
+        mid = (lo + hi) >> 1
+        if not (B[a_end + d - 1 - mid] < A[a_beg + mid]):
+            lo = mid + 1
+        else:
+            hi = mid
+    return (a_beg + lo, a_beg, a_end, b_end)
+
+
+def _partition4(src, n, ts, tiles, nv, rs0, nruns, span, split1, b, G):
+    """k_partition4 for boundary b: the four window starts and run ends."""
+    out = b * nv
+    if out >= n:
+        return [n] * 8
+    q = _nrun_of(rs0, nruns, tiles, out // ts)
+    g0 = (q // (4 * span)) * (4 * span)
+    e = [_nrun_pos(rs0, nruns, g0 + i * span, ts, n) for i in range(5)]
     AB = (e[0], e[1], e[2], e[0] // nv, e[2] - e[0])
     CD = (e[2], e[3], e[4], e[2] // nv, e[4] - e[2])
-    d = out - G0
-    assert d % nv == 0
+    d = out - e[0]
+    assert d % nv == 0 and 0 <= d < e[4] - e[0]
     lo, hi = max(0, d - CD[4]), min(d, AB[4])
     if hi > lo:
         jlo, jhi, dj = (lo + nv - 1) // nv, (hi - 1) // nv, d // nv
@@ -275,12 +330,13 @@ def _partition4(src, n, w, nv, split1, b, G):
                 lo = max(lo, (jt - 1) * nv + 1)
             if jt <= jhi:
                 hi = min(hi, jt * nv)
+        # probe_ab_cd: both keys' searches (each as _pair_key), then the test
         lo, _ = group_search(lo, hi, G, lambda m: not (
             _pair_key(src, split1, CD, nv, d - 1 - m) < _pair_key(src, split1, AB, nv, m)))
     x = lo
     a = _pair_split(src, split1, AB, nv, x)
     c = _pair_split(src, split1, CD, nv, d - x)
-    return [e[0] + a, e[1] + (x - a), e[2] + c, e[3] + (d - x - c)]
+    return [e[0] + a, e[1] + (x - a), e[2] + c, e[3] + (d - x - c)] + e[1:]
 
 
 def _serial(s, a, a_end, b, b_end, ipt, sw=None, c=None):
@@ -401,68 +457,426 @@ class _K:
         return (self.v, self.run, self.pos)
 
 
-@pytest.mark.parametrize("seed", range(6))
-def test_four_way_step_model(seed):
-    """Block-sorted tiles merged by the step schedule of sr_plain.cuh (a 2-way
-    step first when the level count is odd, then 4-way steps) with the split
-    tables and merge tiles of the 4-way kernels modelled: every read inside
-    its run window or the shared buffer, every output tile equal to the stable
-    merge of its group (ties: A, B, C, D, then position)."""
+def _runs_input(rng, n, ts):
+    """Keys with presorted stretches of every kind: sorted runs of random
+    lengths (not aligned to tiles), reversed runs, random stretches, few
+    distinct values."""
+    out = []
+    while len(out) < n:
+        kind = rng.choice(["asc", "desc", "rand", "few"])
+        ln = rng.randint(1, 6 * ts)
+        if kind == "asc":
+            base = rng.randrange(10 ** 6)
+            out.extend(sorted(base + rng.randrange(5000) for _ in range(ln)))
+        elif kind == "desc":
+            out.extend(sorted((rng.randrange(10 ** 6) for _ in range(ln)), reverse=True))
+        elif kind == "rand":
+            out.extend(rng.randrange(10 ** 6) for _ in range(ln))
+        else:
+            out.extend(rng.randrange(3) for _ in range(ln))
+    return out[:n]
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_run_steps_model(seed):
+    """Block-sorted tiles merged by the run planner's steps (sr_plain.cuh):
+    natural runs of whole tiles (k_runs), then steps of fan-in 2 (k_partition
+    + k_merge) or 4 (k_partition, k_partition4 + k_merge4) over groups of
+    consecutive runs.  Every read inside its run window or the shared buffer,
+    every output tile equal to the stable merge of its group (ties: runs in
+    order, then position), the step count ceil(log_f(runs)), and the result
+    sorted and stable."""
     rng = random.Random(100 + seed)
     NT, IPT = 8, 3
     nv = NT * IPT
     ts = 2 * nv
-    for trial in range(12):
+    for trial in range(10):
+        fan = 2 if (seed + trial) % 2 else 4
         n = rng.choice([rng.randint(1, 10 * ts), rng.randint(10 * ts, 70 * ts)])
-        alpha = rng.choice([3, 50, 10 ** 6])
-        vals = [rng.randrange(alpha) for _ in range(n)]
-        # keys compare by value; each remembers its original position
+        if trial % 3 == 0:
+            vals = [rng.randrange(rng.choice([3, 10 ** 6])) for _ in range(n)]
+        elif trial % 3 == 1:
+            vals = _runs_input(rng, n, ts)
+        else:                                      # teeth: a few long sorted runs (not tile-aligned)
+            k = rng.randint(1, 9)
+            vals = [i % (n // k + 1) for i in range(n)]
+        
         tiles = (n + ts - 1) // ts
         keys = []
         for t in range(tiles):
             idx = sorted(range(t * ts, min(n, (t + 1) * ts)), key=lambda i: (vals[i], i))
             keys.extend(_K(vals[i], 0, i) for i in idx)
+        lo_ = [keys[t * ts].v for t in range(tiles)]
+        hi_ = [keys[min(n, (t + 1) * ts) - 1].v for t in range(tiles)]
+        rs0, nruns, nsteps = _runs(lo_, hi_, tiles, fan)
         levels = 0
         while (1 << levels) < tiles:
             levels += 1
-        steps = (levels + 1) // 2
-        for st in range(steps):
-            if levels & 1 and st == 0:
-                l0, nl = 0, 1
-            else:
-                l0, nl = (levels & 1) + 2 * (st - (levels & 1)), 2
-            w = ts << l0
-            if nl == 1:
-                new = []
-                for p0 in range(0, n, 2 * w):
-                    new.extend(sorted(keys[p0:min(n, p0 + 2 * w)], key=lambda k: (k.v, k.pos)))
-                keys = new
-                continue
-            mt = (n + nv - 1) // nv
-            # split1: the 2-way split (k_partition) of every tile boundary
-            split1 = []
-            for b in range(mt + 1):
-                out = min(b * nv, n)
-                pb = (out // (2 * w)) * (2 * w)
-                A, B = keys[pb:min(pb + w, n)], keys[min(pb + w, n):min(pb + 2 * w, n)]
-                split1.append(pb + _stable_split(A, B, out - pb))
-            G = rng.choice([1, 2, 4, 8])
-            split4 = [_partition4(keys, n, w, nv, split1, b, G) for b in range(mt + 1)]
-            # tag every key with its run in the group (A..D) for the tie order
-            tagged = [_K(k.v, (g % (4 * w)) // w, k.pos) for g, k in enumerate(keys)]
+        max_steps = levels if fan == 2 else (levels + 1) // 2
+        assert nsteps <= max_steps
+        mt = (n + nv - 1) // nv
+        span = 1
+        for step in range(nsteps):
+            split1 = [_partition2(keys, n, ts, tiles, nv, rs0, nruns, span, b) for b in range(mt + 1)]
             new = []
-            for b in range(mt):
-                out0, out1 = b * nv, min(b * nv + nv, n)
-                G0 = (out0 // (4 * w)) * (4 * w)
-                last = out1 == min(G0 + 4 * w, n)
-                beg = split4[b]
-                end = [min(G0 + (i + 1) * w, n) for i in range(4)] if last else split4[b + 1]
-                ln = [end[i] - beg[i] for i in range(4)]
-                assert sum(ln) == out1 - out0 and min(ln) >= 0
-                got = _merge_tile4(tagged, n, out0, out1 - out0, beg, ln, NT, IPT, bulk=(b + trial) % 2 == 0)
-                grp = sorted(k.full() for k in tagged[G0:min(G0 + 4 * w, n)])
-                assert [k.full() for k in got] == grp[out0 - G0:out1 - G0], (n, w, b)
-                new.extend(got)
+            if fan == 2:
+                for b in range(mt):
+                    out0, out1 = b * nv, min(b * nv + nv, n)
+                    a0, a_beg, a_end, b_end = split1[b]
+                    a1 = a_end if out1 == b_end else split1[b + 1][0]
+                    b0 = a_end + (out0 - a_beg) - (a0 - a_beg)
+                    cnt = out1 - out0
+                    assert a_beg <= a0 <= a1 <= a_end and a_end <= b0 <= b0 + cnt - (a1 - a0) <= b_end
+                    A = [_K(k.v, 0, k.pos) for k in keys[a0:a1]]
+                    B = [_K(k.v, 1, k.pos) for k in keys[b0:b0 + cnt - (a1 - a0)]]
+                    got = sorted(A + B, key=lambda k: (k.v, k.run, k.pos))
+                    grp = sorted(([_K(k.v, 0, k.pos) for k in keys[a_beg:a_end]] +
+                                  [_K(k.v, 1, k.pos) for k in keys[a_end:b_end]]),
+                                 key=lambda k: (k.v, k.run, k.pos))
+                    assert [k.full() for k in got] == [k.full() for k in grp[out0 - a_beg:out1 - a_beg]]
+                    new.extend(_K(k.v, 0, k.pos) for k in got)
+            else:
+                G = rng.choice([1, 2, 4, 8])
+                split4 = [_partition4(keys, n, ts, tiles, nv, rs0, nruns, span, split1, b, G) for b in range(mt + 1)]
+                for b in range(mt):
+                    out0, out1 = b * nv, min(b * nv + nv, n)
+                    beg, ends = split4[b][:4], split4[b][4:]
+                    last = out1 == ends[3]
+                    end = ends if last else split4[b + 1][:4]
+                    ln = [end[i] - beg[i] for i in range(4)]
+                    assert sum(ln) == out1 - out0 and min(ln) >= 0
+                    # each key of the group tagged with its run, for the tie order
+                    q = _nrun_of(rs0, nruns, tiles, out0 // ts)
+                    g0 = (q // (4 * span)) * (4 * span)
+                    e5 = [_nrun_pos(rs0, nruns, g0 + i * span, ts, n) for i in range(5)]
+                    assert e5[1:] == ends
+                    tg = [None] * n
+                    for r in range(4):
+                        for g in range(e5[r], e5[r + 1]):
+                            tg[g] = _K(keys[g].v, r, keys[g].pos)
+                    got = _merge_tile4(tg, n, out0, out1 - out0, beg, ln, NT, IPT, bulk=(b + trial) % 2 == 0)
+                    grp = sorted(k.full() for k in tg[e5[0]:e5[4]])
+                    assert [k.full() for k in got] == grp[out0 - e5[0]:out1 - e5[0]], (n, b)
+                    new.extend(_K(k.v, 0, k.pos) for k in got)
             keys = new
-            # within a run, positions ascend on ties (every earlier step was stable)
+            span *= fan
         assert [(k.v, k.pos) for k in keys] == sorted((v, i) for i, v in enumerate(vals))
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_neighbour_repair_model(seed):
+    """k_repair_plan + k_repair (sr_kernels.cuh): when every block-sorted
+    tile's keys are <= those of the tile two places on, merging in place the
+    window at each tile boundary (tile t's keys above tile t+1's smallest,
+    tile t+1's keys below tile t's largest) sorts the array, stably; the
+    windows never overlap and stay inside their two tiles.  Inputs: k-distance
+    lists (Section 2) with k up to half a tile, few distinct values, and
+    windows too large (the repair then gives way to the merge steps)."""
+    rng = random.Random(300 + seed)
+    ts, cap = 48, 24
+    tried = applied = 0
+    for trial in range(60):
+        n = rng.randint(3 * ts, 40 * ts)
+        k = rng.choice([1, 3, 8, ts // 2, ts])
+        vals = list(range(n))
+        for s0 in range(0, n, k + 1):                 # k-distance: sections of k+1 shuffled
+            sec = vals[s0:s0 + k + 1]
+            rng.shuffle(sec)
+            vals[s0:s0 + k + 1] = sec
+        if trial % 5 == 4:
+            vals = [v // 7 for v in vals]             # repeated values
+        tiles = (n + ts - 1) // ts
+        keys = []
+        for t in range(tiles):
+            idx = sorted(range(t * ts, min(n, (t + 1) * ts)), key=lambda i: (vals[i], i))
+            keys.extend(_K(vals[i], 0, i) for i in idx)
+        lo_ = [keys[t * ts].v for t in range(tiles)]
+        hi_ = [keys[min(n, (t + 1) * ts) - 1].v for t in range(tiles)]
+        far = any(hi_[q] > lo_[q + 2] for q in range(tiles - 2))
+        _, nruns, steps = _runs(lo_, hi_, tiles, 2)
+        if far or steps == 0:
+            continue
+        tried += 1
+        src = _Checked(keys, "keys")
+        win, fail, covered = [], False, set()
+        for t in range(tiles - 1):                    # k_repair_plan
+            x0, x1, y0, y1 = t * ts, t * ts + ts, t * ts + ts, min(t * ts + 2 * ts, n)
+            a, b = x0, x1
+            while a < b:
+                m = (a + b) >> 1
+                if src[m].v <= lo_[t + 1]:
+                    a = m + 1
+                else:
+                    b = m
+            e, f = y0, y1
+            while e < f:
+                m = (e + f) >> 1
+                if src[m].v < hi_[t]:
+                    e = m + 1
+                else:
+                    f = m
+            na, nb = x1 - a, e - y0
+            if na + nb > cap:
+                fail = True
+            win.append((na, nb))
+        if fail:
+            continue
+        applied += 1
+        out = list(keys)
+        for t, (na, nb) in enumerate(win):            # k_repair: merge_tile in place
+            if na == 0 or nb == 0:
+                continue
+            mid = (t + 1) * ts
+            rng_ = set(range(mid - na, mid + nb))
+            assert not (rng_ & covered)                # windows never overlap
+            covered |= rng_
+            A = [_K(k.v, 0, k.pos) for k in keys[mid - na:mid]]
+            B = [_K(k.v, 1, k.pos) for k in keys[mid:mid + nb]]
+            merged = sorted(A + B, key=lambda k: (k.v, k.run, k.pos))
+            out[mid - na:mid + nb] = [_K(k.v, 0, k.pos) for k in merged]
+        assert [(k.v, k.pos) for k in out] == sorted((v, i) for i, v in enumerate(vals)), (n, k)
+    assert tried >= 20 and applied >= 10, (tried, applied)
+
+
+def _tile_order(tmin, tmax, n, ts, tiles, strict, NT):
+    """k_tile_order with NT threads: chunked running max forward (each tile's
+    chain start), running min backward (its chain end); dest = first + last - q."""
+    full = n // ts
+
+    def desc(q):
+        if q <= 0 or q >= full:
+            return False
+        down = tmax[q] < tmin[q - 1] if strict else tmax[q] <= tmin[q - 1]
+        return down and not (tmax[q - 1] <= tmin[q])
+
+    dest = [0] * tiles
+    carry = 0
+    for t0 in range(0, tiles, NT):
+        run = carry
+        for t in range(NT):
+            q = t0 + t
+            start = q if (q < tiles and not desc(q)) else -1
+            run = max(run, start)
+            if q < tiles:
+                dest[q] = run
+        carry = run
+    carry, any_ = tiles - 1, False
+    t1 = tiles
+    while t1 > 0:
+        run = carry
+        for t in reversed(range(NT)):
+            q = t1 - NT + t
+            end = q if (0 <= q < tiles and not desc(q + 1)) else 10 ** 9
+            run = min(run, end)
+            if 0 <= q < tiles:
+                first = dest[q]
+
+                def asc(x, y):
+                    return 1 if (x >= 0 and y < tiles and tmax[x] <= tmin[y]) else 0
+                gain = (run - first) + asc(first - 1, run) + asc(first, run + 1) - asc(first - 1, first) - \
+                    asc(run, run + 1)
+                flip = run > first and gain > 0
+                any_ |= flip
+                dest[q] = first + run - q if flip else q
+        carry = run
+        t1 -= NT
+    return dest, any_, desc
+
+
+@pytest.mark.parametrize("strict", [False, True])
+def test_tile_order_model(strict):
+    """Chains of tiles in descending order reversed by the block sort: dest is
+    a permutation that reverses every maximal chain of full tiles whose
+    boundaries descend (strictly, for stable pair sorts) and fixes every other
+    tile; after it the chain's tiles ascend.  Against a direct search of the
+    chains, with chunks of a few threads so the scans' carries are used."""
+    rng = random.Random(7 + strict)
+    for trial in range(300):
+        ts = rng.choice([1, 3, 8])
+        tiles = rng.randint(1, 40)
+        n = tiles * ts - (rng.randint(0, ts - 1) if rng.random() < 0.5 else 0)
+        tiles = (n + ts - 1) // ts
+        if tiles == 0:
+            continue
+        # tile extremes from a random sequence of ascending / descending stretches
+        lo_, hi_ = [], []
+        v = 1000
+        for t in range(tiles):
+            step = rng.choice([-40, -40, 40, 0, 5])
+            v += step
+            w = rng.choice([0, 3, 10])
+            lo_.append(v)
+            hi_.append(v + w)
+        dest, any_, desc = _tile_order(lo_, hi_, n, ts, tiles, strict, rng.choice([1, 2, 4, 8]))
+        assert sorted(dest) == list(range(tiles))
+        # direct: maximal chains [a, b] of descending boundaries, turned when
+        # that lowers the number of natural runs (counted on the result)
+        def runs_of(order):
+            return 1 + sum(1 for i in range(1, len(order)) if hi_[order[i - 1]] > lo_[order[i]])
+        want = list(range(tiles))
+        q = 0
+        while q < tiles:
+            b = q
+            while b + 1 < tiles and desc(b + 1):
+                b += 1
+            trial_order = list(range(tiles))
+            trial_order[q:b + 1] = reversed(trial_order[q:b + 1])
+            if b > q and runs_of(trial_order) < runs_of(list(range(tiles))):
+                for r in range(q, b + 1):
+                    want[r] = q + b - r
+            q = b + 1
+        assert dest == want
+        assert any_ == (want != list(range(tiles)))
+        order = [None] * tiles
+        for q in range(tiles):
+            order[dest[q]] = q
+        assert runs_of(order) <= runs_of(list(range(tiles)))
+        for q in range(tiles):
+            if dest[q] != q:
+                assert (q + 1) * ts <= n                # only full tiles move
+        # moved chains ascend (each tile's keys <= the next's; strictly for strict)
+        pos = [None] * tiles
+        for q in range(tiles):
+            pos[dest[q]] = q
+        for p in range(1, tiles):
+            a, b = pos[p - 1], pos[p]
+            if dest[a] != a and dest[b] != b and abs(a - b) == 1:
+                assert hi_[a] <= lo_[b] and (not strict or hi_[a] < lo_[b])
+
+
+def test_few_keys_model():
+    """k_few_sample's bitonic network over the sampled set (padded to a power
+    of two with the largest image) sorts any k <= 4,096 images; k_few_write's
+    exclusive scan (16 counts per thread, 8 partial sums per lane of one warp)
+    and its search for each output's key write every key count times, in
+    order."""
+    rng = random.Random(11)
+    for k in (1, 2, 3, 16, 17, 100, 1000, 4095, 4096):
+        v = [rng.randrange(1 << 32) for _ in range(k)]
+        P = 1
+        while P < k:
+            P <<= 1
+        s = v + [0xFFFFFFFF] * (P - k)
+        size = 2
+        while size <= P:
+            stride = size >> 1
+            while stride > 0:
+                for q in range(P // 2):
+                    lo = 2 * stride * (q // stride) + (q % stride)
+                    hi = lo + stride
+                    assert hi < P
+                    up = (lo & size) == 0
+                    if (s[lo] > s[hi]) == up:
+                        s[lo], s[hi] = s[hi], s[lo]
+                stride >>= 1
+            size <<= 1
+        assert s[:k] == sorted(v)
+        # scan of the counts as k_few_write does it
+        counts = [rng.randint(0, 5) for _ in range(k)]
+        PER = 4096 // 256
+        part = [sum(counts[q] for q in range(t * PER, t * PER + PER) if q < k) for t in range(256)]
+        excl, acc = [0] * 256, 0
+        for lane in range(32):                       # 8 partial sums per lane, then the warp scan
+            for w in range(8):
+                excl[lane * 8 + w] = acc
+                acc += part[lane * 8 + w]
+        start = []
+        for t in range(256):
+            run = excl[t]
+            for e in range(PER):
+                q = t * PER + e
+                if q < k:
+                    start.append(run)
+                    run += counts[q]
+        assert start == [sum(counts[:q]) for q in range(k)]
+        n = sum(counts)
+        out = []
+        for i in range(n):                           # which(i): the last q < k with start[q] <= i
+            lo, hi = 0, k - 1
+            while lo < hi:
+                mid = (lo + hi + 1) >> 1
+                if start[mid] <= i:
+                    lo = mid
+                else:
+                    hi = mid - 1
+            out.append(s[lo])
+        assert out == [s[q] for q in range(k) for _ in range(counts[q])]
+
+
+def test_few_keys_chunked_write_and_lookup_model():
+    """k_few_write's warp chunks (lane l writes 16-byte groups l, l+32, ... of
+    each 256-group chunk, one search per lane per chunk, then a key index that
+    only moves forward) write every position exactly once with the right key,
+    whatever the grid; k_few_count's hash table maps every image of the set to
+    its rank and reports a key outside the set."""
+    rng = random.Random(12)
+    for trial in range(30):
+        k = rng.choice([1, 2, 5, 64, 300, 4096])
+        counts = [rng.choice([0, 1, 3, 9, 1000]) for _ in range(k)]
+        counts[rng.randrange(k)] += 1
+        n = sum(counts)
+        start, acc = [], 0
+        for c in counts:
+            start.append(acc)
+            acc += c
+        want = [q for q in range(k) for _ in range(counts[q])]
+
+        def which(i):
+            lo, hi = 0, k - 1
+            while lo < hi:
+                mid = (lo + hi + 1) >> 1
+                if start[mid] <= i:
+                    lo = mid
+                else:
+                    hi = mid - 1
+            return lo
+        nv = n // 4
+        out = [None] * n
+        blocks, warps_per = rng.choice([1, 3, 7]), 8
+        warps = blocks * warps_per
+        CH = 32 * 8
+        for wid in range(warps):
+            c0 = wid * CH
+            while c0 < nv:
+                end = min(c0 + CH, nv)
+                for lane in range(32):
+                    v = c0 + lane
+                    if v >= end:
+                        continue
+                    j = which(4 * v)
+                    while v < end:
+                        i = 4 * v
+                        for m in range(4):
+                            while j + 1 < k and start[j + 1] <= i + m:
+                                j += 1
+                            assert out[i + m] is None
+                            out[i + m] = j
+                        v += 32
+                c0 += warps * CH
+        for i in range(4 * nv, n):                   # the scalar tail
+            out[i] = which(i)
+        assert out == want
+    # the count pass's table: image -> rank + 1, linear probing, at most half full
+    imgs = sorted(rng.sample(range(1 << 32), 4096))
+    SL, tab = 1 << 13, [0] * (1 << 13)
+    for q, u in enumerate(imgs):
+        h = (u * 2654435761 % (1 << 32)) >> (32 - 13)
+        while tab[h]:
+            h = (h + 1) & (SL - 1)
+        tab[h] = (u << 32) | (q + 1)
+
+    def look(u):
+        h = (u * 2654435761 % (1 << 32)) >> (32 - 13)
+        for _ in range(SL):
+            e = tab[h]
+            if e == 0:
+                return None
+            if e >> 32 == u:
+                return (e & 0xFFFFFFFF) - 1
+            h = (h + 1) & (SL - 1)
+        return None
+    assert all(look(u) == q for q, u in enumerate(imgs))
+    s = set(imgs)
+    for _ in range(2000):
+        u = rng.randrange(1 << 32)
+        assert look(u) == (imgs.index(u) if u in s else None)
