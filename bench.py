@@ -505,12 +505,16 @@ def _sweep(sr, torch, dev, stream, peak, reps=3):
         sr.sort_keys(x)
         k = sr.profile_end()
         kern = {}
-        for name, per_key in (("merge", 8), ("block_sort", 8), ("detect", 4)):
+        # merge and block sort: bytes of one launch over its average time; the
+        # scan: the keys read once over the time of the whole kind (the scan
+        # and the few-distinct-keys sampling kernels it launches with)
+        for name, per_key, per_call in (("merge", 8, False), ("block_sort", 8, False), ("detect", 4, True)):
             launches, t_ms = k.get(name, (0, 0.0))
             if launches:
-                avg = t_ms / launches
+                avg = t_ms if per_call else t_ms / launches
                 gbs = per_key * n / (avg / 1e3) / 1e9
-                kern[name] = {"launches": launches, "avg_launch_ms": avg, "bytes_per_launch": per_key * n,
+                kern[name] = {"launches": launches, "avg_launch_ms" if not per_call else "ms_per_call": avg,
+                              "bytes_per_launch" if not per_call else "bytes_per_call": per_key * n,
                               "achieved_gbs": gbs, "frac": gbs / peak, "frac_nominal": gbs / NOMINAL_HBM_GBS}
         out[f"2^{lg}"] = {"ms": best, "gkeys_s": n / (best / 1e3) / 1e9,
                           "passes_frac": st["bytes_moved"] / (best / 1e3) / 1e9 / peak,

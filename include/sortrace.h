@@ -346,7 +346,8 @@ enum {
     SR_KERNEL_COPY = 5,       /* copy-back / gather */
     SR_KERNEL_SEGMENTED = 6,  /* segmented / bucket sorts */
     SR_KERNEL_MODEL = 7,      /* learned router: train, predict, histogram, scatter */
-    SR_KERNEL_DISPLACED = 8,  /* few displaced keys: bounds, split, bucket sorts, merge */
+    SR_KERNEL_DISPLACED = 8,  /* keys out of place: the few-displaced-keys path (bounds, split, bucket
+                                 sorts, merge) and the in-place merges of the neighbour repair */
     SR_KERNEL_KINDS = 9
 };
 

@@ -273,7 +273,7 @@ k_tile_order(const typename Key<KT>::U *__restrict__ tmin, const typename Key<KT
 // split of the paper's quicksorts (Section 4, techniques (d) and (g)): every
 // distinct key is a pivot, keys equal to a pivot need no further comparisons,
 // so the split alone sorts the input.
-enum { FEW_SAMPLE = 65536, FEW_SAMPLE_A = 4096, FEW_A_MAX = 3072, FEW_NT2 = 1024 };
+enum { FEW_SAMPLE = 65536, FEW_SAMPLE_A = 4096, FEW_A_MAX = 3072, FEW_A_ALONE = 256, FEW_NT2 = 1024 };
 
 // This CTA's `per` samples (sample indices from `first`) into a shared-memory
 // set, then its images not yet in the call's set into it; the number it added
@@ -307,8 +307,9 @@ __device__ __forceinline__ void few_sample_cta(const typename Key<KT>::T *__rest
 
 // Phase A: one CTA of FEW_NT2 threads puts the first FEW_SAMPLE_A samples
 // into a set in shared memory (FEW_A_SLOTS slots, dynamic shared memory); more
-// than FEW_A_MAX distinct images close the call's set at once, else the
-// images go into the call's set in global memory.
+// than FEW_A_MAX distinct images close the call's set at once; at most
+// FEW_A_ALONE (each seen ~16 times or more on average) make the candidate
+// here; else the images go into the call's set in global memory for phase B.
 enum { FEW_A_SLOTS_LOG2 = 13, FEW_A_SLOTS = 1 << FEW_A_SLOTS_LOG2 };
 template <int KT>
 __global__ void __launch_bounds__(FEW_NT2) k_few_sample(const typename Key<KT>::T *__restrict__ keys, long long n,
@@ -334,6 +335,31 @@ __global__ void __launch_bounds__(FEW_NT2) k_few_sample(const typename Key<KT>::
         if (t == 0) atomicExch(&c->few_over, 1);
         return;
     }
+    const unsigned int nd = s_n;
+    if (nd <= FEW_A_ALONE) {
+        // so few distinct keys that each showed up many times in this sample:
+        // the set is taken as complete (the counting pass checks every key), it
+        // is sorted here and phase B does nothing
+        __shared__ unsigned int s_v[FEW_A_ALONE];
+        __shared__ unsigned int s_k;
+        if (t == 0) s_k = 0u;
+        __syncthreads();
+        for (int q = t; q < FEW_A_SLOTS; q += FEW_NT2)
+            if (s_tab[q] != 0ull) s_v[atomicAdd(&s_k, 1u)] = (unsigned int)(s_tab[q] - 1ull);
+        __syncthreads();
+        if (t < (int)nd) {                         // rank of each image among at most FEW_A_ALONE
+            unsigned int r = 0;
+            for (unsigned int q = 0; q < nd; ++q) r += s_v[q] < s_v[t];
+            ft->sorted[r] = s_v[t];
+        }
+        __syncthreads();
+        if (t == 0 && call_mode(c, n) == MODE_SORT) {
+            c->few_n = nd;
+            __threadfence();
+            c->few_cand = 1;
+        }
+        return;
+    }
     for (int q = t; q < FEW_A_SLOTS; q += FEW_NT2)
         if (s_tab[q] != 0ull)
             few_insert<FEW_SLOTS_LOG2>(ft->slot, &s_new, &c->few_over, (unsigned int)(s_tab[q] - 1ull), 0xffffffffu);
@@ -351,7 +377,7 @@ __global__ void __launch_bounds__(FEW_NT2) k_few_sample2(const typename Key<KT>:
     __shared__ unsigned int s_n, s_new, s_k;
     __shared__ int s_over, s_last;
     if (gate && *gate == 0) return;
-    if (((volatile int *)&c->few_over)[0]) return;
+    if (((volatile int *)&c->few_over)[0] || c->few_cand) return;   // closed, or phase A settled it
     const int t = threadIdx.x;
     few_sample_cta<KT, FEW_NT2, 11>(keys, n, FEW_SAMPLE_A + (long long)blockIdx.x * FEW_NT2, c, ft, s_set, &s_n,
                                     &s_new, &s_over);

@@ -197,12 +197,13 @@ template <int KT, bool VALS> struct PlainSort {
         return VALS || sizeof(T) == 8;
     }
     // How a 2-way tile stages its windows when the arrays are 16-byte
-    // aligned: 16-byte loads through registers, unless SORTRACE_MERGE2_STAGE
-    // is "bulk" (1-D bulk copies).
+    // aligned: 1-D bulk copies (measured faster on GB300: 2^28 int32 merge
+    // steps 6.08 -> 5.81 ms), unless SORTRACE_MERGE2_STAGE is "vec" (16-byte
+    // loads through registers).
     static int stage2() {
         static const int m = [] {
             const char *e = std::getenv("SORTRACE_MERGE2_STAGE");
-            return (e && e[0] == 'b') ? (int)STAGE_BULK : (int)STAGE_VEC;
+            return (e && e[0] == 'v') ? (int)STAGE_VEC : (int)STAGE_BULK;
         }();
         return m;
     }
@@ -345,7 +346,7 @@ template <int KT, bool VALS> struct PlainSort {
                           uk, sk, plo, phi, n, (long long)TS, tiles, (int)NV, win, ctrl);
                 const size_t r_smem = merge_tile_smem<U, NT, IPT, VALS>();
                 if ((st = allow_smem(k_repair<KT, NT, IPT, VALS>, r_smem)) != SR_OK) break;
-                SR_LAUNCH(SR_KERNEL_MERGE, (k_repair<KT, NT, IPT, VALS>), (unsigned)(tiles - 1), NT, r_smem, s,
+                SR_LAUNCH(SR_KERNEL_DISPLACED, (k_repair<KT, NT, IPT, VALS>), (unsigned)(tiles - 1), NT, r_smem, s,
                           uk, uv, sk, sv, n, (long long)TS, tiles, win, ctrl);
             }
             const size_t m_smem = merge_tile_smem<U, NT, IPT, VALS>();

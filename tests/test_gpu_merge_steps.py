@@ -1,9 +1,9 @@
 """GPU parity of the merge steps against the CPU oracle, bit for bit, through
-the C ABI: the 4-way steps (the default for payloads and 8-byte keys) with
-their three ways of staging a tile (1-D bulk copies for 16-byte aligned
-arrays, 16-byte loads through registers, scalar loads for unaligned arrays)
-and the 2-way steps (the default for 4-byte keys), at sizes around every tile
-and group boundary and with ragged tails.  The staging and fan-in switches are
+the C ABI: the 4-way steps (the default for payloads and 8-byte keys) and the
+2-way steps (the default for 4-byte keys), each with its three ways of staging
+a tile (1-D bulk copies for 16-byte aligned arrays, 16-byte loads through
+registers, scalar loads for unaligned arrays), at sizes around every tile and
+group boundary and with ragged tails.  The staging and fan-in switches are
 read once per process, so the forced runs go through child processes."""
 import os
 import subprocess
@@ -151,11 +151,11 @@ print("child ok", sr.stats()["passes_planned"])
 @pytest.mark.parametrize("env", [{"SORTRACE_MERGE_FANIN": "4"},
                                  {"SORTRACE_MERGE_FANIN": "4", "SORTRACE_MERGE4_STAGE": "vec"},
                                  {"SORTRACE_MERGE_FANIN": "2"},
-                                 {"SORTRACE_MERGE_FANIN": "2", "SORTRACE_MERGE2_STAGE": "bulk"}])
+                                 {"SORTRACE_MERGE_FANIN": "2", "SORTRACE_MERGE2_STAGE": "vec"}])
 def test_other_staging_and_fanin(env):
     """Every key shape forced to 4-way steps (bulk-copy staging, then 16-byte
-    register staging), and to 2-way steps (16-byte register staging, then
-    bulk copies), in child processes: the same sizes and classes against the
+    register staging), and to 2-way steps (bulk copies, then 16-byte register
+    staging), in child processes: the same sizes and classes against the
     oracle."""
     e = dict(os.environ)
     e.update(env)

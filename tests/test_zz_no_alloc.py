@@ -35,6 +35,9 @@ def test_noalloc_matches_sort_keys_back_to_back(gpu_lib):
         (si.lognormal_f32(300_001, 23), 2),
         (si.reversed_i32(99_999, 24), 0),
         (np.random.default_rng(25).integers(0, 1 << 64, 700_001, dtype=np.uint64), 3),
+        # 8-byte keys at exactly the largest size allowed (the widest layout)
+        (np.random.default_rng(29).integers(0, 1 << 64, MAX_KEYS, dtype=np.uint64), 3),
+        (np.random.default_rng(30).integers(-(1 << 63), (1 << 63) - 1, MAX_KEYS, dtype=np.int64), 4),
         (np.random.default_rng(26).integers(0, 9, 5000).astype(np.int64), 4),
         (si.few_unique_i32(7_681, 27).view(np.uint32), 1),
     ]
