@@ -1345,71 +1345,6 @@ __device__ __forceinline__ void pair_tile(const long long *__restrict__ split1, 
     ye = P.x_end + o1 - (xe - P.x_beg);
 }
 
-// The merge-path test of a 4-way boundary at m: whether AB[m] goes before
-// CD[d - 1 - m] (!(CD[d-1-m] < AB[m])).  The two keys' inner searches run in
-// one loop so their loads are in flight together.
-template <int KT>
-__device__ __forceinline__ bool probe_ab_cd(const typename Key<KT>::T *__restrict__ src,
-                                            const long long *__restrict__ split1, const PairView &AB,
-                                            const PairView &CD, int nv, long long d, long long m) {
-    typedef Key<KT> K;
-    typedef typename K::U U;
-    const long long m2 = d - 1 - m;
-    const long long j1 = m / nv, j2 = m2 / nv;
-    long long xs1, xe1, ys1, ye1, xs2, xe2, ys2, ye2;
-    pair_tile(split1, AB, nv, j1, xs1, xe1, ys1, ye1);
-    pair_tile(split1, CD, nv, j2, xs2, xe2, ys2, ye2);
-    const int r1 = (int)(m - j1 * nv), r2 = (int)(m2 - j2 * nv);
-    const int ny1 = (int)(ye1 - ys1), ny2 = (int)(ye2 - ys2);
-    int lo1 = max(0, r1 + 1 - ny1), hi1 = min(r1 + 1, (int)(xe1 - xs1));
-    int lo2 = max(0, r2 + 1 - ny2), hi2 = min(r2 + 1, (int)(xe2 - xs2));
-    while (lo1 < hi1 || lo2 < hi2) {
-        if (lo1 < hi1) {
-            const int mid = (lo1 + hi1) >> 1;
-            if (!(K::ord(src[ys1 + r1 - mid]) < K::ord(src[xs1 + mid]))) lo1 = mid + 1;
-            else hi1 = mid;
-        }
-        if (lo2 < hi2) {
-            const int mid = (lo2 + hi2) >> 1;
-            if (!(K::ord(src[ys2 + r2 - mid]) < K::ord(src[xs2 + mid]))) lo2 = mid + 1;
-            else hi2 = mid;
-        }
-    }
-    U a = 0, c = 0;                                // AB[m] and CD[m2]: the later of the two last keys taken
-    if (lo1 > 0) a = K::ord(src[xs1 + lo1 - 1]);
-    if (r1 - lo1 >= 0) {
-        const U y = K::ord(src[ys1 + r1 - lo1]);
-        a = a < y ? y : a;
-    }
-    if (lo2 > 0) c = K::ord(src[xs2 + lo2 - 1]);
-    if (r2 - lo2 >= 0) {
-        const U y = K::ord(src[ys2 + r2 - lo2]);
-        c = c < y ? y : c;
-    }
-    return !(c < a);
-}
-
-// How many X keys are among the first x outputs of P (0 <= x <= P.len).
-template <int KT>
-__device__ __forceinline__ long long pair_split(const typename Key<KT>::T *__restrict__ src,
-                                                const long long *__restrict__ split1, const PairView &P, int nv,
-                                                long long x) {
-    typedef Key<KT> K;
-    if (x >= P.len) return P.x_end - P.x_beg;
-    const long long j = x / nv;
-    long long xs, xe, ys, ye;
-    pair_tile(split1, P, nv, j, xs, xe, ys, ye);
-    const int r = (int)(x - j * nv);
-    const int nx = (int)(xe - xs), ny = (int)(ye - ys);
-    int lo = max(0, r - ny), hi = min(r, nx);
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (!(K::ord(src[ys + r - 1 - mid]) < K::ord(src[xs + mid]))) lo = mid + 1;
-        else hi = mid;
-    }
-    return xs + lo - P.x_beg;
-}
-
 // First and last key images of P's tile j (j * nv < P.len).
 template <int KT>
 __device__ __forceinline__ typename Key<KT>::U pair_first(const typename Key<KT>::T *__restrict__ src,
@@ -1436,6 +1371,120 @@ __device__ __forceinline__ typename Key<KT>::U pair_last(const typename Key<KT>:
         v = v < y ? y : v;
     }
     return v;
+}
+
+// S_P(x), how many X keys are among the first x outputs of P (0 <= x <=
+// P.len), at x = j * nv: a tile boundary of P (from the split table), or P's
+// end.
+__device__ __forceinline__ long long pair_count_at_tile(const long long *__restrict__ split1, const PairView &P,
+                                                        int nv, long long j) {
+    if (j <= 0) return 0;
+    if (j * nv >= P.len) return P.x_end - P.x_beg;
+    return split1[4 * (P.t0 + j)] - P.x_beg;
+}
+
+// Two known values of S_P: S_P(xl) = sl and S_P(xh) = sh, xl <= xh.  Since
+// S_P and x - S_P never decrease, S_P(x) for xl <= x <= xh lies in
+// [max(sl, sh - (xh - x)), min(sh, sl + (x - xl))].
+struct PairAnchors {
+    long long xl, sl, xh, sh;
+};
+
+// The bounded merge-path search for S_P(x) inside the anchors' range: about
+// log2 of the anchors' distance dependent rounds of two loads.
+template <int KT>
+__device__ __forceinline__ long long pair_count(const typename Key<KT>::T *__restrict__ src, const PairView &P,
+                                               const PairAnchors &q, long long x) {
+    typedef Key<KT> K;
+    const long long nx = P.x_end - P.x_beg, ny = P.y_end - P.x_end;
+    long long lo = max(max(q.sl, q.sh - (q.xh - x)), max(0ll, x - ny));
+    long long hi = min(min(q.sh, q.sl + (x - q.xl)), min(x, nx));
+    while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if (!(K::ord(src[P.x_end + x - 1 - mid]) < K::ord(src[P.x_beg + mid]))) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// The 4-way split of boundary d (a multiple of nv, outputs counted from A's
+// start) between AB and CD: the number x of AB keys among the first d outputs
+// of merge(AB, CD), found in [lo, hi] (already narrowed to one tile of AB by
+// the coarse search) by a group of 2^lg lanes, with S_AB(x) in *sab and
+// S_CD(d - x) in *scd.  Each round the lanes probe evenly spaced m: AB[m]
+// against CD[d - 1 - m], keys of the never-written merged pairs found by the
+// bounded searches of pair_count; the lanes next to the round's answer hand
+// their counts on as the anchors of the next round, so every search is about
+// as long as the stretch the round leaves (the searches of one boundary take
+// about log2(nv) + log2(nv / (G+1)) + ... rounds instead of log2(nv) per
+// probe).
+template <int KT>
+__device__ __forceinline__ long long ab_cd_split(const typename Key<KT>::T *__restrict__ src,
+                                                 const long long *__restrict__ split1, const PairView &AB,
+                                                 const PairView &CD, int nv, long long d, long long lo, long long hi,
+                                                 int lane, int lg, long long *sab, long long *scd) {
+    typedef Key<KT> K;
+    typedef typename K::U U;
+    const int G = 1 << lg;
+    const int j = lane & (G - 1);
+    const int base = lane & ~(G - 1);
+    const unsigned mask = lg == 5 ? 0xffffffffu : (((1u << G) - 1u) << base);
+    // anchors: the AB tile boundaries around [lo, hi] and the CD boundaries
+    // they face (probe m reads AB up to x = m + 1 and CD up to x = d - m)
+    const long long j0 = lo / nv;
+    PairAnchors ab, cd;
+    ab.xl = j0 * nv;
+    ab.sl = pair_count_at_tile(split1, AB, nv, j0);
+    ab.xh = min((j0 + 1) * nv, AB.len);
+    ab.sh = pair_count_at_tile(split1, AB, nv, j0 + 1);
+    cd.xl = max(d - (j0 + 1) * nv, 0ll);
+    cd.sl = pair_count_at_tile(split1, CD, nv, d / nv - j0 - 1);
+    cd.xh = min(d - j0 * nv, CD.len);
+    cd.sh = pair_count_at_tile(split1, CD, nv, d / nv - j0);
+    while (hi > lo) {
+        const long long step = (hi - lo + G) / (G + 1);
+        const long long m = lo + (long long)(j + 1) * step - 1;
+        bool before = false;
+        long long s1 = 0, s2 = 0;
+        if (m < hi) {
+            const long long x1 = m + 1, x2 = d - m;
+            s1 = pair_count<KT>(src, AB, ab, x1);
+            s2 = pair_count<KT>(src, CD, cd, x2);
+            U a = 0, c = 0;                        // AB[m], CD[d - 1 - m]: the later of the last keys taken
+            if (s1 > 0) a = K::ord(src[AB.x_beg + s1 - 1]);
+            if (x1 - 1 - s1 >= 0) {
+                const U y = K::ord(src[AB.x_end + x1 - 1 - s1]);
+                a = a < y ? y : a;
+            }
+            if (s2 > 0) c = K::ord(src[CD.x_beg + s2 - 1]);
+            if (x2 - 1 - s2 >= 0) {
+                const U y = K::ord(src[CD.x_end + x2 - 1 - s2]);
+                c = c < y ? y : c;
+            }
+            before = !(c < a);
+        }
+        const int cnt = __popc(__ballot_sync(mask, before));
+        const long long s1l = __shfl_sync(mask, s1, base + (cnt > 0 ? cnt - 1 : 0));
+        const long long s2l = __shfl_sync(mask, s2, base + (cnt > 0 ? cnt - 1 : 0));
+        const long long s1h = __shfl_sync(mask, s1, base + (cnt < G ? cnt : G - 1));
+        const long long s2h = __shfl_sync(mask, s2, base + (cnt < G ? cnt : G - 1));
+        const long long mlo = lo + (long long)cnt * step - 1;          // lane cnt - 1's probe
+        const long long mhi = lo + (long long)(cnt + 1) * step - 1;    // lane cnt's probe
+        if (cnt > 0) {
+            ab.xl = mlo + 1; ab.sl = s1l;
+            cd.xh = d - mlo; cd.sh = s2l;
+        }
+        if (cnt < G && mhi < hi) {
+            ab.xh = mhi + 1; ab.sh = s1h;
+            cd.xl = d - mhi; cd.sl = s2h;
+        }
+        const long long nhi = cnt == G ? hi : mhi;
+        lo = lo + (long long)cnt * step;
+        hi = min(hi, nhi);
+    }
+    *sab = pair_count<KT>(src, AB, ab, lo);
+    *scd = pair_count<KT>(src, CD, cd, d - lo);
+    return lo;
 }
 
 // 4-way splits of every output tile boundary of step `step`, whose groups
@@ -1482,14 +1531,12 @@ k_partition4(const typename Key<KT>::T *__restrict__ uk, const typename Key<KT>:
             if (jt > jlo) lo = max(lo, (jt - 1) * nv + 1);
             if (jt <= jhi) hi = min(hi, jt * nv);
         }
-        // fine: AB outputs among the first d outputs of merge(AB, CD)
-        lo = group_search(lo, hi, lane, lg,
-                          [&](long long m) { return probe_ab_cd<KT>(src, split1, AB, CD, nv, d, m); });
     }
+    // fine: AB outputs among the first d outputs of merge(AB, CD), and the
+    // counts of A and C among them
+    long long a, cc;
+    const long long x = ab_cd_split<KT>(src, split1, AB, CD, nv, d, lo, hi, lane, lg, &a, &cc);
     if (leader) {
-        const long long x = lo;
-        const long long a = pair_split<KT>(src, split1, AB, nv, x);
-        const long long cc = pair_split<KT>(src, split1, CD, nv, d - x);
         split4[8 * b + 0] = e[0] + a;
         split4[8 * b + 1] = e[1] + (x - a);
         split4[8 * b + 2] = e[2] + cc;

@@ -330,13 +330,90 @@ def _partition4(src, n, ts, tiles, nv, rs0, nruns, span, split1, b, G):
                 lo = max(lo, (jt - 1) * nv + 1)
             if jt <= jhi:
                 hi = min(hi, jt * nv)
-        # probe_ab_cd: both keys' searches (each as _pair_key), then the test
-        lo, _ = group_search(lo, hi, G, lambda m: not (
-            _pair_key(src, split1, CD, nv, d - 1 - m) < _pair_key(src, split1, AB, nv, m)))
-    x = lo
-    a = _pair_split(src, split1, AB, nv, x)
-    c = _pair_split(src, split1, CD, nv, d - x)
+    x, a, c = _ab_cd_split(src, split1, AB, CD, nv, d, lo, hi, G)
+    # the same split by plain searches: every probe's keys searched in full
+    want, _ = group_search(lo, hi, G, lambda m: not (
+        _pair_key(src, split1, CD, nv, d - 1 - m) < _pair_key(src, split1, AB, nv, m)))
+    assert x == want
+    assert a == _pair_split(src, split1, AB, nv, x) and c == _pair_split(src, split1, CD, nv, d - x)
     return [e[0] + a, e[1] + (x - a), e[2] + c, e[3] + (d - x - c)] + e[1:]
+
+
+def _pair_count_at_tile(split1, P, nv, j):
+    x_beg, x_end, y_end, t0, ln = P
+    if j <= 0:
+        return 0
+    if j * nv >= ln:
+        return x_end - x_beg
+    return split1[t0 + j][0] - x_beg
+
+
+def _pair_count(src, P, q, x):
+    """pair_count: S_P(x) searched inside the anchors q = [xl, sl, xh, sh]."""
+    x_beg, x_end, y_end, t0, ln = P
+    xl, sl, xh, sh = q
+    assert xl <= x <= xh
+    nx, ny = x_end - x_beg, y_end - x_end
+    X, Y = _Checked(src, "X", x_beg, x_end), _Checked(src, "Y", x_end, y_end)
+    lo = max(sl, sh - (xh - x), 0, x - ny)
+    hi = min(sh, sl + (x - xl), x, nx)
+    assert lo <= hi
+    while lo < hi:
+        mid = (lo + hi) >> 1
+        if not (Y[x_end + x - 1 - mid] < X[x_beg + mid]):
+            lo = mid + 1
+        else:
+            hi = mid
+    return lo
+
+
+def _ab_cd_split(src, split1, AB, CD, nv, d, lo, hi, G):
+    """ab_cd_split (sr_kernels.cuh): G lanes, each round's bounded searches
+    anchored by the counts the lanes next to the previous answer found."""
+    j0 = lo // nv
+    ab = [j0 * nv, _pair_count_at_tile(split1, AB, nv, j0), min((j0 + 1) * nv, AB[4]),
+          _pair_count_at_tile(split1, AB, nv, j0 + 1)]
+    cd = [max(d - (j0 + 1) * nv, 0), _pair_count_at_tile(split1, CD, nv, d // nv - j0 - 1),
+          min(d - j0 * nv, CD[4]), _pair_count_at_tile(split1, CD, nv, d // nv - j0)]
+    assert hi <= ab[2] or hi == lo
+    while hi > lo:
+        step = (hi - lo + G) // (G + 1)
+        bs, s1s, s2s = [], [], []
+        for j in range(G):
+            m = lo + (j + 1) * step - 1
+            b, s1, s2 = False, 0, 0
+            if m < hi:
+                x1, x2 = m + 1, d - m
+                s1 = _pair_count(src, AB, ab, x1)
+                s2 = _pair_count(src, CD, cd, x2)
+                a = src[AB[0] + s1 - 1] if s1 > 0 else None
+                if x1 - 1 - s1 >= 0:
+                    y = src[AB[1] + x1 - 1 - s1]
+                    a = y if a is None or a < y else a
+                c = src[CD[0] + s2 - 1] if s2 > 0 else None
+                if x2 - 1 - s2 >= 0:
+                    y = src[CD[1] + x2 - 1 - s2]
+                    c = y if c is None or c < y else c
+                assert a.v == _pair_key(src, split1, AB, nv, m).v
+                assert c.v == _pair_key(src, split1, CD, nv, d - 1 - m).v
+                b = not (c < a)
+            bs.append(b)
+            s1s.append(s1)
+            s2s.append(s2)
+        cnt = sum(bs)
+        assert bs == [True] * cnt + [False] * (G - cnt)
+        mlo = lo + cnt * step - 1
+        mhi = lo + (cnt + 1) * step - 1
+        if cnt > 0:
+            ab[0], ab[1] = mlo + 1, s1s[cnt - 1]
+            cd[2], cd[3] = d - mlo, s2s[cnt - 1]
+        if cnt < G and mhi < hi:
+            ab[2], ab[3] = mhi + 1, s1s[cnt]
+            cd[0], cd[1] = d - mhi, s2s[cnt]
+        nhi = hi if cnt == G else mhi
+        lo = lo + cnt * step
+        hi = min(hi, nhi)
+    return lo, _pair_count(src, AB, ab, lo), _pair_count(src, CD, cd, d - lo)
 
 
 def _serial(s, a, a_end, b, b_end, ipt, sw=None, c=None):
