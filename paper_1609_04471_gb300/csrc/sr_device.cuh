@@ -217,6 +217,27 @@ __device__ __forceinline__ void serial_merge_slack(const U *s, int a, int a_end,
     }
 }
 
+// serial_merge_slack for ranges whose ends are marked: the key after each
+// range is the largest image (umax) and neither range holds a umax key, so an
+// exhausted side is never taken while the other has keys and a step is one
+// comparison (ties still go to A).  A thread whose outputs run past both
+// ranges keeps taking A past its mark: s must be readable IPT keys beyond it.
+template <typename U, int IPT>
+__device__ __forceinline__ void serial_merge_marked(const U *s, int a, int b, U (&k)[IPT], int (&ix)[IPT]) {
+    U ak = s[a];
+    U bk = s[b];
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+        const bool take_a = !(bk < ak);
+        k[i] = take_a ? ak : bk;
+        ix[i] = take_a ? a : b;
+        const int nx = (take_a ? a : b) + 1;
+        const U nk = s[nx];
+        if (take_a) { a = nx; ak = nk; }
+        else        { b = nx; bk = nk; }
+    }
+}
+
 template <typename U, int IPT>
 __device__ __forceinline__ void serial_merge(const U *s, int a, int a_end, int b, int b_end,
                                              U (&k)[IPT], int (&ix)[IPT]) {

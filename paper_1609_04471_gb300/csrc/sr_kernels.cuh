@@ -1053,17 +1053,22 @@ __device__ __forceinline__ void write_tile(const typename Key<KT>::U (&k)[IPT], 
     }
 }
 
-// Dynamic shared memory that merge_tile needs: NT*IPT + 16 staged keys (and
+// Staged keys (and values) of a merge tile of NV keys: the two windows in
+// 4-key groups, a spare group between them for A's end mark, and B's mark.
+template <int NV> constexpr int merge_tile_sv() { return NV + 20; }
+
+// Dynamic shared memory that merge_tile needs: merge_tile_sv staged keys (and
 // as many values), plus the key slack the one-load merge step reads into.
 template <typename U, int NT, int IPT, bool VALS>
 constexpr size_t merge_tile_smem() {
-    return (size_t)(NT * IPT + 16) * (sizeof(U) + (VALS ? 4 : 0)) + (SR_MERGE_1LD ? (size_t)(IPT + 8) * sizeof(U) : 0);
+    return (size_t)merge_tile_sv<NT * IPT>() * (sizeof(U) + (VALS ? 4 : 0)) +
+           (SR_MERGE_1LD ? (size_t)(IPT + 8) * sizeof(U) : 0);
 }
 
 // Merges one output tile: outputs [out0, out0 + cnt) of the stable merge of
 // the sorted ranges A = src[a0 .. a1) and B = src[b0 .. b0 + cnt - (a1 - a0)),
 // written to dst at out0.  All threads of the CTA call it; s / sv are shared
-// buffers of NT*IPT + 16 keys / values, and with SR_MERGE_1LD the key buffer
+// buffers of merge_tile_sv keys / values, and with SR_MERGE_1LD the key buffer
 // must stay readable IPT + 8 keys further (the memory after it: the value
 // buffer, or padding) -- merge_tile_smem gives the dynamic shared memory for
 // s followed by sv.  `n` bounds the global buffers (loads stay below it).
@@ -1079,7 +1084,10 @@ constexpr size_t merge_tile_smem() {
 // 1-D bulk copies that one thread starts, completed on this mbarrier (the
 // keys past the array's last 16-byte boundary by plain loads), then turn them
 // into order images in place; a tile whose copies do not complete within the
-// wait's limit reports SR_ERR_TIMEOUT in `status` and writes nothing.
+// wait's limit reports SR_ERR_TIMEOUT in `status` and writes nothing.  B's
+// groups start one group after A's, and the key after each window is set to
+// umax: when neither window holds a umax key, the merge steps compare once
+// (serial_merge_marked).
 template <int KT, int NT, int IPT, bool VALS, bool VEC>
 __device__ __forceinline__ void merge_tile(const typename Key<KT>::T *__restrict__ src_k,
                                            typename Key<KT>::T *__restrict__ dst_k,
@@ -1102,10 +1110,10 @@ __device__ __forceinline__ void merge_tile(const typename Key<KT>::T *__restrict
         const long long ge[2] = {(a1 + 3) & ~3ll, (b0 + bcnt + 3) & ~3ll};
         const int nag = acnt > 0 ? (int)((ge[0] - g0[0]) >> 2) : 0;
         const int nbg = bcnt > 0 ? (int)((ge[1] - g0[1]) >> 2) : 0;
-        const int first[2] = {0, nag};
+        const int first[2] = {0, nag + 1};        // a spare group between the windows
         const int ng[2] = {nag, nbg};
         sa = (int)(a0 - g0[0]);
-        sb = 4 * nag + (int)(b0 - g0[1]);
+        sb = 4 * (nag + 1) + (int)(b0 - g0[1]);
         const long long n4 = n & ~3ll;
         if (t == 0) mbar_init(bar, 1);
         __syncthreads();
@@ -1145,7 +1153,7 @@ __device__ __forceinline__ void merge_tile(const typename Key<KT>::T *__restrict
             return;
         }
         if (KT != SR_KEY_U32 && KT != SR_KEY_U64) {       // raw keys -> order images, in place
-            for (int g = t; g < nag + nbg; g += NT) {
+            for (int g = t; g < nag + 1 + nbg; g += NT) {
                 if (sizeof(U) == 4) {
                     uint4 q = *reinterpret_cast<uint4 *>(s + 4 * g);
                     q.x = (uint32_t)K::ord((T)q.x); q.y = (uint32_t)K::ord((T)q.y);
@@ -1156,6 +1164,11 @@ __device__ __forceinline__ void merge_tile(const typename Key<KT>::T *__restrict
                     for (int e2 = 0; e2 < 4; ++e2) s[4 * g + e2] = K::ord((T)s[4 * g + e2]);
                 }
             }
+            __syncthreads();
+        }
+        if (t == 0) {                              // the windows' end marks
+            s[sa + acnt] = umax_of<U>();
+            s[sb + bcnt] = umax_of<U>();
         }
     } else if (VEC) {
         const long long a0g = a0 & ~3ll, b0g = b0 & ~3ll;
@@ -1230,7 +1243,11 @@ __device__ __forceinline__ void merge_tile(const typename Key<KT>::T *__restrict
     const int sp = merge_path(s + sa, acnt, s + sb, bcnt, diag);
     U k[IPT];
     int ix[IPT];
-    if (SR_MERGE_1LD)
+    const bool marked = VEC && bar && (acnt == 0 || s[sa + acnt - 1] != umax_of<U>()) &&
+                        (bcnt == 0 || s[sb + bcnt - 1] != umax_of<U>());
+    if (marked)
+        serial_merge_marked<U, IPT>(s, sa + sp, sb + diag - sp, k, ix);
+    else if (SR_MERGE_1LD)
         serial_merge_slack<U, IPT>(s, sa + sp, sa + acnt, sb + diag - sp, sb + bcnt, k, ix);
     else
         serial_merge<U, IPT>(s, sa + sp, sa + acnt, sb + diag - sp, sb + bcnt, k, ix);
@@ -1253,7 +1270,7 @@ k_merge(typename Key<KT>::T *uk, uint32_t *uv, typename Key<KT>::T *sk, uint32_t
     typedef Key<KT> K;
     typedef typename K::U U;
     constexpr int NV = NT * IPT;
-    constexpr int SV = NV + 16;                    // staged keys, with room for window slack
+    constexpr int SV = merge_tile_sv<NV>();        // staged keys, with room for window slack
     if (step >= steps_of(c)) return;               // also when the input needs no sorting
     extern __shared__ __align__(16) unsigned char smem[];
     U *s = reinterpret_cast<U *>(smem);

@@ -957,3 +957,74 @@ def test_few_keys_chunked_write_and_lookup_model():
     for _ in range(2000):
         u = rng.randrange(1 << 32)
         assert look(u) == (imgs.index(u) if u in s else None)
+
+
+def test_marked_merge_tile_model():
+    """merge_tile's bulk staging (sr_kernels.cuh) with end-marked windows: A's
+    4-key groups, a spare group, B's groups, umax after each window, and the
+    one-comparison merge step (serial_merge_marked).  Outputs equal the stable
+    merge (ties to A), every staged slot fits merge_tile_sv, and every read
+    stays below it plus the IPT + 8 keys of slack."""
+    rng = random.Random(11)
+    UMAX = 10 ** 9
+    for trial in range(400):
+        NT, IPT = rng.choice([(4, 3), (8, 5), (16, 7), (8, 25)])
+        NV = NT * IPT
+        SV = NV + 20
+        size = SV + IPT + 8
+        cnt = rng.randint(1, NV)
+        acnt = rng.randint(0, cnt)
+        bcnt = cnt - acnt
+        alpha = rng.choice([3, 50, 10 ** 6])
+        A = sorted(rng.randrange(alpha) for _ in range(acnt))
+        B = sorted(rng.randrange(alpha) for _ in range(bcnt))
+        a0, b0 = rng.randint(0, 50), rng.randint(0, 50)
+        g0a, g0b = a0 & ~3, b0 & ~3
+        nag = (((a0 + acnt + 3) & ~3) - g0a) >> 2 if acnt else 0
+        nbg = (((b0 + bcnt + 3) & ~3) - g0b) >> 2 if bcnt else 0
+        sa = a0 - g0a
+        sb = 4 * (nag + 1) + (b0 - g0b)
+        assert 4 * (nag + 1 + nbg) <= NV + 16 and sb + bcnt < SV
+        # garbage: compared only by the steps of outputs past cnt, never output
+        smem = [(rng.randrange(2 * alpha), 8, i) for i in range(size)]
+        for i, v in enumerate(A):
+            smem[sa + i] = (v, 0, i)
+        for i, v in enumerate(B):
+            smem[sb + i] = (v, 1, i)
+        smem[sa + acnt] = (UMAX, 9, 0)
+        smem[sb + bcnt] = (UMAX, 9, 1)
+        reads = [0]
+
+        def rd(i):
+            assert 0 <= i < size
+            reads[0] = max(reads[0], i)
+            return smem[i]
+
+        def lt(x, y):                                 # the order of the images alone
+            return x[0] < y[0]
+        out = []
+        for t in range(NT):
+            diag = min(t * IPT, cnt)
+            lo, hi = max(0, diag - bcnt), min(diag, acnt)
+            while lo < hi:
+                m = (lo + hi) >> 1
+                if not lt(rd(sb + diag - 1 - m), rd(sa + m)):
+                    lo = m + 1
+                else:
+                    hi = m
+            a, b = sa + lo, sb + diag - lo
+            ak, bk = rd(a), rd(b)
+            k = []
+            for i in range(IPT):
+                take_a = not lt(bk, ak)
+                k.append(ak if take_a else bk)
+                nx = (a if take_a else b) + 1
+                nk = rd(nx)
+                if take_a:
+                    a, ak = nx, nk
+                else:
+                    b, bk = nx, nk
+            out.extend(k[:max(0, min(IPT, cnt - diag))])
+        want = sorted([(v, 0, i) for i, v in enumerate(A)] + [(v, 1, i) for i, v in enumerate(B)])
+        assert out == want, (NT, IPT, acnt, bcnt)
+        assert reads[0] < size
