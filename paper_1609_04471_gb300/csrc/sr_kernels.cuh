@@ -667,11 +667,34 @@ k_block_sort(const typename Key<KT>::T *in_k, const uint32_t *in_v, typename Key
     auto out_tile = [&]() -> long long {
         return (dest && c && c->tile_perm) ? (long long)dest[blockIdx.x] : (long long)blockIdx.x;
     };
+    // whole tiles of 16-byte aligned arrays move in 16-byte vectors
+    typedef typename K::T T;
+    constexpr int VW = 16 / sizeof(T);
+    const bool vec = cnt == NV && (((uintptr_t)(in_k + base)) & 15) == 0 &&
+                     (!VALS || (((uintptr_t)(in_v + base)) & 15) == 0);
+    if (vec) {
+        for (int g = t; g < NV / VW; g += NT) {
+            const uint4 q = __ldg(reinterpret_cast<const uint4 *>(in_k + base) + g);
+            if (sizeof(T) == 4) {
+                *reinterpret_cast<uint4 *>(s + 4 * g) =
+                    make_uint4((uint32_t)K::ord((T)q.x), (uint32_t)K::ord((T)q.y), (uint32_t)K::ord((T)q.z),
+                               (uint32_t)K::ord((T)q.w));
+            } else {
+                *reinterpret_cast<ulonglong2 *>(s + 2 * g) =
+                    make_ulonglong2((unsigned long long)K::ord((T)(((unsigned long long)q.y << 32) | q.x)),
+                                    (unsigned long long)K::ord((T)(((unsigned long long)q.w << 32) | q.z)));
+            }
+        }
+        if (VALS)
+            for (int g = t; g < NV / 4; g += NT)
+                *reinterpret_cast<uint4 *>(sv + 4 * g) = __ldg(reinterpret_cast<const uint4 *>(in_v + base) + g);
+    } else {
 #pragma unroll
-    for (int i = 0; i < IPT; ++i) {
-        const int idx = i * NT + t;
-        s[idx] = idx < cnt ? K::ord(in_k[base + idx]) : umax_of<U>();
-        if (VALS) sv[idx] = idx < cnt ? in_v[base + idx] : 0u;
+        for (int i = 0; i < IPT; ++i) {
+            const int idx = i * NT + t;
+            s[idx] = idx < cnt ? K::ord(in_k[base + idx]) : umax_of<U>();
+            if (VALS) sv[idx] = idx < cnt ? in_v[base + idx] : 0u;
+        }
     }
     __syncthreads();
     // presortedness of the tile
@@ -727,16 +750,42 @@ k_block_sort(const typename Key<KT>::T *in_k, const uint32_t *in_v, typename Key
         v[i] = VALS ? sv[t * IPT + i] : 0u;
     }
     __syncthreads();
-    block_sort<U, NT, IPT, VALS>(k, v, s, sv);
+    if constexpr (!VALS && sizeof(U) == 4 && SR_BSORT_PP == 1) {
+        s = block_sort_pp<U, NT, IPT>(k, s, s + block_sort_pp_keys<NT, IPT>());
+    } else if constexpr (!VALS && sizeof(U) == 4 && SR_BSORT_PP == 2) {
+        s = block_sort_rs<U, NT, IPT>(k, s);
+    } else {
+        block_sort<U, NT, IPT, VALS>(k, v, s, sv);
 #pragma unroll
-    for (int i = 0; i < IPT; ++i) {
-        s[t * IPT + i] = k[i];
-        if (VALS) sv[t * IPT + i] = v[i];
+        for (int i = 0; i < IPT; ++i) {
+            s[t * IPT + i] = k[i];
+            if (VALS) sv[t * IPT + i] = v[i];
+        }
+        __syncthreads();
     }
-    __syncthreads();
     const long long otile = out_tile(), obase = otile * NV;
     if (t == 0 && tile_lo) { tile_lo[otile] = s[0]; tile_hi[otile] = s[cnt - 1]; }
     samples(false, otile);
+    if (vec && (((uintptr_t)(out_k + obase)) & 15) == 0 && (!VALS || (((uintptr_t)(out_v + obase)) & 15) == 0)) {
+        for (int g = t; g < NV / VW; g += NT) {
+            uint4 q;
+            if (sizeof(T) == 4) {
+                const uint4 r = *reinterpret_cast<const uint4 *>(s + 4 * g);
+                q = make_uint4((uint32_t)K::unord((U)r.x), (uint32_t)K::unord((U)r.y), (uint32_t)K::unord((U)r.z),
+                               (uint32_t)K::unord((U)r.w));
+            } else {
+                const ulonglong2 r = *reinterpret_cast<const ulonglong2 *>(s + 2 * g);
+                const unsigned long long e0 = (unsigned long long)K::unord((U)r.x);
+                const unsigned long long e1 = (unsigned long long)K::unord((U)r.y);
+                q = make_uint4((uint32_t)e0, (uint32_t)(e0 >> 32), (uint32_t)e1, (uint32_t)(e1 >> 32));
+            }
+            reinterpret_cast<uint4 *>(out_k + obase)[g] = q;
+        }
+        if (VALS)
+            for (int g = t; g < NV / 4; g += NT)
+                reinterpret_cast<uint4 *>(out_v + obase)[g] = *reinterpret_cast<const uint4 *>(sv + 4 * g);
+        return;
+    }
     for (int idx = t; idx < cnt; idx += NT) {
         out_k[obase + idx] = K::unord(s[idx]);
         if (VALS) out_v[obase + idx] = sv[idx];

@@ -1028,3 +1028,94 @@ def test_marked_merge_tile_model():
         want = sorted([(v, 0, i) for i, v in enumerate(A)] + [(v, 1, i) for i, v in enumerate(B)])
         assert out == want, (NT, IPT, acnt, bcnt)
         assert reads[0] < size
+
+
+def _block_sort_pp(keys, NT, IPT, umax):
+    """block_sort_pp and block_sort_rs (sr_device.cuh) on one tile of NT*IPT
+    keys: the per-warp stretches of the warp-synchronised rounds and the end
+    marks (the layout both share; block_sort_rs reads a round's runs from the
+    buffer it then writes, after its warp or block has read them all).  Checks
+    every read against the buffer and, in those rounds, every read and write
+    against the warp's own stretch, and that a round reads only slots the
+    round before it wrote."""
+    W = 32 * IPT + 32
+    size = NT * IPT + NT
+    assert (NT // 32) * W == size
+    bufs = [[None] * size, [None] * size]
+    regs = [sorted(keys[t * IPT:(t + 1) * IPT]) for t in range(NT)]
+    fast = not any(r[-1] == umax for r in regs)
+    for t in range(NT):
+        w, lane = t >> 5, t & 31
+        for i in range(IPT):
+            bufs[0][w * W + lane * (IPT + 1) + i] = regs[t][i]
+        bufs[0][w * W + lane * (IPT + 1) + IPT] = umax
+    src, dst = 0, 1
+    coop = 2
+    while coop <= NT:
+        new = [None] * size
+        for t in range(NT):
+            w = t >> 5
+            first = t & ~(coop - 1)
+            run = (coop >> 1) * IPT
+            diag = (t - first) * IPT
+            if coop <= 32:
+                gl = (first & 31) // coop
+                a0 = w * W + 2 * gl * (run + 1)
+                b0 = a0 + run + 1
+                o0 = w * W + gl * (2 * run + 1)
+                lo_ok, hi_ok = w * W, (w + 1) * W
+            else:
+                rs = (coop // 64) * W
+                g = first // coop
+                a0, o0 = 2 * g * rs, 2 * g * rs
+                b0 = a0 + rs
+                lo_ok, hi_ok = 0, size
+
+            def rd(i):
+                assert lo_ok <= i < hi_ok and bufs[src][i] is not None, (coop, t, i)
+                return bufs[src][i]
+            lo, hi = max(0, diag - run), min(diag, run)
+            while lo < hi:
+                mid = (lo + hi) >> 1
+                if not (rd(b0 + diag - 1 - mid) < rd(a0 + mid)):
+                    lo = mid + 1
+                else:
+                    hi = mid
+            a, b, a_end, b_end = a0 + lo, b0 + diag - lo, a0 + run, b0 + run
+            ak, bk = rd(a), rd(b)
+            for i in range(IPT):
+                tb = (bk < ak) if fast else (b < b_end and (a >= a_end or bk < ak))
+                o = o0 + diag + i
+                assert lo_ok <= o < hi_ok
+                new[o] = bk if tb else ak
+                nx = (b if tb else a) + 1
+                nk = rd(nx)
+                if tb:
+                    b, bk = nx, nk
+                else:
+                    a, ak = nx, nk
+            if t - first == coop - 1:
+                assert lo_ok <= o0 + 2 * run < hi_ok
+                new[o0 + 2 * run] = umax
+        bufs[dst] = new
+        src, dst = dst, src
+        coop <<= 1
+    return bufs[src][:NT * IPT]
+
+
+@pytest.mark.parametrize("NT,IPT", [(64, 3), (128, 5), (256, 3)])
+def test_block_sort_pp_model(NT, IPT):
+    """The ping-pong block sort's layout: sorted tiles with and without keys
+    equal to the end mark (the bounded rounds), every access in bounds and in
+    the accessing warp's stretch while warps synchronise alone."""
+    rng = random.Random(NT + IPT)
+    umax = 2 ** 32 - 1
+    for trial in range(6):
+        n = NT * IPT
+        if trial % 3 == 0:
+            keys = [rng.randrange(2 ** 32 - 1) for _ in range(n)]
+        elif trial % 3 == 1:
+            keys = [rng.randrange(7) for _ in range(n)]
+        else:
+            keys = [rng.choice([0, umax, rng.randrange(100)]) for _ in range(n)]
+        assert _block_sort_pp(keys, NT, IPT, umax) == sorted(keys)
