@@ -10,6 +10,12 @@
 #ifndef SR_SPLIT_SAMPLES
 #define SR_SPLIT_SAMPLES 1  // merge splits searched over recorded tile samples first
 #endif
+#ifndef SR_MERGE_CHAINS
+#define SR_MERGE_CHAINS 1   // 2: end-marked merge tiles run two merge chains per thread
+#endif
+#ifndef SR_MERGE_RAW_I32
+#define SR_MERGE_RAW_I32 0  // 1: bulk-staged int32 merge tiles compare raw keys as signed (no image pass)
+#endif
 #ifndef SR_MERGE_1LD
 #define SR_MERGE_1LD 1      // global merge tiles: one unguarded shared load per merge step (padded buffer)
 #endif
@@ -1021,11 +1027,16 @@ template <int KT, int NT, int IPT, bool VALS, bool VEC>
 __device__ __forceinline__ void write_tile(const typename Key<KT>::U (&k)[IPT], const uint32_t (&v)[IPT],
                                            typename Key<KT>::U *s, uint32_t *sv,
                                            typename Key<KT>::T *__restrict__ dst_k, uint32_t *__restrict__ dst_v,
-                                           long long out0, int cnt, typename Key<KT>::U *samp, long long tile) {
+                                           long long out0, int cnt, typename Key<KT>::U *samp, long long tile,
+                                           bool raw = false) {
     typedef Key<KT> K;
     typedef typename K::U U;
     typedef typename K::T T;
     const int t = threadIdx.x;
+    // raw: the keys are the caller's own bit patterns (int32 compared as
+    // signed), not order images; they leave unchanged and the samples get
+    // their images
+    auto out = [raw](U x) -> T { return raw ? (T)x : K::unord(x); };
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
@@ -1034,14 +1045,14 @@ __device__ __forceinline__ void write_tile(const typename Key<KT>::U (&k)[IPT], 
     }
     __syncthreads();
     if (samp && t == 0) {                          // the output tile's first and last key, for the next pass
-        samp[2 * tile] = s[0];
-        samp[2 * tile + 1] = s[cnt - 1];
+        samp[2 * tile] = raw ? K::ord((T)s[0]) : s[0];
+        samp[2 * tile + 1] = raw ? K::ord((T)s[cnt - 1]) : s[cnt - 1];
     }
     if (VEC) {
         // keys before the first 4-key group boundary of the output go one by one
         const int head = min(cnt, (int)((4 - (out0 & 3)) & 3));
         if (t < head) {
-            dst_k[out0 + t] = K::unord(s[t]);
+            dst_k[out0 + t] = out(s[t]);
             if (VALS) dst_v[out0 + t] = sv[t];
         }
         const int full = (cnt - head) >> 2;
@@ -1052,15 +1063,15 @@ __device__ __forceinline__ void write_tile(const typename Key<KT>::U (&k)[IPT], 
                 if (sizeof(T) == 4) {
                     const uint4 q = *reinterpret_cast<const uint4 *>(s + j);
                     *reinterpret_cast<uint4 *>(dst_k + out0 + j) =
-                        make_uint4((uint32_t)K::unord((U)q.x), (uint32_t)K::unord((U)q.y),
-                                   (uint32_t)K::unord((U)q.z), (uint32_t)K::unord((U)q.w));
+                        make_uint4((uint32_t)out((U)q.x), (uint32_t)out((U)q.y),
+                                   (uint32_t)out((U)q.z), (uint32_t)out((U)q.w));
                 } else {
                     const ulonglong2 q0 = *reinterpret_cast<const ulonglong2 *>(s + j);
                     const ulonglong2 q1 = *reinterpret_cast<const ulonglong2 *>(s + j + 2);
-                    const unsigned long long e0 = (unsigned long long)K::unord((U)q0.x);
-                    const unsigned long long e1 = (unsigned long long)K::unord((U)q0.y);
-                    const unsigned long long e2 = (unsigned long long)K::unord((U)q1.x);
-                    const unsigned long long e3 = (unsigned long long)K::unord((U)q1.y);
+                    const unsigned long long e0 = (unsigned long long)out((U)q0.x);
+                    const unsigned long long e1 = (unsigned long long)out((U)q0.y);
+                    const unsigned long long e2 = (unsigned long long)out((U)q1.x);
+                    const unsigned long long e3 = (unsigned long long)out((U)q1.y);
                     *reinterpret_cast<uint4 *>(dst_k + out0 + j) =
                         make_uint4((uint32_t)e0, (uint32_t)(e0 >> 32), (uint32_t)e1, (uint32_t)(e1 >> 32));
                     *reinterpret_cast<uint4 *>(dst_k + out0 + j + 2) =
@@ -1072,16 +1083,16 @@ __device__ __forceinline__ void write_tile(const typename Key<KT>::U (&k)[IPT], 
             const int j = head + 4 * g;
             if (sizeof(T) == 4) {
                 uint4 q;
-                q.x = (uint32_t)K::unord(s[j + 0]);
-                q.y = (uint32_t)K::unord(s[j + 1]);
-                q.z = (uint32_t)K::unord(s[j + 2]);
-                q.w = (uint32_t)K::unord(s[j + 3]);
+                q.x = (uint32_t)out(s[j + 0]);
+                q.y = (uint32_t)out(s[j + 1]);
+                q.z = (uint32_t)out(s[j + 2]);
+                q.w = (uint32_t)out(s[j + 3]);
                 *reinterpret_cast<uint4 *>(dst_k + out0 + j) = q;
             } else {
-                const unsigned long long e0 = (unsigned long long)K::unord(s[j + 0]);
-                const unsigned long long e1 = (unsigned long long)K::unord(s[j + 1]);
-                const unsigned long long e2 = (unsigned long long)K::unord(s[j + 2]);
-                const unsigned long long e3 = (unsigned long long)K::unord(s[j + 3]);
+                const unsigned long long e0 = (unsigned long long)out(s[j + 0]);
+                const unsigned long long e1 = (unsigned long long)out(s[j + 1]);
+                const unsigned long long e2 = (unsigned long long)out(s[j + 2]);
+                const unsigned long long e3 = (unsigned long long)out(s[j + 3]);
                 *reinterpret_cast<uint4 *>(dst_k + out0 + j) =
                     make_uint4((uint32_t)e0, (uint32_t)(e0 >> 32), (uint32_t)e1, (uint32_t)(e1 >> 32));
                 *reinterpret_cast<uint4 *>(dst_k + out0 + j + 2) =
@@ -1091,14 +1102,43 @@ __device__ __forceinline__ void write_tile(const typename Key<KT>::U (&k)[IPT], 
                 *reinterpret_cast<uint4 *>(dst_v + out0 + j) = make_uint4(sv[j], sv[j + 1], sv[j + 2], sv[j + 3]);
         }
         for (int i = head + 4 * full + t; i < cnt; i += NT) {
-            dst_k[out0 + i] = K::unord(s[i]);
+            dst_k[out0 + i] = out(s[i]);
             if (VALS) dst_v[out0 + i] = sv[i];
         }
     } else {
         for (int i = t; i < cnt; i += NT) {
-            dst_k[out0 + i] = K::unord(s[i]);
+            dst_k[out0 + i] = out(s[i]);
             if (VALS) dst_v[out0 + i] = sv[i];
         }
+    }
+}
+
+// The merge of one tile's staged windows A = s[sa, sa + acnt) and B = s[sb,
+// sb + bcnt): thread outputs diag .. diag + IPT into k (with their staged
+// positions in ix).  `marks`: the key after each window is `mark`, so when
+// neither window holds it the steps compare once (serial_merge_marked).  C is
+// the type the keys compare in (the order images, or int32 for raw int32 keys).
+template <typename C, int IPT>
+__device__ __forceinline__ void tile_merge(const C *s, int sa, int acnt, int sb, int bcnt, int cnt, int diag,
+                                           bool marks, C mark, C (&k)[IPT], int (&ix)[IPT]) {
+    const int sp = merge_path(s + sa, acnt, s + sb, bcnt, diag);
+    const bool marked = marks && (acnt == 0 || s[sa + acnt - 1] != mark) && (bcnt == 0 || s[sb + bcnt - 1] != mark);
+    if (marked && SR_MERGE_CHAINS == 2) {
+        constexpr int H = (IPT + 1) / 2;           // the second chain's split: within H outputs of the first's
+        const int d2 = min(diag + H, cnt);
+        int lo = max(sp, d2 - bcnt), hi = min(sp + (d2 - diag), acnt);
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (!(s[sb + d2 - 1 - mid] < s[sa + mid])) lo = mid + 1;
+            else hi = mid;
+        }
+        serial_merge_marked2<C, IPT, H>(s, sa + sp, sb + diag - sp, sa + lo, sb + d2 - lo, k, ix);
+    } else if (marked) {
+        serial_merge_marked<C, IPT>(s, sa + sp, sb + diag - sp, k, ix);
+    } else if (SR_MERGE_1LD) {
+        serial_merge_slack<C, IPT>(s, sa + sp, sa + acnt, sb + diag - sp, sb + bcnt, k, ix);
+    } else {
+        serial_merge<C, IPT>(s, sa + sp, sa + acnt, sb + diag - sp, sb + bcnt, k, ix);
     }
 }
 
@@ -1153,6 +1193,10 @@ __device__ __forceinline__ void merge_tile(const typename Key<KT>::T *__restrict
     const int t = threadIdx.x;
     const int acnt = (int)(a1 - a0);
     const int bcnt = cnt - acnt;
+    // bulk-staged int32 keys may stay raw and compare as signed int32 (no image pass)
+    constexpr bool RAW_OK = KT == SR_KEY_I32 && SR_MERGE_RAW_I32;
+    const bool raw = RAW_OK && VEC && bar;
+    const U mark = raw ? (U)INT_MAX : umax_of<U>();
     int sa, sb;                                    // staged positions of A[a0] and B[b0]
     if (VEC && bar) {
         const long long g0[2] = {a0 & ~3ll, b0 & ~3ll};
@@ -1201,7 +1245,7 @@ __device__ __forceinline__ void merge_tile(const typename Key<KT>::T *__restrict
             mbar_wait_bounded(bar, 0, BULK_WAIT_TRIES);   // copies still in flight must land first
             return;
         }
-        if (KT != SR_KEY_U32 && KT != SR_KEY_U64) {       // raw keys -> order images, in place
+        if (KT != SR_KEY_U32 && KT != SR_KEY_U64 && !raw) {   // raw keys -> order images, in place
             for (int g = t; g < nag + 1 + nbg; g += NT) {
                 if (sizeof(U) == 4) {
                     uint4 q = *reinterpret_cast<uint4 *>(s + 4 * g);
@@ -1216,8 +1260,8 @@ __device__ __forceinline__ void merge_tile(const typename Key<KT>::T *__restrict
             __syncthreads();
         }
         if (t == 0) {                              // the windows' end marks
-            s[sa + acnt] = umax_of<U>();
-            s[sb + bcnt] = umax_of<U>();
+            s[sa + acnt] = mark;
+            s[sb + bcnt] = mark;
         }
     } else if (VEC) {
         const long long a0g = a0 & ~3ll, b0g = b0 & ~3ll;
@@ -1289,23 +1333,27 @@ __device__ __forceinline__ void merge_tile(const typename Key<KT>::T *__restrict
     }
     __syncthreads();
     const int diag = min(t * IPT, cnt);
-    const int sp = merge_path(s + sa, acnt, s + sb, bcnt, diag);
     U k[IPT];
     int ix[IPT];
-    const bool marked = VEC && bar && (acnt == 0 || s[sa + acnt - 1] != umax_of<U>()) &&
-                        (bcnt == 0 || s[sb + bcnt - 1] != umax_of<U>());
-    if (marked)
-        serial_merge_marked<U, IPT>(s, sa + sp, sb + diag - sp, k, ix);
-    else if (SR_MERGE_1LD)
-        serial_merge_slack<U, IPT>(s, sa + sp, sa + acnt, sb + diag - sp, sb + bcnt, k, ix);
-    else
-        serial_merge<U, IPT>(s, sa + sp, sa + acnt, sb + diag - sp, sb + bcnt, k, ix);
+    if constexpr (RAW_OK) {
+        if (raw) {
+            int ki[IPT];
+            tile_merge<int, IPT>(reinterpret_cast<const int *>(s), sa, acnt, sb, bcnt, cnt, diag, true, INT_MAX, ki,
+                                 ix);
+#pragma unroll
+            for (int i = 0; i < IPT; ++i) k[i] = (U)ki[i];
+        } else {
+            tile_merge<U, IPT>(s, sa, acnt, sb, bcnt, cnt, diag, VEC && bar, mark, k, ix);
+        }
+    } else {
+        tile_merge<U, IPT>(s, sa, acnt, sb, bcnt, cnt, diag, VEC && bar, mark, k, ix);
+    }
     uint32_t v[IPT];
     if (VALS) {
 #pragma unroll
         for (int i = 0; i < IPT; ++i) v[i] = (diag + i < cnt) ? sv[ix[i]] : 0u;
     }
-    write_tile<KT, NT, IPT, VALS, VEC>(k, v, s, sv, dst_k, dst_v, out0, cnt, samp, tile);
+    write_tile<KT, NT, IPT, VALS, VEC>(k, v, s, sv, dst_k, dst_v, out0, cnt, samp, tile, raw);
 }
 
 // One CTA per output tile of NT*IPT keys of a 2-way merge step.  The tile's
