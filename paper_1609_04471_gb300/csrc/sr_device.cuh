@@ -246,37 +246,6 @@ __device__ __forceinline__ void serial_merge_marked(const U *s, int a, int b, U 
     }
 }
 
-// serial_merge_marked as two independent chains: outputs [0, H) from (a, b),
-// outputs [H, IPT) from (a2, b2), the merge-path split H outputs further on;
-// the chains' loads can overlap.
-template <typename U, int IPT, int H>
-__device__ __forceinline__ void serial_merge_marked2(const U *s, int a, int b, int a2, int b2, U (&k)[IPT],
-                                                     int (&ix)[IPT]) {
-    U ak = s[a], bk = s[b];
-    U ak2 = s[a2], bk2 = s[b2];
-#pragma unroll
-    for (int i = 0; i < H; ++i) {
-        {
-            const bool take_a = !(bk < ak);
-            k[i] = take_a ? ak : bk;
-            ix[i] = take_a ? a : b;
-            const int nx = (take_a ? a : b) + 1;
-            const U nk = s[nx];
-            if (take_a) { a = nx; ak = nk; }
-            else        { b = nx; bk = nk; }
-        }
-        if (H + i < IPT) {
-            const bool take_a = !(bk2 < ak2);
-            k[H + i] = take_a ? ak2 : bk2;
-            ix[H + i] = take_a ? a2 : b2;
-            const int nx = (take_a ? a2 : b2) + 1;
-            const U nk = s[nx];
-            if (take_a) { a2 = nx; ak2 = nk; }
-            else        { b2 = nx; bk2 = nk; }
-        }
-    }
-}
-
 template <typename U, int IPT>
 __device__ __forceinline__ void serial_merge(const U *s, int a, int a_end, int b, int b_end,
                                              U (&k)[IPT], int (&ix)[IPT]) {
