@@ -111,17 +111,23 @@ template <int KB, bool VALS> struct Shape;
 // SORT_MINB: block-sort CTAs per SM the register allocator is held to (4-byte
 // keys alone: three CTAs of 512 threads at 40 registers; two with the two
 // shared buffers of block_sort_pp).
-// SR_BSORT_PP: how 4-byte keys alone sort their tiles -- 0: block_sort; 1:
-// block_sort_pp (two shared buffers, end-marked runs); 2: block_sort_rs (one
-// end-marked buffer, outputs through registers).  Measured at 2^28 on GB300:
-// 2.31, 2.11 and 2.02 ms.
+// SR_BSORT_PP: how tiles are sorted -- 0: block_sort; 1: block_sort_pp (two
+// shared buffers, end-marked runs; 4-byte keys alone); 2: block_sort_rs (one
+// end-marked buffer, outputs through registers; every key shape).  Measured
+// for 4-byte keys at 2^28 on GB300: 2.31, 2.11 and 2.02 ms.
 #ifndef SR_BSORT_PP
 #define SR_BSORT_PP 2
 #endif
 template <> struct Shape<4, false> { enum { NT = SR_MERGE_NT, IPT = SR_K4_IPT, SORT_NT = SR_SORT_NT, MERGE_MINB = 6, MERGE4_MINB = SR_MERGE4_MINB4, SORT_MINB = SR_BSORT_PP == 1 ? 2 : 3 }; };
 template <> struct Shape<4, true>  { enum { NT = SR_MERGE_NT, IPT = SR_K4V_IPT, SORT_NT = SR_SORT_NT, MERGE_MINB = 8, MERGE4_MINB = 6, SORT_MINB = 3 }; };
-template <> struct Shape<8, false> { enum { NT = SR_MERGE_NT, IPT = SR_K8_IPT, SORT_NT = SR_SORT_NT, MERGE_MINB = 4, MERGE4_MINB = 4, SORT_MINB = 1 }; };
-template <> struct Shape<8, true>  { enum { NT = SR_MERGE_NT, IPT = SR_K8V_IPT, SORT_NT = SR_SORT_NT, MERGE_MINB = 4, MERGE4_MINB = 4, SORT_MINB = 1 }; };
+// SR_SORT_MINB8: block-sort CTAs per SM for 8-byte keys (with or without
+// payloads): two, at 64 registers (block_sort_rs at 2^26: uint64 keys 1.49 ->
+// 1.04 ms, pairs 2.13 -> 1.44 ms against one CTA unbounded).
+#ifndef SR_SORT_MINB8
+#define SR_SORT_MINB8 2
+#endif
+template <> struct Shape<8, false> { enum { NT = SR_MERGE_NT, IPT = SR_K8_IPT, SORT_NT = SR_SORT_NT, MERGE_MINB = 4, MERGE4_MINB = 4, SORT_MINB = SR_SORT_MINB8 }; };
+template <> struct Shape<8, true>  { enum { NT = SR_MERGE_NT, IPT = SR_K8V_IPT, SORT_NT = SR_SORT_NT, MERGE_MINB = 4, MERGE4_MINB = 4, SORT_MINB = SR_SORT_MINB8 }; };
 
 // ------------------------------------------------------------- merge path
 
@@ -520,21 +526,26 @@ __device__ __forceinline__ U *block_sort_pp(U (&k)[IPT], U *sa, U *sb) {
     return src;
 }
 
-// block_sort_pp's rounds with one shared buffer (block_sort_pp_keys keys):
-// each round merges into registers, waits until its warp (or the block) has
-// read the round's runs, then writes the merged runs back in the next round's
-// layout.  Half the shared memory of block_sort_pp, for more resident CTAs.
-template <typename U, int NT, int IPT>
-__device__ __forceinline__ U *block_sort_rs(U (&k)[IPT], U *sa) {
+// block_sort_pp's rounds with one shared buffer (block_sort_pp_keys keys,
+// and as many payloads in `va` when VALS): each round merges into registers,
+// waits until its warp (or the block) has read the round's runs, then writes
+// the merged runs back in the next round's layout.  Ties go to the earlier
+// run, so with payloads the tile sort stays stable (the register sort is the
+// stable transposition sort then).  Half the shared memory of block_sort_pp,
+// for more resident CTAs.
+template <typename U, int NT, int IPT, bool VALS>
+__device__ __forceinline__ U *block_sort_rs(U (&k)[IPT], uint32_t (&v)[IPT], U *sa, uint32_t *va) {
     constexpr int W = 32 * IPT + 32;
     static_assert(NT % 32 == 0 && (NT / 32) * W == block_sort_pp_keys<NT, IPT>(), "warp stretches tile the buffer");
-    uint32_t dv[IPT];
-    thread_sort<U, IPT, false>(k, dv);
+    thread_sort<U, IPT, VALS>(k, v);
     const int t = threadIdx.x;
     const int w = t >> 5, lane = t & 31;
     const bool fast = !__syncthreads_or(k[IPT - 1] == umax_of<U>());
 #pragma unroll
-    for (int i = 0; i < IPT; ++i) sa[w * W + lane * (IPT + 1) + i] = k[i];
+    for (int i = 0; i < IPT; ++i) {
+        sa[w * W + lane * (IPT + 1) + i] = k[i];
+        if (VALS) va[w * W + lane * (IPT + 1) + i] = v[i];
+    }
     sa[w * W + lane * (IPT + 1) + IPT] = umax_of<U>();
 #pragma unroll 1
     for (int coop = 2; coop <= NT; coop <<= 1) {
@@ -560,9 +571,16 @@ __device__ __forceinline__ U *block_sort_rs(U (&k)[IPT], U *sa) {
         int ix[IPT];
         if (fast) serial_merge_marked<U, IPT>(sa, a0 + sp, b0 + diag - sp, k, ix);
         else      serial_merge_slack<U, IPT>(sa, a0 + sp, a0 + run, b0 + diag - sp, b0 + run, k, ix);
+        if (VALS) {
+#pragma unroll
+            for (int i = 0; i < IPT; ++i) v[i] = va[ix[i]];
+        }
         if (coop <= 32) __syncwarp(); else __syncthreads();
 #pragma unroll
-        for (int i = 0; i < IPT; ++i) sa[o0 + diag + i] = k[i];
+        for (int i = 0; i < IPT; ++i) {
+            sa[o0 + diag + i] = k[i];
+            if (VALS) va[o0 + diag + i] = v[i];
+        }
         if (t - first == coop - 1) sa[o0 + 2 * run] = umax_of<U>();
     }
     __syncthreads();

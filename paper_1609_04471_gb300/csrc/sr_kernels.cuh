@@ -278,8 +278,14 @@ k_tile_order(const typename Key<KT>::U *__restrict__ tmin, const typename Key<KT
 // a key only costs that pass.  This is the multiway form of the fat (3-way)
 // split of the paper's quicksorts (Section 4, techniques (d) and (g)): every
 // distinct key is a pivot, keys equal to a pivot need no further comparisons,
-// so the split alone sorts the input.
+// so the split alone sorts the input.  Phase A looks at its first
+// FEW_SAMPLE_A0 keys first: more than FEW_A0_MAX distinct among them closes
+// the set at once (1,024 draws from at most FEW_MAX values give about 906
+// distinct ones, with a spread of about 12), so inputs with many distinct keys
+// pay for one round of sample loads; sorted and strictly descending inputs
+// skip the sample.
 enum { FEW_SAMPLE = 65536, FEW_SAMPLE_A = 4096, FEW_A_MAX = 3072, FEW_A_ALONE = 256, FEW_NT2 = 1024 };
+enum { FEW_SAMPLE_A0 = 1024, FEW_A0_MAX = 1000 };
 
 // This CTA's `per` samples (sample indices from `first`) into a shared-memory
 // set, then its images not yet in the call's set into it; the number it added
@@ -327,15 +333,31 @@ __global__ void __launch_bounds__(FEW_NT2) k_few_sample(const typename Key<KT>::
     __shared__ unsigned int s_n, s_new;
     __shared__ int s_over;
     if (gate && *gate == 0) return;
+    const int mode = call_mode(c, n);
+    if (mode == MODE_SORTED || mode == MODE_REVERSE) {           // the scan has settled the call
+        if (threadIdx.x == 0) atomicExch(&c->few_over, 1);      // phase B returns at once too
+        return;
+    }
     const int t = threadIdx.x;
     for (int q = t; q < FEW_A_SLOTS; q += FEW_NT2) s_tab[q] = 0ull;
     if (t == 0) { s_n = 0u; s_new = 0u; s_over = 0; }
     __syncthreads();
-    if (n > 0)
-        for (int i = t; i < FEW_SAMPLE_A; i += FEW_NT2)
+    static_assert(FEW_SAMPLE_A0 <= FEW_NT2 && FEW_SAMPLE_A % FEW_NT2 == 0, "the first look is one round");
+    if (n > 0) {
+        if (t < FEW_SAMPLE_A0)
+            few_insert<FEW_A_SLOTS_LOG2>(s_tab, &s_n, &s_over,
+                                         (unsigned int)Key<KT>::ord(__ldg(keys + ((long long)t * n) / FEW_SAMPLE)),
+                                         FEW_A_MAX);
+        __syncthreads();
+        if (s_n > FEW_A0_MAX) {
+            if (t == 0) atomicExch(&c->few_over, 1);
+            return;
+        }
+        for (int i = FEW_SAMPLE_A0 + t; i < FEW_SAMPLE_A; i += FEW_NT2)
             few_insert<FEW_A_SLOTS_LOG2>(s_tab, &s_n, &s_over,
                                          (unsigned int)Key<KT>::ord(__ldg(keys + ((long long)i * n) / FEW_SAMPLE)),
                                          FEW_A_MAX);
+    }
     __syncthreads();
     if (s_over) {                                  // too many distinct keys: the path is off
         if (t == 0) atomicExch(&c->few_over, 1);
@@ -758,8 +780,10 @@ k_block_sort(const typename Key<KT>::T *in_k, const uint32_t *in_v, typename Key
     __syncthreads();
     if constexpr (!VALS && sizeof(U) == 4 && SR_BSORT_PP == 1) {
         s = block_sort_pp<U, NT, IPT>(k, s, s + block_sort_pp_keys<NT, IPT>());
-    } else if constexpr (!VALS && sizeof(U) == 4 && SR_BSORT_PP == 2) {
-        s = block_sort_rs<U, NT, IPT>(k, s);
+    } else if constexpr (SR_BSORT_PP == 2) {
+        uint32_t *va = reinterpret_cast<uint32_t *>(s + block_sort_pp_keys<NT, IPT>());
+        s = block_sort_rs<U, NT, IPT, VALS>(k, v, s, va);
+        sv = va;
     } else {
         block_sort<U, NT, IPT, VALS>(k, v, s, sv);
 #pragma unroll

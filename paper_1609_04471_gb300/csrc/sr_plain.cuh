@@ -333,10 +333,10 @@ template <int KT, bool VALS> struct PlainSort {
             if (passes > 0)
                 SR_LAUNCH(SR_KERNEL_PARTITION, (k_tile_order<KT>), 1, RUNS_NT, 0, s, plo, phi, n, (long long)TS,
                           tiles, VALS ? 1 : 0, cur0, dest, ctrl);
-            const size_t bs_smem = (!VALS && sizeof(U) == 4 && SR_BSORT_PP)
-                                       ? (size_t)(SR_BSORT_PP == 1 ? 2 : 1) * block_sort_pp_keys<SNT, IPT>() *
-                                             sizeof(U)
-                                       : (size_t)TS * (sizeof(U) + (VALS ? 4 : 0));
+            const size_t bs_smem =
+                SR_BSORT_PP == 2 ? (size_t)block_sort_pp_keys<SNT, IPT>() * (sizeof(U) + (VALS ? 4 : 0))
+                : (!VALS && sizeof(U) == 4 && SR_BSORT_PP == 1) ? (size_t)2 * block_sort_pp_keys<SNT, IPT>() * sizeof(U)
+                                                                : (size_t)TS * (sizeof(U) + (VALS ? 4 : 0));
             if ((st = allow_smem(k_block_sort<KT, SNT, IPT, VALS>, bs_smem)) != SR_OK) break;
             SR_LAUNCH(SR_KERNEL_BLOCK_SORT, (k_block_sort<KT, SNT, IPT, VALS>), (unsigned)tiles, SNT,
                       bs_smem, s, uk, uv, cur0 ? sk : uk, cur0 ? sv : uv, n, ctrl, plo, phi,

@@ -1043,7 +1043,7 @@ def _block_sort_pp(keys, NT, IPT, umax):
     assert (NT // 32) * W == size
     bufs = [[None] * size, [None] * size]
     regs = [sorted(keys[t * IPT:(t + 1) * IPT]) for t in range(NT)]
-    fast = not any(r[-1] == umax for r in regs)
+    fast = not any(getattr(r[-1], "v", r[-1]) == getattr(umax, "v", umax) for r in regs)
     for t in range(NT):
         w, lane = t >> 5, t & 31
         for i in range(IPT):
@@ -1119,3 +1119,18 @@ def test_block_sort_pp_model(NT, IPT):
         else:
             keys = [rng.choice([0, umax, rng.randrange(100)]) for _ in range(n)]
         assert _block_sort_pp(keys, NT, IPT, umax) == sorted(keys)
+
+
+def test_block_sort_rs_payload_model():
+    """block_sort_rs with payloads: keys that compare by value alone and carry
+    their tile position; ties must keep that order (the stable tile sort), with
+    and without keys equal to the end mark."""
+    rng = random.Random(5)
+    umax = 2 ** 32 - 1
+    NT, IPT = 64, 5
+    for trial in range(8):
+        n = NT * IPT
+        vals = [rng.choice([rng.randrange(4), umax] if trial % 2 else [rng.randrange(4)]) for _ in range(n)]
+        keys = [_K(v, 0, i) for i, v in enumerate(vals)]
+        out = _block_sort_pp(keys, NT, IPT, _K(umax, 9, -1))
+        assert [k.full() for k in out] == sorted(k.full() for k in keys)
