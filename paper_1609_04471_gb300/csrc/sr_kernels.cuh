@@ -101,7 +101,34 @@ __global__ void __launch_bounds__(NT) k_detect(const typename Key<KT>::T *__rest
     unsigned int d = 0, nd = 0, din = 0, ndin = 0;
     U kmin = umax_of<U>(), kmax = U(0);
     const int ng = (cnt + VW - 1) / VW;
-    for (int g = t; g < ng; g += NT) {
+    // vectors whose VW pairs and next key all lie inside the tile: no bounds
+    // tests; their non-descents are counted as pairs minus descents afterwards
+    const int nfast = vec ? (cnt - 1) / VW : 0;    // vectors g with g*VW + VW < cnt
+    unsigned int dfast = 0, pfast = 0;
+    for (int g = t; g < nfast; g += NT) {
+        const int j0 = g * VW;
+        U x[VW + 1];
+        if constexpr (VW == 4) {
+            const uint4 q = __ldg(reinterpret_cast<const uint4 *>(keys + base + j0));
+            x[0] = K::ord((T)q.x); x[1] = K::ord((T)q.y); x[2] = K::ord((T)q.z); x[3] = K::ord((T)q.w);
+        } else {
+            const ulonglong2 q = __ldg(reinterpret_cast<const ulonglong2 *>(keys + base + j0));
+            x[0] = K::ord((T)q.x); x[1] = K::ord((T)q.y);
+        }
+        x[VW] = K::ord(__ldg(keys + base + j0 + VW));
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+            dfast += x[e] > x[e + 1];
+            kmin = x[e] < kmin ? x[e] : kmin;
+            kmax = x[e] > kmax ? x[e] : kmax;
+        }
+        pfast += VW;
+    }
+    d += dfast;
+    nd += pfast - dfast;
+    din |= dfast != 0;
+    ndin |= pfast != dfast;
+    for (int g = nfast + t; g < ng; g += NT) {
         const int j0 = g * VW;                     // tile index of the vector's first key
         U x[VW + 1];
         if (vec && j0 + VW <= cnt) {
