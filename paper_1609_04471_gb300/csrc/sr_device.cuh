@@ -82,9 +82,11 @@ template <int KB, bool VALS> struct Shape;
 // 1024-thread block sort saves one global pass but its extra shared-memory
 // level costs more than that pass on GB300: 2.87 ms against 0.57 ms at 2^28.)
 // Defaults measured on GB300 (plain int32 sort, 2^24 and 2^28 keys); each
-// can be overridden at build time.
+// can be overridden at build time.  4-byte keys alone take 33 keys per thread:
+// 16,896-key block-sort tiles need one merge step fewer than 12,800-key ones
+// at 2^24 and at 2^28 (2^28: 7.68 -> 7.15 ms; 2^24: 0.539 -> 0.507 ms).
 #ifndef SR_K4_IPT
-#define SR_K4_IPT 25
+#define SR_K4_IPT 33
 #endif
 #ifndef SR_K4V_IPT
 #define SR_K4V_IPT 11
@@ -102,15 +104,15 @@ template <int KB, bool VALS> struct Shape;
 #define SR_MERGE_NT 256
 #endif
 // MERGE_MINB: resident merge CTAs per SM the register allocator is held to
-// (4-byte keys: 40 registers, six CTAs -- measured 9.14 -> 9.00 ms at 2^28;
-// the others keep the occupancy they reach unconstrained).
+// (4-byte keys: 40 registers, six CTAs; the others keep the occupancy they
+// reach unconstrained).
 // MERGE4_MINB: the same for the 4-way merge kernel.
 #ifndef SR_MERGE4_MINB4
 #define SR_MERGE4_MINB4 5
 #endif
 // SORT_MINB: block-sort CTAs per SM the register allocator is held to (4-byte
-// keys alone: three CTAs of 512 threads at 40 registers; two with the two
-// shared buffers of block_sort_pp).
+// keys alone: two CTAs of 512 threads, 64 registers, with 33 keys a thread;
+// three at 40 registers spilled).
 // SR_BSORT_PP: how tiles are sorted -- 0: block_sort; 1: block_sort_pp (two
 // shared buffers, end-marked runs; 4-byte keys alone); 2: block_sort_rs (one
 // end-marked buffer, outputs through registers; every key shape).  Measured
@@ -118,7 +120,13 @@ template <int KB, bool VALS> struct Shape;
 #ifndef SR_BSORT_PP
 #define SR_BSORT_PP 2
 #endif
-template <> struct Shape<4, false> { enum { NT = SR_MERGE_NT, IPT = SR_K4_IPT, SORT_NT = SR_SORT_NT, MERGE_MINB = 6, MERGE4_MINB = SR_MERGE4_MINB4, SORT_MINB = SR_BSORT_PP == 1 ? 2 : 3 }; };
+#ifndef SR_MERGE_MINB4
+#define SR_MERGE_MINB4 6
+#endif
+#ifndef SR_SORT_MINB4
+#define SR_SORT_MINB4 2
+#endif
+template <> struct Shape<4, false> { enum { NT = SR_MERGE_NT, IPT = SR_K4_IPT, SORT_NT = SR_SORT_NT, MERGE_MINB = SR_MERGE_MINB4, MERGE4_MINB = SR_MERGE4_MINB4, SORT_MINB = SR_SORT_MINB4 }; };
 template <> struct Shape<4, true>  { enum { NT = SR_MERGE_NT, IPT = SR_K4V_IPT, SORT_NT = SR_SORT_NT, MERGE_MINB = 8, MERGE4_MINB = 6, SORT_MINB = 3 }; };
 // SR_SORT_MINB8: block-sort CTAs per SM for 8-byte keys (with or without
 // payloads): two, at 64 registers (block_sort_rs at 2^26: uint64 keys 1.49 ->
@@ -341,8 +349,8 @@ __host__ __device__ constexpr int merge_step_count(int levels, bool fan4) {
 }
 
 // Sort of a thread's IPT registers.  Keys alone: Batcher's odd-even merge
-// sort network cut to IPT inputs, its pairs generated at compile time (140
-// compare-exchanges for 25 keys against 300 for transposition; equal keys are
+// sort network cut to IPT inputs, its pairs generated at compile time (246
+// compare-exchanges for 33 keys against 528 for transposition; equal keys are
 // indistinguishable, so stability does not arise).  Keys with values: odd-even
 // transposition, which is stable (only neighbours swap, and only on a strict
 // descent).

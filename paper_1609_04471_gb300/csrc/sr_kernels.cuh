@@ -208,16 +208,17 @@ __global__ void __launch_bounds__(NT) k_detect(const typename Key<KT>::T *__rest
 // only when that lowers the count of natural runs (two tiles at the seam of
 // two ascending runs also form a chain, and turning them would cut both runs).
 // One CTA, from the scan's per-tile extremes: dest[t] = the tile position the
-// block sort writes tile t to (dest[t] = t outside turned chains).  Only when the block sort writes to
-// the other buffer (cur0 = 1): in place, a tile written elsewhere could
-// overwrite one not yet read.  Sets c->tile_perm when some chain exists.
+// block sort writes tile t to (dest[t] = t outside turned chains).  Sets
+// c->tile_perm when some chain is turned; the block sort then writes to the
+// scratch buffer whatever the step count (in place, a tile written elsewhere
+// could overwrite one not yet read), and the run planner starts the steps there.
 template <int KT>
 __global__ void __launch_bounds__(RUNS_NT)
 k_tile_order(const typename Key<KT>::U *__restrict__ tmin, const typename Key<KT>::U *__restrict__ tmax,
-             long long n, long long ts, long long tiles, int strict, int cur0, int *__restrict__ dest,
+             long long n, long long ts, long long tiles, int strict, int *__restrict__ dest,
              Ctrl *__restrict__ c) {
     griddep_wait();
-    if (call_mode(c, n) != MODE_SORT || !cur0) return;
+    if (call_mode(c, n) != MODE_SORT) return;
     __shared__ int s_carry;
     __shared__ int s_any;
     const int t = threadIdx.x;
@@ -701,15 +702,22 @@ __global__ void k_reverse(typename Key<KT>::T *__restrict__ k, uint32_t *__restr
 // largest key images in tile_lo / tile_hi (if given) for the pass planner.
 template <int KT, int NT, int IPT, bool VALS>
 __global__ void __launch_bounds__(NT, Shape<sizeof(typename Key<KT>::T), VALS>::SORT_MINB)
-k_block_sort(const typename Key<KT>::T *in_k, const uint32_t *in_v, typename Key<KT>::T *out_k,
-             uint32_t *out_v, long long n, const Ctrl *__restrict__ c,
+k_block_sort(const typename Key<KT>::T *in_k, const uint32_t *in_v, typename Key<KT>::T *out_k0,
+             uint32_t *out_v0, typename Key<KT>::T *alt_k, uint32_t *alt_v, long long n, const Ctrl *__restrict__ c,
              typename Key<KT>::U *__restrict__ tile_lo, typename Key<KT>::U *__restrict__ tile_hi,
-             typename Key<KT>::U *__restrict__ samp, int mv, const int *__restrict__ dest) {
+             typename Key<KT>::U *__restrict__ samp0, long long smt, int mv, const int *__restrict__ dest) {
     griddep_wait();
     typedef Key<KT> K;
     typedef typename K::U U;
     constexpr int NV = NT * IPT;
     if (c && call_mode(c, n) != MODE_SORT) return;
+    // the output buffer: out_k0 / out_v0, or the scratch pair alt_k / alt_v when
+    // the tile planner turned chains and out_k0 is the input itself; tile
+    // samples go with the buffer written (samp0 + smt for the scratch one)
+    const bool to_alt = c && c->tile_perm && (const void *)out_k0 == (const void *)in_k;
+    typename Key<KT>::T *out_k = to_alt ? alt_k : out_k0;
+    uint32_t *out_v = to_alt ? alt_v : out_v0;
+    U *samp = samp0 ? samp0 + ((const void *)out_k == (const void *)in_k ? 0 : smt) : nullptr;
     extern __shared__ __align__(16) unsigned char smem[];
     U *s = reinterpret_cast<U *>(smem);
     uint32_t *sv = reinterpret_cast<uint32_t *>(s + NV);
@@ -860,7 +868,7 @@ k_block_sort(const typename Key<KT>::T *in_k, const uint32_t *in_v, typename Key
 //
 // One CTA: rs0[q] = the first tile of natural run q (q < nruns), rs0[nruns] =
 // tiles; nsteps = ceil(log_f(nruns)); src_buf[s] = the buffer holding the data
-// before step s (the block sort's output buffer is cur0).  Steps s >= nsteps of
+// before step s (the block sort's output buffer: cur0, or 1 when it turned chains of tiles).  Steps s >= nsteps of
 // the launched sequence return at once.
 template <int KT>
 __global__ void __launch_bounds__(RUNS_NT)
@@ -904,7 +912,8 @@ k_runs(const typename Key<KT>::U *__restrict__ lo, const typename Key<KT>::U *__
         c->nruns = base;
         c->nsteps = steps;
         c->repair = (!far && steps > 0 && tiles >= 3) ? 1 : 0;
-        for (int s = 0; s <= steps; ++s) c->src_buf[s] = (signed char)(cur0 ^ (s & 1));
+        const int cur = cur0 | (c->tile_perm ? 1 : 0);   // turned chains: the block sort wrote to scratch
+        for (int s = 0; s <= steps; ++s) c->src_buf[s] = (signed char)(cur ^ (s & 1));
     }
 }
 

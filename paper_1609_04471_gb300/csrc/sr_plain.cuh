@@ -332,15 +332,15 @@ template <int KT, bool VALS> struct PlainSort {
             int *dest = win;                        // free until the repair planner runs
             if (passes > 0)
                 SR_LAUNCH(SR_KERNEL_PARTITION, (k_tile_order<KT>), 1, RUNS_NT, 0, s, plo, phi, n, (long long)TS,
-                          tiles, VALS ? 1 : 0, cur0, dest, ctrl);
+                          tiles, VALS ? 1 : 0, dest, ctrl);
             const size_t bs_smem =
                 SR_BSORT_PP == 2 ? (size_t)block_sort_pp_keys<SNT, IPT>() * (sizeof(U) + (VALS ? 4 : 0))
                 : (!VALS && sizeof(U) == 4 && SR_BSORT_PP == 1) ? (size_t)2 * block_sort_pp_keys<SNT, IPT>() * sizeof(U)
                                                                 : (size_t)TS * (sizeof(U) + (VALS ? 4 : 0));
             if ((st = allow_smem(k_block_sort<KT, SNT, IPT, VALS>, bs_smem)) != SR_OK) break;
             SR_LAUNCH(SR_KERNEL_BLOCK_SORT, (k_block_sort<KT, SNT, IPT, VALS>), (unsigned)tiles, SNT,
-                      bs_smem, s, uk, uv, cur0 ? sk : uk, cur0 ? sv : uv, n, ctrl, plo, phi,
-                      samp ? samp + cur0 * 2 * mtiles : nullptr, (int)NV, passes > 0 ? dest : nullptr);
+                      bs_smem, s, uk, uv, cur0 ? sk : uk, cur0 ? sv : uv, sk, sv, n, ctrl, plo, phi, samp,
+                      (long long)2 * mtiles, (int)NV, passes > 0 ? dest : nullptr);
             if (passes == 0) break;
             const int fan = fan4 ? 4 : 2;
             SR_LAUNCH(SR_KERNEL_PARTITION, (k_runs<KT>), 1, RUNS_NT, 0, s, plo, phi, n, tiles, fan, cur0, runs, ctrl);

@@ -38,6 +38,8 @@
 // decide how many keys land in buckets.
 #pragma once
 
+#include <type_traits>
+
 #include "sr_device.cuh"
 #include "sr_kernels.cuh"
 
@@ -153,6 +155,9 @@ __device__ __forceinline__ long long rem_dest(const U *__restrict__ bound, long 
 #ifndef SR_REM_SPLIT_MINB
 #define SR_REM_SPLIT_MINB 4     // 64 registers: four CTAs per SM
 #endif
+__device__ __forceinline__ unsigned int popc_mask(unsigned int m) { return __popc(m); }
+__device__ __forceinline__ unsigned int popc_mask(unsigned long long m) { return __popcll(m); }
+
 template <int KT, int NT, int IPT>
 __global__ void __launch_bounds__(NT, SR_REM_SPLIT_MINB)
 k_rem_split(const typename Key<KT>::T *__restrict__ keys, long long n, long long tiles, Ctrl *__restrict__ c,
@@ -164,7 +169,8 @@ k_rem_split(const typename Key<KT>::T *__restrict__ keys, long long n, long long
     typedef typename K::U U;
     constexpr int TS = NT * IPT;
     constexpr int NW = NT / 32;
-    static_assert(IPT <= 32, "one bit per key of a thread");
+    static_assert(IPT <= 64, "one bit per key of a thread");
+    typedef typename std::conditional<(IPT > 32), unsigned long long, unsigned int>::type Mask;
     if (!c->rem_active) return;
     extern __shared__ __align__(16) unsigned char smem[];
     U *s = reinterpret_cast<U *>(smem);
@@ -192,14 +198,14 @@ k_rem_split(const typename Key<KT>::T *__restrict__ keys, long long n, long long
     }
     __syncthreads();
     U k[IPT];
-    unsigned int keep = 0, valid = 0;
+    Mask keep = 0, valid = 0;
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
         const int j = t * IPT + i;
         k[i] = j < cnt ? s[j] : U(0);
         if (j < cnt) {
-            valid |= 1u << i;
-            if (k[i] >= lo && (top || k[i] < hi)) keep |= 1u << i;
+            valid |= Mask(1) << i;
+            if (k[i] >= lo && (top || k[i] < hi)) keep |= Mask(1) << i;
         }
     }
     // Are the candidates in order already (the usual case)?  Each must be at
@@ -208,7 +214,7 @@ k_rem_split(const typename Key<KT>::T *__restrict__ keys, long long n, long long
         U tmax = 0;
 #pragma unroll
         for (int i = 0; i < IPT; ++i)
-            if (((keep >> i) & 1u) && k[i] > tmax) tmax = k[i];
+            if (((keep >> i) & Mask(1)) && k[i] > tmax) tmax = k[i];
         U incl = tmax;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -223,7 +229,7 @@ k_rem_split(const typename Key<KT>::T *__restrict__ keys, long long n, long long
         int bad = 0;
 #pragma unroll
         for (int i = 0; i < IPT; ++i) {
-            if ((keep >> i) & 1u) {
+            if ((keep >> i) & Mask(1)) {
                 bad |= k[i] < run;
                 run = k[i] > run ? k[i] : run;
             }
@@ -236,7 +242,7 @@ k_rem_split(const typename Key<KT>::T *__restrict__ keys, long long n, long long
         U val = 0;
 #pragma unroll
         for (int i = 0; i < IPT; ++i)
-            if ((keep >> i) & 1u) { has = 1; val = k[i]; idx = t * IPT + i; }
+            if ((keep >> i) & Mask(1)) { has = 1; val = k[i]; idx = t * IPT + i; }
         // inclusive scan over the CTA of "the latest candidate so far"
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -257,16 +263,16 @@ k_rem_split(const typename Key<KT>::T *__restrict__ keys, long long n, long long
                 if (w_idx[w] >= 0) { ph = 1; pv = w_val[w]; pi = w_idx[w]; break; }
         }
         // consecutive candidates out of order: both stop being candidates
-        unsigned int drop = 0;
+        Mask drop = 0;
         int found = 0;
 #pragma unroll
         for (int i = 0; i < IPT; ++i) {
-            if ((keep >> i) & 1u) {
+            if ((keep >> i) & Mask(1)) {
                 if (ph && pv > k[i]) {
                     found = 1;
-                    drop |= 1u << i;
+                    drop |= Mask(1) << i;
                     const int pt = pi / IPT;
-                    if (pt == t) drop |= 1u << (pi - t * IPT);
+                    if (pt == t) drop |= Mask(1) << (pi - t * IPT);
                     else dropf[pi] = 1;
                 }
                 ph = 1; pv = k[i]; pi = t * IPT + i;
@@ -276,7 +282,7 @@ k_rem_split(const typename Key<KT>::T *__restrict__ keys, long long n, long long
         const int any = __syncthreads_or(found);
 #pragma unroll
         for (int i = 0; i < IPT; ++i)
-            if (dropf[t * IPT + i]) keep &= ~(1u << i);
+            if (dropf[t * IPT + i]) keep &= ~(Mask(1) << i);
         if (!any) break;
         if (round + 1 >= REM_ROUNDS) { keep = 0; break; }
         __syncthreads();                            // w_val / w_idx are rewritten next round
@@ -286,7 +292,7 @@ split_done:
     // both counts in one scan ((candidates << 16) | others: a tile has fewer
     // than 2^16 keys)
     {
-        const unsigned int ns = __popc(keep), nd = __popc(valid) - ns;
+        const unsigned int ns = popc_mask(keep), nd = popc_mask(valid) - ns;
         unsigned int tot;
         const unsigned int mine = (ns << 16) | nd;
         const unsigned int ex = rem_block_sum_scan<NT, unsigned int>(mine, w_cnt, &tot) - mine;
@@ -295,8 +301,8 @@ split_done:
         __syncthreads();                            // every key is in registers: s is free
 #pragma unroll
         for (int i = 0; i < IPT; ++i) {
-            if ((keep >> i) & 1u) s[ps++] = k[i];
-            else if ((valid >> i) & 1u) s[pd++] = k[i];
+            if ((keep >> i) & Mask(1)) s[ps++] = k[i];
+            else if ((valid >> i) & Mask(1)) s[pd++] = k[i];
         }
         if (t == 0) s_count[tile] = s_tot;
         __syncthreads();

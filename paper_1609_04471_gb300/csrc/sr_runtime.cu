@@ -270,7 +270,8 @@ extern "C" sr_status sr_get_stats(sr_stats *out) {
         skipped = out->passes_planned - merged;
         bytes += (unsigned long long)merged * 2 * n * elem;
         if (repaired) bytes += 2 * c.repair_keys * elem;                  // the boundary windows, in place
-        if (((r.cur0 + merged) & 1) != 0) bytes += 2 * n * elem;         // copy back
+        const int cur = r.cur0 | (c.tile_perm ? 1 : 0);                  // where the block sort wrote
+        if (((cur + merged) & 1) != 0) bytes += 2 * n * elem;            // copy back
     } else if (out->input_class == 2) {
         bytes += 2 * n * elem;                                          // one reversal
     } else if (out->input_class == 3) {

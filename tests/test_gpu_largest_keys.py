@@ -51,7 +51,7 @@ def _dev(a):
 @pytest.mark.parametrize("dtype", [np.int32, np.uint32, np.float32, np.uint64, np.int64])
 def test_keys_with_the_largest_key(gpu_lib, dtype):
     rng = np.random.default_rng(17)
-    for n in (1000, 12800 * 3 + 11, 200_003, (1 << 20) + 77):
+    for n in (1000, 16896 * 3 + 11, 12800 * 5 + 3, 200_003, (1 << 20) + 77):
         for share, alphabet in ((0.0, None), (1e-4, None), (0.01, None), (0.3, 9), (1.0, None)):
             a = _input(rng, n, dtype, share, alphabet)
             x = _dev(a)
@@ -65,7 +65,7 @@ def test_keys_with_the_largest_key(gpu_lib, dtype):
 def test_pairs_with_the_largest_key(gpu_lib, dtype):
     import torch
     rng = np.random.default_rng(19)
-    for n in (12800 * 2 + 5, 200_003, (1 << 20) + 3):
+    for n in (12800 * 2 + 5, 16896 * 2 + 7, 200_003, (1 << 20) + 3):
         for share, alphabet in ((1e-3, None), (0.2, 5)):
             k = _input(rng, n, dtype, share, alphabet)
             v = np.arange(n, dtype=np.uint32)

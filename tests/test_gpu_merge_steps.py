@@ -50,6 +50,14 @@ def _sizes(sr, kb, vals=False):
     return sorted(out)
 
 
+def _tile(sr):
+    """The block-sort tile of 4-byte keys alone, as the library's statistics
+    report it after a small sort."""
+    import torch
+    sr.sort_keys(torch.zeros(1000, dtype=torch.int32, device="cuda"), key_type=0)
+    return sr.stats()["tile"]
+
+
 def _dev(a, offset=0):
     """A device copy of a; offset > 0 puts it that many elements past a
     16-byte boundary (a view into a larger buffer)."""
@@ -103,9 +111,9 @@ def test_presorted_groups_skip_steps(gpu_lib):
     are skipped (statistics) and the result still equals the oracle's."""
     import torch
     st0 = None
-    for n in (64 * 12800 + 5, 33 * 12800):
+    ts = _tile(gpu_lib)
+    for n in (64 * ts + 5, 33 * ts):
         a = np.sort(si.uniform_i32(n, 5))
-        ts = 12800
         # shuffle inside each block-sort tile only: every merge level is in order
         rng = np.random.default_rng(5)
         for t0 in range(0, n, ts):
@@ -124,7 +132,9 @@ import sys, numpy as np, torch
 sys.path.insert(0, {root!r})
 import paper_1609_04471_gb300 as sr, oracle, sortrace_inputs as si
 rng = np.random.default_rng(9)
-sizes = [12801, 2 * 12800 + 3, 4 * 12800 + 1, 5 * 12800 + 7, 17 * 12800 + 1, (1 << 20) + 3]
+sr.sort_keys(torch.zeros(1000, dtype=torch.int32, device="cuda"), key_type=0)
+ts = sr.stats()["tile"]
+sizes = [ts + 1, 2 * ts + 3, 4 * ts + 1, 5 * ts + 7, 17 * ts + 1, (1 << 20) + 3]
 for n in sizes:
     for dt, kt in ((np.int32, 0), (np.uint64, 3)):
         a = rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(dt) if dt == np.int32 else \
@@ -144,7 +154,7 @@ a = si.uniform_i32(1 << 24, 3)
 x = torch.from_numpy(a.copy()).cuda()
 sr.sort_keys(x, key_type=0)
 assert x.cpu().numpy().tobytes() == oracle.sort_keys(a).tobytes()
-print("child ok", sr.stats()["passes_planned"])
+print("child ok", sr.stats()["passes_planned"], ts)
 """
 
 
@@ -163,8 +173,8 @@ def test_other_staging_and_fanin(env):
                        timeout=600)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "child ok" in r.stdout
-    planned = int(r.stdout.split("child ok")[1].split()[0])
-    levels = 11                                  # 2^24 int32 keys: 1311 tiles of 12,800
+    planned, ts = (int(x) for x in r.stdout.split("child ok")[1].split()[:2])
+    levels = int(np.ceil(np.log2(-(-(1 << 24) // ts))))     # binary merge levels over 2^24 int32 keys
     assert planned == ((levels + 1) // 2 if env.get("SORTRACE_MERGE_FANIN") == "4" else levels)
 
 
@@ -176,7 +186,7 @@ def test_descending_tile_chains(gpu_lib):
     where the block sort writes to the other buffer and where it works in
     place."""
     import torch
-    ts = 12800
+    ts = _tile(gpu_lib)
     for n in (64 * ts, 64 * ts + 77, 32 * ts + 5, 33 * ts):
         rng = np.random.default_rng(n)
         cases = [si.k_even_teeth(n - n % 4, 4), si.k_sharp_teeth(n - n % 8, 8),
