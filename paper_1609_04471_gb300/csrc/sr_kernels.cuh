@@ -490,8 +490,13 @@ __global__ void __launch_bounds__(FEW_NT2) k_few_sample2(const typename Key<KT>:
 // own histogram, which goes to row blockIdx.x of `hist` with plain stores; a
 // key outside the set raises few_miss and the ordinary sort runs instead.  At
 // most FEW_COUNT_CTAS CTAs; dynamic shared memory: few_count_smem().
-enum { FEW_COUNT_CTAS = 160, FEW_COUNT_NT = 1024 };
-constexpr size_t few_count_smem() { return (size_t)FEW_A_SLOTS * 8 + (size_t)FEW_MAX * 4; }
+// With at most FEW_WARP_HIST distinct keys every warp counts into its own
+// shared histogram row (the rows are summed at the end), so the warps of a CTA
+// do not contend for the same few counters.
+enum { FEW_COUNT_CTAS = 160, FEW_COUNT_NT = 1024, FEW_WARP_HIST = 64 };
+constexpr size_t few_count_smem() {
+    return (size_t)FEW_A_SLOTS * 8 + (size_t)FEW_MAX * 4 + (size_t)(FEW_COUNT_NT / 32) * FEW_WARP_HIST * 4;
+}
 template <int KT>
 __global__ void __launch_bounds__(FEW_COUNT_NT) k_few_count(const typename Key<KT>::T *__restrict__ keys, long long n,
                                                             Ctrl *__restrict__ c, const FewTables *__restrict__ ft,
@@ -502,11 +507,15 @@ __global__ void __launch_bounds__(FEW_COUNT_NT) k_few_count(const typename Key<K
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long *s_tab = reinterpret_cast<unsigned long long *>(smem);
     unsigned int *s_h = reinterpret_cast<unsigned int *>(s_tab + FEW_A_SLOTS);
+    unsigned int *s_wh = s_h + FEW_MAX;            // per-warp rows when k <= FEW_WARP_HIST
     if (!c->few_cand) return;
     const int t = threadIdx.x;
     const int k = (int)c->few_n;
+    const bool rows = k <= FEW_WARP_HIST;
+    unsigned int *h_mine = rows ? s_wh + (t >> 5) * FEW_WARP_HIST : s_h;
     for (int q = t; q < FEW_A_SLOTS; q += FEW_COUNT_NT) s_tab[q] = 0ull;
     for (int q = t; q < k; q += FEW_COUNT_NT) s_h[q] = 0u;
+    for (int q = t; q < (FEW_COUNT_NT / 32) * FEW_WARP_HIST; q += FEW_COUNT_NT) s_wh[q] = 0u;
     __syncthreads();
     constexpr unsigned int MASK = FEW_A_SLOTS - 1;
     for (int q = t; q < k; q += FEW_COUNT_NT) {    // the images are distinct: one slot each
@@ -525,7 +534,7 @@ __global__ void __launch_bounds__(FEW_COUNT_NT) k_few_count(const typename Key<K
             const unsigned long long e2 = s_tab[h];
             if (e2 == 0ull) { miss = true; return; }
             if ((unsigned int)(e2 >> 32) == u) {
-                atomicAdd(&s_h[(unsigned int)e2 - 1u], 1u);
+                atomicAdd(&h_mine[(unsigned int)e2 - 1u], 1u);
                 return;
             }
         }
@@ -546,6 +555,14 @@ __global__ void __launch_bounds__(FEW_COUNT_NT) k_few_count(const typename Key<K
     for (long long i = tail + gtid; i < n; i += stride) count(__ldg(keys + i));
     if (miss && !((volatile int *)&c->few_miss)[0]) atomicExch(&c->few_miss, 1);
     __syncthreads();
+    if (rows) {
+        for (int q = t; q < k; q += FEW_COUNT_NT) {
+            unsigned int sum = 0;
+            for (int w = 0; w < FEW_COUNT_NT / 32; ++w) sum += s_wh[w * FEW_WARP_HIST + q];
+            s_h[q] = sum;
+        }
+        __syncthreads();
+    }
     for (int q = t; q < k; q += FEW_COUNT_NT) hist[(long long)blockIdx.x * FEW_MAX + q] = s_h[q];
 }
 
@@ -555,11 +572,17 @@ static __global__ void __launch_bounds__(256) k_few_reduce(const unsigned int *_
                                                     const Ctrl *__restrict__ c, FewTables *__restrict__ ft) {
     griddep_wait();
     if (!c->few_cand || c->few_miss) return;
-    const int j = blockIdx.x * 256 + threadIdx.x;
-    if (j >= (int)c->few_n) return;
-    unsigned long long s = 0;
-    for (int r = 0; r < rows; ++r) s += hist[(long long)r * FEW_MAX + j];
-    ft->count[j] = s;
+    // one warp per distinct key: its lanes sum the CTAs' rows, then a warp sum
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x / 32);
+    const int k = (int)c->few_n;
+    for (int j = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); j < k; j += warps) {
+        unsigned long long s = 0;
+        for (int r = lane; r < rows; r += 32) s += hist[(long long)r * FEW_MAX + j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) ft->count[j] = s;
+    }
 }
 
 // Few distinct keys, step 3: when every key was in the set, writes the sorted
@@ -642,14 +665,22 @@ __global__ void __launch_bounds__(256) k_few_write(typename Key<KT>::T *__restri
             long long v = c0 + lane;
             if (v >= end) continue;
             int j = which(4 * v);
+            uint32_t kj = (uint32_t)key_of(j);      // the key of run j, and where run j ends
+            long long ej = j + 1 < k ? (long long)s_start[j + 1] : LLONG_MAX;
             for (; v < end; v += 32) {
                 const long long i = 4 * v;
+                if (i + 4 <= ej) {                 // the whole vector lies in run j
+                    q4[v] = make_uint4(kj, kj, kj, kj);
+                    continue;
+                }
                 uint32_t e4[4];
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
                     while (j + 1 < k && (long long)s_start[j + 1] <= i + m) ++j;
                     e4[m] = (uint32_t)key_of(j);
                 }
+                kj = e4[3];
+                ej = j + 1 < k ? (long long)s_start[j + 1] : LLONG_MAX;
                 q4[v] = make_uint4(e4[0], e4[1], e4[2], e4[3]);
             }
         }

@@ -921,13 +921,21 @@ def test_few_keys_chunked_write_and_lookup_model():
                     if v >= end:
                         continue
                     j = which(4 * v)
+                    ej = start[j + 1] if j + 1 < k else float("inf")   # where run j ends
                     while v < end:
                         i = 4 * v
+                        if i + 4 <= ej:                 # the whole vector in run j
+                            for m in range(4):
+                                assert out[i + m] is None
+                                out[i + m] = j
+                            v += 32
+                            continue
                         for m in range(4):
                             while j + 1 < k and start[j + 1] <= i + m:
                                 j += 1
                             assert out[i + m] is None
                             out[i + m] = j
+                        ej = start[j + 1] if j + 1 < k else float("inf")
                         v += 32
                 c0 += warps * CH
         for i in range(4 * nv, n):                   # the scalar tail
