@@ -299,12 +299,13 @@ template <int KT, bool VALS> struct PlainSort {
                 if ((st = allow_smem(k_rem_merge<KT, REM_TNT, RMIPT, true>, rm_smem)) != SR_OK) break;
                 if ((st = allow_smem(k_rem_merge<KT, REM_TNT, RMIPT, false>, rm_smem)) != SR_OK) break;
                 const long long n_src = dofs + rtiles * (long long)REM_CAP;
+                int *st_word = status ? status : &ctrl->status;
                 if (vec) {
                     SR_LAUNCH(SR_KERNEL_DISPLACED, (k_rem_merge<KT, REM_TNT, RMIPT, true>), rgrid, REM_TNT, rm_smem,
-                              s, uk, sk, n_src, dofs, (int)RT, rtiles, ctrl, scount, bcount, blk);
+                              s, uk, sk, n_src, dofs, (int)RT, rtiles, ctrl, scount, bcount, blk, st_word);
                 } else {
                     SR_LAUNCH(SR_KERNEL_DISPLACED, (k_rem_merge<KT, REM_TNT, RMIPT, false>), rgrid, REM_TNT, rm_smem,
-                              s, uk, sk, n_src, dofs, (int)RT, rtiles, ctrl, scount, bcount, blk);
+                              s, uk, sk, n_src, dofs, (int)RT, rtiles, ctrl, scount, bcount, blk, st_word);
                 }
             }
         } while (0);

@@ -418,12 +418,13 @@ __global__ void SR_REM_MERGE_BOUNDS
 k_rem_merge(typename Key<KT>::T *__restrict__ out, const typename Key<KT>::T *__restrict__ src, long long n_src,
             long long dofs, int ts, long long tiles, const Ctrl *__restrict__ c,
             const unsigned int *__restrict__ s_count, const unsigned int *__restrict__ b_count,
-            const long long *__restrict__ blk_off) {
+            const long long *__restrict__ blk_off, int *status) {
     griddep_wait();
     typedef Key<KT> K;
     typedef typename K::U U;
     if (!c->rem_gate) return;
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned long long bar;             // the bulk-copy staging's barrier, set up per tile
     U *s = reinterpret_cast<U *>(smem);
     for (long long b = blockIdx.x; b < tiles; b += gridDim.x) {
         const long long na = s_count[b], nb = b_count[b];
@@ -431,7 +432,8 @@ k_rem_merge(typename Key<KT>::T *__restrict__ out, const typename Key<KT>::T *__
         __syncthreads();                            // the previous tile's shared buffers are free
         if (na + nb > 0)                            // na <= ts and nb <= REM_CAP: one merge tile holds it
             merge_tile<KT, NT, MIPT, false, VEC>(src, out, nullptr, nullptr, n_src, blk_off[b], (int)(na + nb), a_beg,
-                                                 a_beg + na, b_beg, s, nullptr);
+                                                 a_beg + na, b_beg, s, nullptr, nullptr, 0, VEC ? &bar : nullptr,
+                                                 status);
     }
 }
 
