@@ -134,7 +134,13 @@ template <> struct Shape<4, true>  { enum { NT = SR_MERGE_NT, IPT = SR_K4V_IPT, 
 #ifndef SR_SORT_MINB8
 #define SR_SORT_MINB8 2
 #endif
-template <> struct Shape<8, false> { enum { NT = SR_MERGE_NT, IPT = SR_K8_IPT, SORT_NT = SR_SORT_NT, MERGE_MINB = 4, MERGE4_MINB = 4, SORT_MINB = SR_SORT_MINB8 }; };
+// MERGE4_MINB for 8-byte keys: five CTAs per SM for keys alone (48 registers;
+// uint64 keys at 2^26: 4-way steps 2.30 -> 2.10 ms), four with payloads (five
+// spill and ran slower).
+#ifndef SR_MERGE4_MINB8
+#define SR_MERGE4_MINB8 5
+#endif
+template <> struct Shape<8, false> { enum { NT = SR_MERGE_NT, IPT = SR_K8_IPT, SORT_NT = SR_SORT_NT, MERGE_MINB = 4, MERGE4_MINB = SR_MERGE4_MINB8, SORT_MINB = SR_SORT_MINB8 }; };
 template <> struct Shape<8, true>  { enum { NT = SR_MERGE_NT, IPT = SR_K8V_IPT, SORT_NT = SR_SORT_NT, MERGE_MINB = 4, MERGE4_MINB = 4, SORT_MINB = SR_SORT_MINB8 }; };
 
 // ------------------------------------------------------------- merge path
