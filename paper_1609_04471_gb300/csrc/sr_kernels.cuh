@@ -992,8 +992,9 @@ k_repair_plan(const typename Key<KT>::T *__restrict__ uk, const typename Key<KT>
 
 // Where natural run q starts (n for q >= nruns; keys, not tiles).
 __device__ __forceinline__ long long nrun_pos(const int *__restrict__ rs0, int nruns, long long q, long long ts,
-                                              long long n) {
-    return q >= nruns ? n : min((long long)rs0[q] * ts, n);
+                                              long long n, long long tiles) {
+    if (q >= nruns) return n;
+    return min((nruns == tiles ? q : (long long)rs0[q]) * ts, n);   // every tile a run: no table read
 }
 
 // The natural run that holds tile t (the last q with rs0[q] <= t).
@@ -1075,9 +1076,9 @@ k_partition(const typename Key<KT>::T *__restrict__ uk, const typename Key<KT>::
     const int nruns = c->nruns;
     const long long q = nrun_of(rs0, nruns, tiles, out / ts);
     const long long p0 = (q / (2 * span)) * (2 * span);
-    const long long a_beg = nrun_pos(rs0, nruns, p0, ts, n);
-    const long long a_end = nrun_pos(rs0, nruns, p0 + span, ts, n);
-    const long long b_end = nrun_pos(rs0, nruns, p0 + 2 * span, ts, n);
+    const long long a_beg = nrun_pos(rs0, nruns, p0, ts, n, tiles);
+    const long long a_end = nrun_pos(rs0, nruns, p0 + span, ts, n, tiles);
+    const long long b_end = nrun_pos(rs0, nruns, p0 + 2 * span, ts, n, tiles);
     const long long sp = merge_split<KT>(cur ? sk : uk, a_beg, a_end, b_end, out, nv, lane, lg,
                                          samp ? samp + cur * smt : nullptr);
     if (leader) {
@@ -1449,17 +1450,20 @@ k_merge(typename Key<KT>::T *uk, uint32_t *uv, typename Key<KT>::T *sk, uint32_t
     typedef typename K::U U;
     constexpr int NV = NT * IPT;
     constexpr int SV = merge_tile_sv<NV>();        // staged keys, with room for window slack
-    if (step >= steps_of(c)) return;               // also when the input needs no sorting
+    const long long b = blockIdx.x;
+    // the tile's split entries (the table has a boundary past the last tile)
+    // and the call's state, loaded together before any of them is tested
+    const long long a0 = splits[4 * b], a_beg = splits[4 * b + 1], a_end = splits[4 * b + 2];
+    const long long b_end = splits[4 * b + 3], a_next = splits[4 * (b + 1)];
+    const int nsteps = steps_of(c);
+    const int cur = c->src_buf[step];
+    if (step >= nsteps) return;                    // also when the input needs no sorting
     extern __shared__ __align__(16) unsigned char smem[];
     U *s = reinterpret_cast<U *>(smem);
     uint32_t *sv = reinterpret_cast<uint32_t *>(s + SV);
-    const int cur = c->src_buf[step];
-    const long long b = blockIdx.x;
     const long long out0 = b * NV;
     const long long out1 = min(out0 + NV, n);
-    const long long a0 = splits[4 * b], a_beg = splits[4 * b + 1], a_end = splits[4 * b + 2];
-    const long long b_end = splits[4 * b + 3];
-    const long long a1 = (out1 == b_end) ? a_end : splits[4 * (b + 1)];
+    const long long a1 = (out1 == b_end) ? a_end : a_next;
     const long long b0 = a_end + (out0 - a_beg) - (a0 - a_beg);
     // the output's tile samples go with the buffer it lands in
     __shared__ unsigned long long bar;
@@ -1711,7 +1715,7 @@ k_partition4(const typename Key<KT>::T *__restrict__ uk, const typename Key<KT>:
     const long long g0 = (q / (4 * span)) * (4 * span);
     long long e[5];                                // A = [e0, e1), B = [e1, e2), C = [e2, e3), D = [e3, e4)
 #pragma unroll
-    for (int i = 0; i < 5; ++i) e[i] = nrun_pos(rs0, nruns, g0 + i * span, ts, n);
+    for (int i = 0; i < 5; ++i) e[i] = nrun_pos(rs0, nruns, g0 + i * span, ts, n, tiles);
     const PairView AB = pair_view(e[0], e[1], e[2], nv), CD = pair_view(e[2], e[3], e[4], nv);
     const long long d = out - e[0];                // a multiple of nv
     long long lo = max(0ll, d - CD.len), hi = min(d, AB.len);
