@@ -572,17 +572,25 @@ static __global__ void __launch_bounds__(256) k_few_reduce(const unsigned int *_
                                                     const Ctrl *__restrict__ c, FewTables *__restrict__ ft) {
     griddep_wait();
     if (!c->few_cand || c->few_miss) return;
-    // one warp per distinct key: its lanes sum the CTAs' rows, then a warp sum
-    const int lane = threadIdx.x & 31;
-    const int warps = gridDim.x * (blockDim.x / 32);
     const int k = (int)c->few_n;
-    for (int j = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); j < k; j += warps) {
+    const int warps = gridDim.x * (blockDim.x / 32);
+    if (k > warps) {                               // many keys: one thread per key, its rows in sequence
+        const int j = blockIdx.x * blockDim.x + threadIdx.x;
+        if (j >= k) return;
         unsigned long long s = 0;
-        for (int r = lane; r < rows; r += 32) s += hist[(long long)r * FEW_MAX + j];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) ft->count[j] = s;
+        for (int r = 0; r < rows; ++r) s += hist[(long long)r * FEW_MAX + j];
+        ft->count[j] = s;
+        return;
     }
+    // few keys: one warp per key, its lanes sum the CTAs' rows, then a warp sum
+    const int lane = threadIdx.x & 31;
+    const int j = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (j >= k) return;
+    unsigned long long s = 0;
+    for (int r = lane; r < rows; r += 32) s += hist[(long long)r * FEW_MAX + j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) ft->count[j] = s;
 }
 
 // Few distinct keys, step 3: when every key was in the set, writes the sorted
