@@ -266,6 +266,32 @@ __device__ __forceinline__ void serial_merge_marked(const U *s, int a, int b, U 
     }
 }
 
+// serial_merge_marked for keys alone, where equal keys cannot be told apart
+// and no output needs its source index: the two heads are kept as (the head
+// not taken, with its index) and (the key just loaded, with its index), so a
+// step is the min and the max of the two heads and only the taken side's
+// index moves (two selects fewer than tracking A's and B's heads).  The
+// outputs are those of serial_merge_marked; the reads are the same keys, and
+// a thread whose outputs run past both ranges keeps taking one side past its
+// mark, so s must be readable IPT keys beyond the later mark.
+template <typename U, int IPT>
+__device__ __forceinline__ void serial_merge_marked_keys(const U *s, int a, int b, U (&k)[IPT]) {
+    U x = s[a], y = s[b];
+    int px = a, py = b;
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+        const bool p = y < x;                      // take y's side
+        k[i] = p ? y : x;
+        const U o = p ? x : y;
+        const int po = p ? px : py;
+        const int pt = (p ? py : px) + 1;
+        x = o;
+        px = po;
+        y = s[pt];
+        py = pt;
+    }
+}
+
 template <typename U, int IPT>
 __device__ __forceinline__ void serial_merge(const U *s, int a, int a_end, int b, int b_end,
                                              U (&k)[IPT], int (&ix)[IPT]) {
@@ -583,8 +609,9 @@ __device__ __forceinline__ U *block_sort_rs(U (&k)[IPT], uint32_t (&v)[IPT], U *
         }
         const int sp = merge_path(sa + a0, run, sa + b0, run, diag);
         int ix[IPT];
-        if (fast) serial_merge_marked<U, IPT>(sa, a0 + sp, b0 + diag - sp, k, ix);
-        else      serial_merge_slack<U, IPT>(sa, a0 + sp, a0 + run, b0 + diag - sp, b0 + run, k, ix);
+        if (fast && !VALS) serial_merge_marked_keys<U, IPT>(sa, a0 + sp, b0 + diag - sp, k);
+        else if (fast)     serial_merge_marked<U, IPT>(sa, a0 + sp, b0 + diag - sp, k, ix);
+        else               serial_merge_slack<U, IPT>(sa, a0 + sp, a0 + run, b0 + diag - sp, b0 + run, k, ix);
         if (VALS) {
 #pragma unroll
             for (int i = 0; i < IPT; ++i) v[i] = va[ix[i]];

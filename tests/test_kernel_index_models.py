@@ -967,12 +967,31 @@ def test_few_keys_chunked_write_and_lookup_model():
         assert look(u) == (imgs.index(u) if u in s else None)
 
 
+def _marked_keys_step(rd, a, b, IPT, lt):
+    """serial_merge_marked_keys (sr_device.cuh): the heads kept as (the head
+    not taken, its index) and (the key just loaded, its index); a step takes
+    the smaller head and moves only the taken side's index."""
+    x, px = rd(a), a
+    y, py = rd(b), b
+    out = []
+    for _ in range(IPT):
+        p = lt(y, x)
+        out.append(y if p else x)
+        o, po = (x, px) if p else (y, py)
+        pt = (py if p else px) + 1
+        x, px = o, po
+        y, py = rd(pt), pt
+    return out
+
+
 def test_marked_merge_tile_model():
     """merge_tile's bulk staging (sr_kernels.cuh) with end-marked windows: A's
     4-key groups, a spare group, B's groups, umax after each window, and the
     one-comparison merge step (serial_merge_marked).  Outputs equal the stable
     merge (ties to A), every staged slot fits merge_tile_sv, and every read
-    stays below it plus the IPT + 8 keys of slack."""
+    stays below it plus the IPT + 8 keys of slack.  The keys-alone step
+    (serial_merge_marked_keys) gives the same key values, its reads (threads
+    past the tile's end included) inside the same bounds."""
     rng = random.Random(11)
     UMAX = 10 ** 9
     for trial in range(400):
@@ -1010,7 +1029,7 @@ def test_marked_merge_tile_model():
 
         def lt(x, y):                                 # the order of the images alone
             return x[0] < y[0]
-        out = []
+        out, out_keys = [], []
         for t in range(NT):
             diag = min(t * IPT, cnt)
             lo, hi = max(0, diag - bcnt), min(diag, acnt)
@@ -1021,6 +1040,8 @@ def test_marked_merge_tile_model():
                 else:
                     hi = m
             a, b = sa + lo, sb + diag - lo
+            kk = _marked_keys_step(rd, a, b, IPT, lt)
+            out_keys.extend(x[0] for x in kk[:max(0, min(IPT, cnt - diag))])
             ak, bk = rd(a), rd(b)
             k = []
             for i in range(IPT):
@@ -1035,17 +1056,19 @@ def test_marked_merge_tile_model():
             out.extend(k[:max(0, min(IPT, cnt - diag))])
         want = sorted([(v, 0, i) for i, v in enumerate(A)] + [(v, 1, i) for i, v in enumerate(B)])
         assert out == want, (NT, IPT, acnt, bcnt)
+        assert out_keys == [x[0] for x in want], (NT, IPT, acnt, bcnt)
         assert reads[0] < size
 
 
-def _block_sort_pp(keys, NT, IPT, umax):
+def _block_sort_pp(keys, NT, IPT, umax, keys_only=False):
     """block_sort_pp and block_sort_rs (sr_device.cuh) on one tile of NT*IPT
     keys: the per-warp stretches of the warp-synchronised rounds and the end
     marks (the layout both share; block_sort_rs reads a round's runs from the
     buffer it then writes, after its warp or block has read them all).  Checks
     every read against the buffer and, in those rounds, every read and write
     against the warp's own stretch, and that a round reads only slots the
-    round before it wrote."""
+    round before it wrote.  keys_only: block_sort_rs for keys alone, whose
+    marked rounds take serial_merge_marked_keys's step."""
     W = 32 * IPT + 32
     size = NT * IPT + NT
     assert (NT // 32) * W == size
@@ -1090,6 +1113,18 @@ def _block_sort_pp(keys, NT, IPT, umax):
                 else:
                     hi = mid
             a, b, a_end, b_end = a0 + lo, b0 + diag - lo, a0 + run, b0 + run
+            if fast and keys_only:
+                def rd_run(i):                        # inside the two runs and their marks
+                    assert a0 <= i <= a_end or b0 <= i <= b_end, (coop, t, i)
+                    return rd(i)
+                for i, v in enumerate(_marked_keys_step(rd_run, a, b, IPT, lambda x, y: x < y)):
+                    o = o0 + diag + i
+                    assert lo_ok <= o < hi_ok
+                    new[o] = v
+                if t - first == coop - 1:
+                    assert lo_ok <= o0 + 2 * run < hi_ok
+                    new[o0 + 2 * run] = umax
+                continue
             ak, bk = rd(a), rd(b)
             for i in range(IPT):
                 tb = (bk < ak) if fast else (b < b_end and (a >= a_end or bk < ak))
@@ -1127,6 +1162,7 @@ def test_block_sort_pp_model(NT, IPT):
         else:
             keys = [rng.choice([0, umax, rng.randrange(100)]) for _ in range(n)]
         assert _block_sort_pp(keys, NT, IPT, umax) == sorted(keys)
+        assert _block_sort_pp(keys, NT, IPT, umax, keys_only=True) == sorted(keys)
 
 
 def test_block_sort_rs_payload_model():
