@@ -1216,17 +1216,14 @@ __device__ __forceinline__ void write_tile(const typename Key<KT>::U (&k)[IPT], 
 // The merge of one tile's staged windows A = s[sa, sa + acnt) and B = s[sb,
 // sb + bcnt): thread outputs diag .. diag + IPT into k (with their staged
 // positions in ix).  `marks`: the key after each window is `mark`, so when
-// neither window holds it the steps compare once (serial_merge_marked, or
-// serial_merge_marked_keys when KEYS: keys alone, ix not needed).  C is the
-// type the keys compare in (the order images, or int32 for raw int32 keys).
-template <typename C, int IPT, bool KEYS>
+// neither window holds it the steps compare once (serial_merge_marked).  C is
+// the type the keys compare in (the order images, or int32 for raw int32 keys).
+template <typename C, int IPT>
 __device__ __forceinline__ void tile_merge(const C *s, int sa, int acnt, int sb, int bcnt, int cnt, int diag,
                                            bool marks, C mark, C (&k)[IPT], int (&ix)[IPT]) {
     const int sp = merge_path(s + sa, acnt, s + sb, bcnt, diag);
     const bool marked = marks && (acnt == 0 || s[sa + acnt - 1] != mark) && (bcnt == 0 || s[sb + bcnt - 1] != mark);
-    if (marked && KEYS) {
-        serial_merge_marked_keys<C, IPT>(s, sa + sp, sb + diag - sp, k);
-    } else if (marked) {
+    if (marked) {
         serial_merge_marked<C, IPT>(s, sa + sp, sb + diag - sp, k, ix);
     } else if (SR_MERGE_1LD) {
         serial_merge_slack<C, IPT>(s, sa + sp, sa + acnt, sb + diag - sp, sb + bcnt, k, ix);
@@ -1431,15 +1428,15 @@ __device__ __forceinline__ void merge_tile(const typename Key<KT>::T *__restrict
     if constexpr (RAW_OK) {
         if (raw) {
             int ki[IPT];
-            tile_merge<int, IPT, !VALS>(reinterpret_cast<const int *>(s), sa, acnt, sb, bcnt, cnt, diag, true,
-                                        INT_MAX, ki, ix);
+            tile_merge<int, IPT>(reinterpret_cast<const int *>(s), sa, acnt, sb, bcnt, cnt, diag, true, INT_MAX, ki,
+                                 ix);
 #pragma unroll
             for (int i = 0; i < IPT; ++i) k[i] = (U)ki[i];
         } else {
-            tile_merge<U, IPT, !VALS>(s, sa, acnt, sb, bcnt, cnt, diag, VEC && bar, mark, k, ix);
+            tile_merge<U, IPT>(s, sa, acnt, sb, bcnt, cnt, diag, VEC && bar, mark, k, ix);
         }
     } else {
-        tile_merge<U, IPT, !VALS>(s, sa, acnt, sb, bcnt, cnt, diag, VEC && bar, mark, k, ix);
+        tile_merge<U, IPT>(s, sa, acnt, sb, bcnt, cnt, diag, VEC && bar, mark, k, ix);
     }
     uint32_t v[IPT];
     if (VALS) {

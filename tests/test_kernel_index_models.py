@@ -989,9 +989,7 @@ def test_marked_merge_tile_model():
     4-key groups, a spare group, B's groups, umax after each window, and the
     one-comparison merge step (serial_merge_marked).  Outputs equal the stable
     merge (ties to A), every staged slot fits merge_tile_sv, and every read
-    stays below it plus the IPT + 8 keys of slack.  The keys-alone step
-    (serial_merge_marked_keys) gives the same key values, its reads (threads
-    past the tile's end included) inside the same bounds."""
+    stays below it plus the IPT + 8 keys of slack."""
     rng = random.Random(11)
     UMAX = 10 ** 9
     for trial in range(400):
@@ -1029,7 +1027,7 @@ def test_marked_merge_tile_model():
 
         def lt(x, y):                                 # the order of the images alone
             return x[0] < y[0]
-        out, out_keys = [], []
+        out = []
         for t in range(NT):
             diag = min(t * IPT, cnt)
             lo, hi = max(0, diag - bcnt), min(diag, acnt)
@@ -1040,8 +1038,6 @@ def test_marked_merge_tile_model():
                 else:
                     hi = m
             a, b = sa + lo, sb + diag - lo
-            kk = _marked_keys_step(rd, a, b, IPT, lt)
-            out_keys.extend(x[0] for x in kk[:max(0, min(IPT, cnt - diag))])
             ak, bk = rd(a), rd(b)
             k = []
             for i in range(IPT):
@@ -1056,7 +1052,6 @@ def test_marked_merge_tile_model():
             out.extend(k[:max(0, min(IPT, cnt - diag))])
         want = sorted([(v, 0, i) for i, v in enumerate(A)] + [(v, 1, i) for i, v in enumerate(B)])
         assert out == want, (NT, IPT, acnt, bcnt)
-        assert out_keys == [x[0] for x in want], (NT, IPT, acnt, bcnt)
         assert reads[0] < size
 
 
