@@ -261,7 +261,11 @@ enum {
  * sample of the input, scattering them, sorting each bucket, and checking
  * that every bucket's largest key is <= the next bucket's smallest; if the
  * check fails the plain sort runs instead (the fallback is in stats.fallback).
- * The call reads the check's outcome back, so it waits for `stream` once.
+ * The call reads the check's outcome back, so it waits for `stream` once;
+ * inside a stream capture it reads nothing back: the plain sort becomes the
+ * body of a conditional (IF) graph node whose condition the check sets on the
+ * device, so the whole call can be captured and replayed (the first call on a
+ * device must come before any capture).
  * The paper has no learned component; this is the partition-then-sort form of
  * its quicksort (Section 4: split by pivots, then sort the parts), with the
  * pivots read off a learned CDF.

@@ -19,7 +19,9 @@
 //   k_bucket_check every bucket's last key <= the next bucket's first key;
 //                 else the fallback flag is set
 //   (plain sort)  only if the check failed (the flag is read back: this call
-//                 waits for its stream once)
+//                 waits for its stream once; inside a stream capture the
+//                 plain sort is the body of an IF node that a one-thread
+//                 kernel sets from the flag, so nothing is read back)
 //
 // The network (H = 32 hidden units; theta = [x0, delta[H], beta[H]]):
 //   d_j = softplus(delta_j), x_j = x0 + sum_{i<j} d_i, h_j = ramp((x - x_j)/d_j),
@@ -35,6 +37,7 @@
 // check catches any router for which that fails (the SR_MODEL_FORCE_BAD hook).
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 
 #include "sr_device.cuh"
 #include "sr_plain.cuh"
@@ -871,8 +874,30 @@ __global__ void k_bucket_check(const typename Key<KT>::T *__restrict__ keys, con
     if (b > 0 && p > 0 && p < n && Key<KT>::ord(keys[p - 1]) > Key<KT>::ord(keys[p])) atomicExch(&lc->fallback, 1);
 }
 
+// One thread: the condition of the IF node that holds the plain sort inside a
+// stream capture, from the bucket check's outcome.
+__global__ void k_fallback_cond(cudaGraphConditionalHandle h, const LearnCtrl *__restrict__ lc) {
+    griddep_wait();
+    if (threadIdx.x != 0) return;              // one setter of the condition
+    cudaGraphSetConditional(h, lc->fallback ? 1u : 0u);
+}
+
 // ------------------------------------------------------------- host
 
+
+// A stream per device that captures the fallback IF node's body (it never
+// runs work of its own).
+static sr_status fallback_capture_stream(int dev, cudaStream_t *out) {
+    constexpr int kMaxDev = 64;
+    static std::mutex mu;
+    static cudaStream_t streams[kMaxDev];
+    if (dev < 0 || dev >= kMaxDev) return SR_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess)
+        return launch_status();
+    *out = streams[dev];
+    return SR_OK;
+}
 
 template <int KB> struct UKey;
 template <> struct UKey<4> { enum { KT = SR_KEY_U32 }; };
@@ -905,6 +930,8 @@ static sr_status learned_impl(void *d_keys, size_t n, const sr_learned_opts *o, 
     if (n < 2) return SR_OK;
     DeviceState *ds = nullptr;
     SR_TRY(device_state(&ds));
+    cudaStream_t cb = nullptr;                     // made on the first call, before any capture that needs it
+    SR_TRY(fallback_capture_stream(ds->device, &cb));
 
     const long long N = (long long)n;
     const long long m = (N + stride - 1) / stride;
@@ -1019,6 +1046,23 @@ static sr_status learned_impl(void *d_keys, size_t n, const sr_learned_opts *o, 
             break;
         }
         rec.aux_kind = 4;
+        cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cst) != cudaSuccess) { st = launch_status(); break; }
+        if (cst == cudaStreamCaptureStatusActive) {
+            // inside the caller's capture: the plain sort goes into the body of
+            // an IF node whose condition the check's outcome sets on the device
+            // (no host read); its kernels run only when a replay falls back
+            cudaGraphConditionalHandle h;
+            if ((st = new_handle(s, &h)) != SR_OK) break;
+            SR_LAUNCH(SR_KERNEL_MODEL, k_fallback_cond, 1, 32, 0, s, h, (const LearnCtrl *)lc);
+            cudaGraph_t body[1];
+            if ((st = add_conditional(s, h, cudaGraphCondTypeIf, 1, body)) != SR_OK) break;
+            unsigned int k = 0;
+            st = capture_into(body[0], cb, [&](cudaStream_t x) { return fallback_sort.launch(uk, nullptr, sp + o_fb, x); },
+                              &k);
+            count_launches(-(long long)k);         // captured into the body, run only on a fallback
+            break;
+        }
         // the check's outcome decides whether the plain sort runs: read it back
         // (launching the plain sort gated on the device would still cost every
         // one of its kernels a full grid of empty CTAs)

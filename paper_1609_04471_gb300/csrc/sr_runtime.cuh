@@ -77,6 +77,29 @@ unsigned long long thread_launch_count();   // ... by this host thread
 // the device after it finishes its queued work; 0 if no graph ran).
 unsigned long long graph_kernel_count();
 
+// Graph conditional nodes (sr_sort.cu), for launch sequences that branch on
+// the device inside a stream capture: a handle in the graph that s is
+// capturing into; and a conditional node of `type` with `size` bodies
+// (returned in bodies) after s's current capture dependencies, which then
+// becomes the capture's only dependency.
+sr_status new_handle(cudaStream_t s, cudaGraphConditionalHandle *h);
+sr_status add_conditional(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                          unsigned size, cudaGraph_t *bodies);
+
+// Captures `fn(cb)` into the graph `body` on stream cb (which must not be
+// capturing); *kernels = the kernels it launched.
+template <typename F>
+sr_status capture_into(cudaGraph_t body, cudaStream_t cb, F fn, unsigned int *kernels) {
+    const unsigned long long l0 = thread_launch_count();
+    if (cudaStreamBeginCaptureToGraph(cb, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+        return launch_status();
+    sr_status st = fn(cb);
+    cudaGraph_t out = nullptr;
+    if (cudaStreamEndCapture(cb, &out) != cudaSuccess && st == SR_OK) st = launch_status();
+    *kernels = (unsigned int)(thread_launch_count() - l0);
+    return st;
+}
+
 // Kernel instrumentation: every launch site calls launch_begin / launch_end
 // around its <<<>>> (see SR_LAUNCH).
 void launch_begin(int kind, cudaStream_t s);

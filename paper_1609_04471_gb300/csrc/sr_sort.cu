@@ -98,6 +98,7 @@ bool graphs_enabled() {
     }();
     return on;
 }
+}  // namespace
 
 // Adds a conditional node of `type` with `size` bodies after the current
 // capture dependencies of s, and makes it the capture's only dependency.
@@ -129,21 +130,6 @@ sr_status new_handle(cudaStream_t s, cudaGraphConditionalHandle *h) {
     if (cudaStreamGetCaptureInfo(s, &cst, nullptr, &g) != cudaSuccess) return launch_status();
     if (cudaGraphConditionalHandleCreate(h, g, 0, 0) != cudaSuccess) return launch_status();
     return SR_OK;
-}
-}  // namespace
-
-// Captures `fn(stream)` into `body` on stream `cb`; *kernels = the kernels it
-// launched.
-template <typename F>
-static sr_status capture_into(cudaGraph_t body, cudaStream_t cb, F fn, unsigned int *kernels) {
-    const unsigned long long l0 = thread_launch_count();
-    if (cudaStreamBeginCaptureToGraph(cb, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess)
-        return launch_status();
-    sr_status st = fn(cb);
-    cudaGraph_t out = nullptr;
-    if (cudaStreamEndCapture(cb, &out) != cudaSuccess && st == SR_OK) st = launch_status();
-    *kernels = (unsigned int)(thread_launch_count() - l0);
-    return st;
 }
 
 // The kernels fn would launch (captured into a scratch graph and dropped).

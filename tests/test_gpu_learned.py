@@ -155,6 +155,32 @@ def test_forced_bad_router_falls_back_exactly(gpu_lib):
     assert got.view(np.uint32).tobytes() == oracle.sort_keys(a).view(np.uint32).tobytes()
 
 
+@pytest.mark.parametrize("model", ["trained", "force_bad"])
+def test_learned_in_captured_graph(gpu_lib, model):
+    """sr_sort_keys_learned captured whole in the caller's CUDA graph (no host
+    read: the plain sort sits behind an IF node that the bucket check sets on
+    the device) and replayed on new inputs: every output equals the oracle's;
+    with the forced non-monotone router every replay takes the fallback."""
+    import torch
+    m = gpu_lib.MODEL_TRAINED if model == "trained" else gpu_lib.MODEL_FORCE_BAD
+    arrays = [si.lognormal_f32(300_007, seed) for seed in (21, 22, 23)]
+    x = _dev(arrays[0])
+    gpu_lib.sort_keys_learned(x.clone(), key_type=2, model=m)   # device state exists before the capture
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        gpu_lib.sort_keys_learned(x, key_type=2, model=m, stream=s)
+    for a in arrays:
+        x.copy_(_dev(a))
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        assert x.cpu().numpy().view(np.uint32).tobytes() == oracle.sort_keys(a).view(np.uint32).tobytes()
+        assert gpu_lib.stats()["fallback"] == (1 if model == "force_bad" else 0)
+
+
 def test_trained_model_gains_over_ablations(gpu_lib):
     """What the trained network gains: on the lognormal mixture its bucket
     sizes are much closer to even than equal-width buckets' (the second moment
